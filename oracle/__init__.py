@@ -1,0 +1,12 @@
+"""FP64 CPU oracle for MGRIT on 1D periodic conservation laws (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It is compiled from ``mgrit_oracle.c``
+with gcc and shares nothing with the CUDA library.
+"""
+from .api import (  # noqa: F401
+    SCHEME_WENO5_SSPRK3, SCHEME_FO_FE, FLUX_BURGERS, FLUX_ADVECTION,
+    NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE, RELAX_F, RELAX_FCF, GUESS_EQ17, GUESS_INJECT,
+    OK, EINVAL, EDIVERGED, ENOTCONV,
+    build, weno5_left, spatial_op, step, serial, mgrit, residual, num_threads,
+)

@@ -1,0 +1,140 @@
+"""ctypes wrapper around the oracle's shared library (test infrastructure only)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mgrit_oracle.c")
+_LIB = os.path.join(_HERE, "liborc_mgrit.so")
+
+SCHEME_WENO5_SSPRK3, SCHEME_FO_FE = 0, 1
+FLUX_BURGERS, FLUX_ADVECTION = 0, 1
+NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE = 0, 1
+RELAX_F, RELAX_FCF = 0, 1
+GUESS_EQ17, GUESS_INJECT = 0, 1
+OK, EINVAL, EDIVERGED, ENOTCONV = 0, -1, -4, -5
+
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        D = ctypes.c_double
+        I = ctypes.c_int
+        P = ctypes.c_void_p
+        lib.orc_weno5_left.restype = D
+        lib.orc_weno5_left.argtypes = [P, P, P, P]
+        lib.orc_spatial_op.restype = None
+        lib.orc_spatial_op.argtypes = [I, D, I, I, I, P, P]
+        lib.orc_step.restype = None
+        lib.orc_step.argtypes = [I, D, D, I, I, I, P, P]
+        lib.orc_serial.restype = None
+        lib.orc_serial.argtypes = [I, D, D, I, I, I, I, P, P, I]
+        lib.orc_mgrit.restype = I
+        lib.orc_mgrit.argtypes = [I, I, I, I, I, I, I, D, D, I, I, D, I,
+                                  P, P, P, P, P, P, P]
+        lib.orc_residual.restype = I
+        lib.orc_residual.argtypes = [I, I, I, I, I, I, D, D, P, P]
+        lib.orc_num_threads.restype = I
+        lib.orc_num_threads.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads():
+    return _load().orc_num_threads()
+
+
+def weno5_left(q5):
+    """q^-_{i+1/2} from q_{i-2..i+2}; returns (value, p[3], beta[3], omega[3])."""
+    q = _f64(q5)
+    assert q.shape == (5,)
+    p, b, w = np.zeros(3), np.zeros(3), np.zeros(3)
+    v = _load().orc_weno5_left(_ptr(q), _ptr(p), _ptr(b), _ptr(w))
+    return v, p, b, w
+
+
+def spatial_op(u, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS, numflux=NUMFLUX_LF_SPLIT,
+               Lx=1.0):
+    u = _f64(u)
+    out = np.zeros_like(u)
+    _load().orc_spatial_op(u.size, Lx, scheme, flux, numflux, _ptr(u), _ptr(out))
+    return out
+
+
+def step(u, dt, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS, numflux=NUMFLUX_LF_SPLIT,
+         Lx=1.0):
+    u = _f64(u)
+    out = np.zeros_like(u)
+    _load().orc_step(u.size, Lx, dt, scheme, flux, numflux, _ptr(u), _ptr(out))
+    return out
+
+
+def serial(u0, dt, nsteps, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
+           numflux=NUMFLUX_LF_SPLIT, Lx=1.0, store_all=False):
+    u0 = _f64(u0)
+    nx = u0.size
+    out = np.zeros(((nsteps + 1) if store_all else 1, nx))
+    _load().orc_serial(nx, Lx, dt, nsteps, scheme, flux, numflux, _ptr(u0), _ptr(out),
+                       1 if store_all else 0)
+    return out if store_all else out[0]
+
+
+def mgrit(u0, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
+          numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, tol=1e-10,
+          max_iter=64, Lx=1.0, uC_init=None, want_full=False):
+    """Run the oracle MGRIT V-cycle.  Returns a dict with status, iters,
+    res_hist, uC ((nt/m+1, nx)), uT and (optionally) the full trajectory."""
+    u0 = _f64(u0)
+    nx = u0.size
+    nc = nt // m
+    uC = np.zeros((nc + 1, nx))
+    uT = np.zeros(nx)
+    full = np.zeros((nt + 1, nx)) if want_full else None
+    hist = np.zeros(max_iter + 2)
+    iters = ctypes.c_int(0)
+    init = None if uC_init is None else _f64(uC_init)
+    st = _load().orc_mgrit(nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax, guess,
+                           tol, max_iter, _ptr(u0), _ptr(init), _ptr(uC), _ptr(full),
+                           _ptr(uT), ctypes.cast(ctypes.pointer(iters), ctypes.c_void_p),
+                           _ptr(hist))
+    k = iters.value
+    out = dict(status=st, iters=k, res_hist=hist[:k + 1].copy(), uC=uC, uT=uT)
+    if want_full:
+        out["u"] = full
+    return out
+
+
+def residual(uC, nt, m, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
+             numflux=NUMFLUX_LF_SPLIT, Lx=1.0):
+    uC = _f64(uC)
+    nx = uC.shape[1]
+    out = np.zeros(1)
+    st = _load().orc_residual(nx, nt, m, scheme, flux, numflux, Lx, T, _ptr(uC), _ptr(out))
+    if st != OK:
+        raise ValueError("orc_residual: invalid arguments")
+    return float(out[0])
