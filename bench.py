@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark: fine cell-updates/s of the MGRIT V-cycle on one GB300.
+
+Workload (one step = one full V-cycle from the initial iterate, all levels):
+inviscid Burgers, WENO5-JS + global Lax-Friedrichs splitting + SSPRK3, FP64,
+nx = 4096 cells, nt = 16384 steps to T = 1, coarsening m = 4, 6 levels
+(coarsened until 16 C-points remain), FCF relaxation, coarse guess of
+Eq. (restriction::u); u0 = 0.5 + 8-mode random Fourier series (seed 0),
+exact cell averages.  Synthetic data: the paper's workloads are analytic
+initial conditions.
+
+value  = cells x Phi applications of one V-cycle (all levels) / device time
+e2e    = same, measured through the C ABI with u0 copied from pinned host
+         memory and u(T) copied back inside the timed region
+roofline = the level-0 relaxation kernel (the dominant kernel) against the
+         FP64 pipe: algorithmic FLOPs per cell update x cell updates per
+         launch / CUDA-event launch time
+cpu_baseline / --impl reference = the FP64 C oracle on the host cores, one
+         V-cycle of the same workload over the first quarter of the time
+         horizon (nt = 4096, T = 0.25).
+
+Multi-GPU (torchrun): independent replicas, one per GPU (the path has no
+exchange step on one problem); value = all ranks' cell updates / max time.
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(nx=4096, nt=16384, m=4, levels=6, T=1.0, seed=0)
+SAMPLE = dict(nx=4096, nt=4096, m=4, levels=6, T=0.25, seed=0)   # CPU baseline sample
+
+# Algorithmic FLOPs per cell update of one SSPRK3 step of WENO5-JS with the
+# global LF splitting, counted from the paper's formulas (every +, -, x, /,
+# |.| and max counts 1): per reconstruction 73 (3 candidates x 6, 3
+# smoothness indicators x 12, 3 weights x 3, normalisation 5 + sum 5), per
+# stage and cell 2 reconstructions + 1 (flux sum) + 2 (flux difference / dx)
+# + 9 (|u|, max, f = u^2/2, f^+/-) = 158; 3 stages + 12 for the RK
+# combinations = 486 (Burgers).
+FLOPS_PER_CELL_UPDATE = 486
+
+# FP64 peak of the SIMT pipe, from the unit counts and clocks: 152 SMs x
+# 2.07 GHz x 4 FP64 FLOP/clk/SM (the nominal 1.25 TFLOP/s FP64 rate).
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+
+# DRAM bytes (read + write) per level-0 relaxation launch from an ncu
+# capture, keyed by a hash of the kernel sources it was taken on; reported
+# only while the kernel is unchanged.
+TRAFFIC = {}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("slab.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2104_09404_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mgrit", choices=["mgrit", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serial-steps", type=int, default=1024,
+                   help="fine steps of the serial GPU stepper timed (extrapolated to nt)")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle ---
+
+def oracle_cycle_rate(sample, cycles=1):
+    """The oracle, as it stands, on `cycles` V-cycles of the sample; returns
+    (cell updates/s, seconds, threads).  Cell updates counted like the GPU's."""
+    import numpy as np  # noqa: F401
+    import oracle as O
+    from paper_2104_09404_gb300 import inputs
+    O.build()
+    u0 = inputs.fourier_ic(sample["nx"], seed=sample["seed"])
+    t0 = time.perf_counter()
+    O.vcycles(u0, sample["nt"], sample["m"], sample["levels"], sample["T"], cycles)
+    dt = time.perf_counter() - t0
+    upd = cycle_updates(sample) * cycles
+    return upd / dt, dt, O.num_threads()
+
+
+def cycle_updates(w, fcf=True):
+    # cells x Phi applications of one V-cycle (same count as mgrit_cycle_cell_updates)
+    m, L = w["m"], w["levels"]
+    steps = 0
+    for l in range(L - 1):
+        nc = w["nt"] // m ** (l + 1)
+        steps += (2 * nc * m if fcf else nc * m) + nc
+        if l >= 1:
+            steps += nc * (m - 1)
+    steps += w["nt"] // m ** (L - 1)
+    return steps * w["nx"]
+
+
+def sample_desc(s):
+    return ("one V-cycle of the workload over its first quarter: nx=%d, nt=%d, T=%g, m=%d, "
+            "%d levels, seed %d" % (s["nx"], s["nt"], s["T"], s["m"], s["levels"], s["seed"]))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_cycle_rate(SAMPLE)
+    times = []
+    for _ in range(args.steps):
+        _, dt, cores = oracle_cycle_rate(SAMPLE)
+        times.append(dt)
+    tot = sum(times)
+    upd = cycle_updates(SAMPLE) * args.steps
+    value = upd / tot
+    line = {
+        "impl": "reference",
+        "metric": "fine cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "FP64 C oracle (CPU), " + sample_desc(SAMPLE)},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
+                         "kind": "oracle", "sample": sample_desc(SAMPLE)},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------- GPU ---
+
+def run_mgrit(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2104_09404_gb300 import build as B, inputs, mgrit
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        tdist.barrier()
+    W = WORKLOAD
+    u0_np = inputs.fourier_ic(W["nx"], seed=W["seed"])
+    u0 = torch.as_tensor(u0_np, device=dev)
+    s = mgrit.Solver(W["nx"], W["nt"], W["m"], W["levels"], T=W["T"])
+    stream = torch.cuda.current_stream()
+    per_cycle = s.cycle_cell_updates()
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if ws > 1:
+            tdist.barrier()
+            torch.cuda.synchronize()
+
+    # ---- device-resident throughput: one V-cycle per step ---------------
+    for _ in range(max(args.warmup, 3)):
+        s.run_cycles(u0, 1)
+    barrier_sync()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.run_cycles(u0, 1)
+    e1.record(stream)
+    barrier_sync()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * per_cycle * args.steps / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers -----------------
+    h_u0 = torch.as_tensor(u0_np).pin_memory()
+    h_uT = torch.empty(W["nx"], dtype=torch.float64).pin_memory()
+    d_u0 = torch.empty_like(u0)
+    d_uC = torch.empty((W["nt"] // W["m"] + 1, W["nx"]), dtype=torch.float64, device=dev)
+
+    def e2e_step():
+        d_u0.copy_(h_u0, non_blocking=True)
+        s.run_cycles(d_u0, 1)
+        s.cpoints(d_uC)
+        h_uT.copy_(d_uC[-1], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier_sync()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier_sync()
+    ms_e2e = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = ws * per_cycle * args.steps / (ms_e2e / 1e3)
+
+    # ---- per-kernel times inside the cycle (CUDA events, same stream) ----
+    s.run_cycles(u0, 1)
+    torch.cuda.synchronize()
+    kern = {}
+    reps = 3
+
+    def time_kernel(name, which, level):
+        s.launch_kernel(which, level, 1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.launch_kernel(which, level, reps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        kern[name] = a.elapsed_time(b) / reps
+
+    time_kernel("relax_l0", 0, 0)
+    time_kernel("restrict_l0", 1, 0)
+    time_kernel("relax_l1", 0, 1)
+    time_kernel("coarsest", 2, 0)
+    time_kernel("interp_l1", 3, 1)
+    nC0 = W["nt"] // W["m"]
+    relax0_updates = W["nx"] * (2 * nC0 * W["m"] + nC0)
+    achieved = FLOPS_PER_CELL_UPDATE * relax0_updates / (kern["relax_l0"] / 1e3) / 1e12
+    traffic = TRAFFIC.get(kernel_hash())
+
+    # ---- serial GPU stepping and the MGRIT outcome ------------------------
+    ns = args.serial_steps
+    s.serial_step(u0, 8)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.serial_step(u0, ns)
+    b.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = a.elapsed_time(b)
+    st, _, _, stats = s.solve(u0, want_uC=False)
+    outcome = {"status": mgrit.STATUS_NAMES[st], "cycles": stats.iters,
+               "res_hist": [stats.res_hist[k] for k in range(min(stats.iters + 1, 8))],
+               "t_ms": stats.t_total_ms}
+
+    if rank != 0:
+        if ws > 1:
+            tdist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        rate, secs, cores = oracle_cycle_rate(SAMPLE)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": sample_desc(SAMPLE), "seconds": secs}
+
+    L = W["levels"]
+    launches_per_cycle = 3 + 2 * (L - 2) + 1 + (L - 2) + 1   # graph A, graph B, init broadcast
+    line = {
+        "metric": "fine cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Burgers WENO5-JS/LF-split/SSPRK3 FP64 MGRIT V-cycle: nx=4096, "
+                               "nt=16384, T=1, m=4, 6 levels, FCF, Fourier u0 seed 0",
+                   "step": "one V-cycle (all levels) from the initial iterate",
+                   "cell_updates_per_step": per_cycle,
+                   "l2": "inputs larger than L2: each cycle streams >500 MB of level rows",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "level-0 relaxation (k_slab, MODE_RELAX)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "derived FP64 SIMT rate: 152 SMs x 2.07 GHz x 4 FLOP/clk",
+                     "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                     "cell_updates_per_launch": relax0_updates},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "cell-updates/s",
+                "h2d_bytes_per_step": 8 * W["nx"], "d2h_bytes_per_step": 8 * W["nx"]},
+        "gpu_launches": launches_per_cycle * args.steps,
+        "clocks": clk,
+        "kernel_ms": kern,
+        "serial_gpu": {"steps_timed": ns, "ms_per_step": serial_ms / ns,
+                       "extrapolated_s_for_nt": serial_ms / ns * W["nt"] / 1e3,
+                       "cell_updates_per_s": W["nx"] * ns / (serial_ms / 1e3)},
+        "mgrit_outcome": outcome,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mgrit(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

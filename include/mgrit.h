@@ -1,0 +1,168 @@
+/*
+ * mgrit.h -- C ABI of libmgrit.so: GB300 (sm_103a) MGRIT for 1D periodic
+ * scalar conservation laws, after Danieli & MacLachlan, "Multigrid Reduction
+ * in Time for non-linear hyperbolic equations" (arXiv:2104.09404).
+ *
+ * Problem (Sec. 2, Eq. consLaw): u_t + f(u)_x = 0 on [0, L) x [0, T],
+ * periodic, f = u^2/2 (Burgers, Eq. burgers) or f = u (advection, speed 1).
+ * Space: nx finite-volume cells of width dx = L/nx (Sec. 2.1, Eq. spaceDisc),
+ * WENO5-JS reconstruction (Sec. 2.1.1, k = 2) or first-order (k = 0), global
+ * Lax-Friedrichs flux (Sec. 2.1.2).  Time: nt steps of dt = T/nt with SSPRK3
+ * (Eq. SSPRK3) or forward Euler (Eq. SSPRK1).
+ * Solver: FAS MGRIT V-cycle (Sec. 3.2, Algorithm 1) with coarsening factor m
+ * in time only, rediscretised coarse integrators Phi_l with step dt*m^l
+ * (Sec. 3.3), F- or FCF-relaxation (Eq. relaxation), injection restriction
+ * with the coarse initial guess of Eq. (restriction::u) or plain injection,
+ * sequential coarsest solve (Eq. coarseCorr), ideal interpolation
+ * (Eq. interpolation).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are FP64, row-major [time][cell]; one row is nx contiguous cell
+ *    values (cell i covers [i dx, (i+1) dx)).  Pointers named *_dev are
+ *    device pointers on the current CUDA device; the caller allocates and
+ *    owns them.  The context owns all level workspaces and CUDA graphs.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; functions that return a host value synchronise it.
+ *  - Return value: MGRIT_OK or a negative MGRIT_E* code; nothing aborts.
+ *    mgrit_last_error() gives a one-line description of the last failure.
+ *  - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef MGRIT_H
+#define MGRIT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgrit_ctx mgrit_ctx;
+
+enum {
+    MGRIT_OK = 0,
+    MGRIT_EINVAL = -1,     /* bad argument or unsupported size */
+    MGRIT_ECUDA = -2,      /* a CUDA runtime call failed */
+    MGRIT_ENOMEM = -3,     /* device or pinned-host allocation failed */
+    MGRIT_EDIVERGED = -4,  /* residual not finite or > 1e8 x first residual */
+    MGRIT_ENOTCONV = -5,   /* max_iter cycles without reaching tol */
+    MGRIT_ETIMEOUT = -6    /* reserved: a bounded device wait gave up */
+};
+
+/* spatial reconstruction + time integrator (Sec. 2.1.1, Sec. 2.2) */
+enum { MGRIT_WENO5_SSPRK3 = 0, MGRIT_FO_FE = 1 };
+/* physical flux f (Sec. 2): Burgers u^2/2, or linear advection with speed 1 */
+enum { MGRIT_BURGERS = 0, MGRIT_ADVECTION = 1 };
+/* numerical flux (Sec. 2.1.2): global Lax-Friedrichs splitting
+ * f^{+/-} = (f(u) +/- alpha u)/2 reconstructed left/right-biased, or the
+ * state form of Eq. (LFflux) with the dissipative sign; alpha is the
+ * global maximum of |f'| over the stage input (split) or over all
+ * reconstructed states (state form), recomputed at every RK stage */
+enum { MGRIT_LF_SPLIT = 0, MGRIT_LF_STATE = 1 };
+enum { MGRIT_RELAX_F = 0, MGRIT_RELAX_FCF = 1 };         /* Sec. 3.2 */
+enum { MGRIT_GUESS_EQ17 = 0, MGRIT_GUESS_INJECT = 1 };   /* Eq. restriction::u */
+
+typedef struct {
+    double T;        /* final time (default 1) */
+    double L;        /* domain length (default 1) */
+    int relax;       /* MGRIT_RELAX_F / MGRIT_RELAX_FCF (default FCF) */
+    int cycle;       /* 0 = V-cycle (Algorithm 1); the only value accepted */
+    int guess;       /* MGRIT_GUESS_EQ17 (default) / MGRIT_GUESS_INJECT */
+    int numflux;     /* MGRIT_LF_SPLIT (default) / MGRIT_LF_STATE */
+    double tol;      /* stop when the level-0 residual 2-norm < tol (default 1e-10) */
+    int max_iter;    /* cycles before MGRIT_ENOTCONV (default 64, at most 254) */
+    int precision;   /* 64: every sweep in FP64 (the only value accepted) */
+} mgrit_params;
+
+typedef struct {
+    int iters;            /* completed V-cycles when the solve stopped */
+    int status;           /* same code as the return value */
+    double res_hist[256]; /* res_hist[k] = residual 2-norm after the level-0
+                             relaxation of cycle k, k = 0..iters */
+    double t_total_ms;    /* device time of the solve (CUDA events) */
+    double cell_updates;  /* cells x Phi applications executed on the GPU */
+} mgrit_stats;
+
+/* Fill *p with the defaults listed in mgrit_params. */
+void mgrit_default_params(mgrit_params *p);
+
+/*
+ * Create a solver for nx cells, nt fine steps, coarsening factor m and
+ * `levels` time levels (level l has nt/m^l steps).  Requires m >= 2,
+ * levels >= 2, nt divisible by m^(levels-1), nx >= 5 (WENO5) or nx >= 3
+ * (first order), and nx within the single-CTA slab limit of the build
+ * (MGRIT_EINVAL otherwise).  Device memory is allocated on the current
+ * device at the first solve.  Sec. 3.1 (C/F splitting, time chunks of m
+ * steps); Eq. (monolithicSystem) for nt and the time grid.
+ */
+int mgrit_create(mgrit_ctx **out, int nx, int nt, int m, int levels, int scheme, int flux);
+
+/* Replace the solver parameters (validated; MGRIT_EINVAL on bad values). */
+int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p);
+
+/*
+ * FAS MGRIT V-cycle solve (Algorithm 1) from u0_dev (nx values, cell
+ * averages of the initial condition).  The level-0 initial iterate has every
+ * C-point equal to u0.  Cycle k relaxes level 0, forms the residual
+ *   r^i = Phi_0(u^{mi-1}) - u^{mi},  i = 1..nt/m,
+ * and stops if ||r||_2 < tol; else it restricts (Eqs. restriction::rhs,
+ * restriction::u), recurses and interpolates (Eq. interpolation).
+ * Outputs (device, may be NULL): uC_out_dev = (nt/m + 1) x nx C-point
+ * states after the last relaxation; uT_out_dev = the state at T (nx).
+ * Returns MGRIT_OK, MGRIT_EDIVERGED or MGRIT_ENOTCONV (outputs written in
+ * all three cases), or an error.  Synchronises `stream` once per cycle to
+ * read the residual.  stats may be NULL.
+ */
+int mgrit_solve(mgrit_ctx *ctx, const double *u0_dev, double *uC_out_dev, double *uT_out_dev,
+                void *stream, mgrit_stats *stats);
+
+/*
+ * Run exactly `ncycles` V-cycles from the initial iterate built from u0_dev,
+ * with no stopping test and no host synchronisation (throughput
+ * measurement).  The C-point states after the last level-0 relaxation are
+ * left in the context (read them with mgrit_solve's outputs semantics via
+ * mgrit_copy_cpoints).  Asynchronous on `stream`.
+ */
+int mgrit_run_cycles(mgrit_ctx *ctx, const double *u0_dev, int ncycles, void *stream);
+
+/* Copy the C-point states after the last level-0 relaxation
+ * ((nt/m + 1) x nx) to uC_out_dev.  Asynchronous on `stream`. */
+int mgrit_copy_cpoints(mgrit_ctx *ctx, double *uC_out_dev, void *stream);
+
+/*
+ * Sequential fine time-stepping: uT_dev = Phi_0^nsteps(u0_dev), i.e. forward
+ * substitution of Eq. (monolithicSystem).  Baseline for time-to-tolerance.
+ * u0_dev and uT_dev hold nx values and may alias.  Asynchronous.
+ */
+int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *uT_dev, int nsteps,
+                      void *stream);
+
+/*
+ * Level-0 residual 2-norm of given C-point states uC_dev ((nt/m+1) x nx):
+ *   ||r||_2,  r^i = Phi_0^m(u^{m(i-1)}) - u^{mi},  i = 1..nt/m
+ * (the fine-level residual of the Schur system, Eq. schurComplement).
+ * Writes the host double *norm_out; synchronises `stream`.
+ */
+int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void *stream);
+
+/*
+ * Profiling hook: launch one named kernel of the V-cycle `reps` times on
+ * `stream` with the context's current level data, so that a caller can
+ * time it with CUDA events.  which = 0: level-`level` relaxation;
+ * 1: level-`level` residual/restriction; 2: coarsest solve;
+ * 3: level-`level` interpolation (level >= 1).  Requires a prior
+ * mgrit_solve or mgrit_run_cycles.  Asynchronous.
+ */
+int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *stream);
+
+/* Cells x Phi applications of one V-cycle (for throughput figures). */
+double mgrit_cycle_cell_updates(const mgrit_ctx *ctx);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * mgrit_create when ctx is NULL). */
+const char *mgrit_last_error(const mgrit_ctx *ctx);
+
+/* Free every device/host resource of ctx (NULL is allowed). */
+void mgrit_destroy(mgrit_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGRIT_H */

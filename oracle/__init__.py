@@ -8,5 +8,5 @@ from .api import (  # noqa: F401
     SCHEME_WENO5_SSPRK3, SCHEME_FO_FE, FLUX_BURGERS, FLUX_ADVECTION,
     NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE, RELAX_F, RELAX_FCF, GUESS_EQ17, GUESS_INJECT,
     OK, EINVAL, EDIVERGED, ENOTCONV,
-    build, weno5_left, spatial_op, step, serial, mgrit, residual, num_threads,
+    build, weno5_left, spatial_op, step, serial, mgrit, residual, num_threads, vcycles,
 )

@@ -51,6 +51,8 @@ def _load():
                                   P, P, P, P, P, P, P]
         lib.orc_residual.restype = I
         lib.orc_residual.argtypes = [I, I, I, I, I, I, D, D, P, P]
+        lib.orc_vcycles.restype = I
+        lib.orc_vcycles.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, P, P, P]
         lib.orc_num_threads.restype = I
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -138,3 +140,17 @@ def residual(uC, nt, m, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
     if st != OK:
         raise ValueError("orc_residual: invalid arguments")
     return float(out[0])
+
+
+def vcycles(u0, nt, m, levels, T, ncycles, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
+            numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, Lx=1.0):
+    """Exactly ncycles V-cycles (no stopping test); returns (uC, res_hist)."""
+    u0 = _f64(u0)
+    nx = u0.size
+    uC = np.zeros((nt // m + 1, nx))
+    hist = np.zeros(max(ncycles, 1))
+    st = _load().orc_vcycles(nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax, guess,
+                             ncycles, _ptr(u0), _ptr(uC), _ptr(hist))
+    if st != OK:
+        raise ValueError("orc_vcycles: invalid arguments")
+    return uC, hist[:ncycles]

@@ -517,6 +517,36 @@ int orc_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, int numfl
     return st;
 }
 
+/*
+ * Exactly ncycles V-cycles from the initial iterate (all C-points = u0), each
+ * recording the level-0 residual after its relaxation; no stopping test.
+ * Used to time the oracle on the same work as one GPU V-cycle.  The final
+ * level-0 C-points (after the last cycle's relaxation) go to uC_out if given.
+ */
+int orc_vcycles(int nx, int nt, int m, int levels, int scheme, int flux, int numflux,
+                double Lx, double T, int relax_kind, int guess, int ncycles,
+                const double *u0, double *uC_out, double *res_hist)
+{
+    orc_mg M;
+    int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess);
+    if (st) return st;
+    size_t rowb = sizeof(double) * (size_t)nx;
+    memcpy(row(M.g[0], nx, 0), u0, rowb);
+    for (int i = 0; i <= M.nt[0]; ++i) memcpy(row(M.u[0], nx, i), u0, rowb);
+    for (int k = 0; k < ncycles; ++k) {
+        relax(&M, 0);
+        double rk = sqrt(residual_restrict(&M, 0, 1));
+        if (res_hist) res_hist[k] = rk;
+        vcycle_from(&M, 1);
+        interpolate(&M, 0, 0);
+    }
+    if (uC_out)
+        for (int i = 0; i <= M.nt[0] / m; ++i)
+            memcpy(uC_out + (size_t)i * nx, row(M.u[0], nx, m * i), rowb);
+    mg_free(&M);
+    return ORC_OK;
+}
+
 /* ||r|| for given level-0 C-points uC ((nt/m+1)*nx): each chunk is stepped
  * m times from its C-point and compared with the next C-point. */
 int orc_residual(int nx, int nt, int m, int scheme, int flux, int numflux, double Lx,

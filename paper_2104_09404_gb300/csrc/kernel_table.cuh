@@ -1,0 +1,30 @@
+// Table of slab-kernel instances, indexed by [scheme][flux][cells-per-thread].
+#pragma once
+#include "kernels.cuh"
+
+namespace mgrit {
+
+constexpr int NCPT = 5;
+constexpr int CPT_VALUES[NCPT] = {1, 2, 4, 8, 16};
+constexpr int MAX_THREADS = 512;   // matches __launch_bounds__ of k_slab
+
+struct KernelTable {
+    const void *slab64[2][2][NCPT];
+};
+
+template <typename R, int S, int F>
+void fill_sf(const void *(&t)[2][2][NCPT])
+{
+    t[S][F][0] = (const void *)&k_slab<R, S, F, 1>;
+    t[S][F][1] = (const void *)&k_slab<R, S, F, 2>;
+    t[S][F][2] = (const void *)&k_slab<R, S, F, 4>;
+    t[S][F][3] = (const void *)&k_slab<R, S, F, 8>;
+    t[S][F][4] = (const void *)&k_slab<R, S, F, 16>;
+}
+
+// one translation unit per (precision, scheme, flux), compiled in parallel
+void fill_f64_weno_burgers(KernelTable &t);
+void fill_f64_weno_advection(KernelTable &t);
+void fill_f64_fo(KernelTable &t);
+
+}  // namespace mgrit

@@ -1,0 +1,125 @@
+// MGRIT slab kernel (Sec. 3.2, Algorithm 1): one launch-time mode selects
+//   MODE_RELAX   F- or FCF-relaxation of every C-interval of one level, plus the
+//                two extra steps the FAS restriction needs (one CTA per chunk)
+//   MODE_INTERP  ideal interpolation: injection + F-relaxation (Eq. interpolation)
+//   MODE_SEQ     sequential stepping in one CTA: the coarsest solve (Eq.
+//                coarseCorr) or the serial fine stepper
+// The residual/restriction and norm kernels live in restrict.cu.
+#pragma once
+#include "slab.cuh"
+
+namespace mgrit {
+
+enum { MODE_RELAX = 0, MODE_INTERP = 1, MODE_SEQ = 2 };
+
+template <typename T>
+__device__ __forceinline__ T *rowp(T *base, long long r, int nx)
+{
+    return base + r * (long long)nx;
+}
+
+template <typename R>
+struct SlabArgs {
+    int mode;
+    int nx, m, nC, fcf, numflux;
+    int nsteps;           // MODE_SEQ
+    R dxinv, dt, dtc;
+    // MODE_RELAX
+    const R *uC;          // C-point sources: C_j at uC + j * strideC (MODE_INTERP: coarse rows)
+    long long strideC;
+    R *newC;              // relaxed C-points, rows 0..nC (null: not stored)
+    R *phirow;            // row j+1 = Phi_l(u^{m(j+1)-1})
+    R *cstep;             // row j = Phi_{l+1}(newC_j), j < nC (null: skipped; needs newC)
+    const R *g;           // level right-hand side rows, or null (zero)
+    // MODE_SEQ: start state src, rows 1..nsteps out in rows (optional), final in out
+    // MODE_INTERP: fine rows out in rows
+    const R *src;
+    R *rows;
+    R *out;
+};
+
+template <typename R, int SCHEME, int FLUX, int CPT>
+__device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a)
+{
+    // CTA j = 0..nC.  FCF: new C_j = (Phi_l + g) applied m times from the old
+    // C_{j-1} (F- then C-relaxation of chunk j-1); F: C_j kept.  Then the
+    // F-relaxation of chunk j from the new C_j.  Chunks are independent
+    // (block-diagonal A_FF, Eq. AFF): no grid-wide synchronisation.
+    const int j = blockIdx.x;
+    const int nx = a.nx, m = a.m;
+    R u[CPT];
+    if (j == 0 || !a.fcf) {
+        S.load(u, a.uC + (long long)j * a.strideC);
+    } else {
+        S.load(u, a.uC + (long long)(j - 1) * a.strideC);
+        for (int r = 1; r <= m; ++r) {
+            S.step(u, a.dt);
+            if (a.g) S.add(u, rowp(a.g, (long long)m * (j - 1) + r, nx));
+        }
+    }
+    if (a.newC) S.store(u, rowp(a.newC, j, nx));
+    if (j == a.nC) return;
+    if (a.cstep) {
+        // coarse step of the FAS term; u is then re-read from the row this
+        // thread just stored (its own cells), which saves CPT registers
+        S.step(u, a.dtc);
+        S.store(u, rowp(a.cstep, j, nx));
+        S.load(u, rowp(a.newC, j, nx));
+    }
+    for (int r = 1; r < m; ++r) {
+        S.step(u, a.dt);
+        if (a.g) S.add(u, rowp(a.g, (long long)m * j + r, nx));
+    }
+    S.step(u, a.dt);
+    S.store(u, rowp(a.phirow, j + 1, nx));
+}
+
+template <typename R, int SCHEME, int FLUX, int CPT>
+__device__ __forceinline__ void interp_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a)
+{
+    // Eq. (interpolation): u_l^{mj} = u_{l+1}^j, u_l^{mj+r} = Phi_l(u_l^{mj+r-1}) + g_l^{mj+r}
+    const int j = blockIdx.x;
+    const int nx = a.nx, m = a.m;
+    R u[CPT];
+    S.load(u, rowp(a.uC, j, nx));
+    S.store(u, rowp(a.rows, (long long)m * j, nx));
+    for (int r = 1; r < m; ++r) {
+        S.step(u, a.dt);
+        S.add(u, rowp(a.g, (long long)m * j + r, nx));
+        S.store(u, rowp(a.rows, (long long)m * j + r, nx));
+    }
+    if (j == a.nC - 1) {   // the last C-point of the level
+        S.load(u, rowp(a.uC, a.nC, nx));
+        S.store(u, rowp(a.rows, (long long)m * a.nC, nx));
+    }
+}
+
+template <typename R, int SCHEME, int FLUX, int CPT>
+__device__ __forceinline__ void seq_march(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a)
+{
+    // u^i = Phi(u^{i-1}) + g^i, i = 1..nsteps, in one CTA
+    const int nx = a.nx;
+    R u[CPT];
+    S.load(u, a.src);
+    for (int i = 1; i <= a.nsteps; ++i) {
+        S.step(u, a.dt);
+        if (a.g) S.add(u, rowp(a.g, i, nx));
+        if (a.rows) S.store(u, rowp(a.rows, i, nx));
+    }
+    if (a.out) S.store(u, a.out);
+}
+
+template <typename R, int SCHEME, int FLUX, int CPT>
+__global__ void __launch_bounds__(512) k_slab(SlabArgs<R> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
+    if (a.mode == MODE_RELAX)
+        relax_chunk(S, a);
+    else if (a.mode == MODE_INTERP)
+        interp_chunk(S, a);
+    else
+        seq_march(S, a);
+}
+
+}  // namespace mgrit

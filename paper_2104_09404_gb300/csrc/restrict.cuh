@@ -1,0 +1,29 @@
+// Residual / FAS restriction at C-points and the deterministic norm.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mgrit {
+
+struct RestrictArgs {
+    const double *newC;    // level-l C-points after relaxation, rows 0..nC
+    const double *phirow;  // rows 1..nC: Phi_l(u^{mi-1})
+    const double *cstep;   // rows 0..nC-1: Phi_{l+1}(u^{m(i-1)}), or null (residual only)
+    const double *g;       // level-l g rows (nt_l+1) x nx, or null (level 0)
+    double *gn;            // level-(l+1) g rows, or null
+    double *un;            // level-(l+1) u rows, or null
+    double *partials;      // per-block sums of r^2, or null
+    int nx, m, nC, guess;
+};
+
+constexpr int RESTRICT_THREADS = 256;
+
+// number of blocks used for nC x nx elements (fixed per problem size, so the
+// norm's summation order is fixed)
+int restrict_blocks(int nC, int nx);
+
+cudaError_t launch_restrict(const RestrictArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_norm(const double *partials, int n, double *out, cudaStream_t s);
+cudaError_t launch_broadcast_row(const double *src, double *dst, int nx, long long nrows,
+                                 cudaStream_t s);
+
+}  // namespace mgrit

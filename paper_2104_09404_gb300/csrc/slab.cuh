@@ -1,0 +1,272 @@
+// Slab engine: one CTA owns one spatial slice u^n (nx cells) and applies the
+// time-stepper Phi of Sec. 2.2 to it, keeping u^n in registers and the
+// stage fluxes in shared memory for every step of a C-interval.
+//
+// Cell ownership is interleaved: thread t owns cells t + c*blockDim.x,
+// c = 0..CPT-1 (cells >= nx are idle).  Consecutive lanes touch
+// consecutive cells, so shared-memory traffic is conflict-free and global
+// row loads/stores are coalesced.
+//
+// Shared memory: three arrays of nx + 6 values (the split fluxes f^+ and f^-
+// with 3 periodic ghost cells on each side -- the WENO5 half-stencil -- and
+// the interface fluxes) plus NWARP_MAX values for the block max reduction of
+// the global Lax-Friedrichs alpha.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mgrit {
+
+enum { SCH_WENO5_SSPRK3 = 0, SCH_FO_FE = 1 };
+enum { FLX_BURGERS = 0, FLX_ADVECTION = 1 };
+enum { NF_SPLIT = 0, NF_STATE = 1 };
+
+constexpr int GHOST = 3;
+constexpr int NWARP_MAX = 32;
+
+// Physical flux (Sec. 2, Eq. burgers) and |eigenvalue| of its Jacobian.
+template <int FLUX, typename R>
+__device__ __forceinline__ R phys_flux(R u)
+{
+    return FLUX == FLX_BURGERS ? R(0.5) * u * u : u;
+}
+template <int FLUX, typename R>
+__device__ __forceinline__ R phys_speed(R u)
+{
+    return FLUX == FLX_BURGERS ? fabs(u) : R(1);
+}
+
+// WENO5-JS value left of the interface i+1/2 from (a..e) = q_{i-2..i+2}
+// (Sec. 2.1.1, k = 2).  Candidate values P_r (times 6), smoothness
+// indicators in the expanded form 13/12 (2nd difference)^2 + 1/4 (1st
+// difference)^2 (equal to the quadratic forms B_r of the paper), weights
+// alpha_r = d_r / (eps + beta_r)^2 with d = (1, 6, 3)/10 for the stencils
+// ending at i, i+1, i+2.  The weight normalisation is done over a common
+// denominator: multiplying numerator and denominator of
+// sum_r alpha_r p_r / sum_r alpha_r by prod_r (eps + beta_r)^2 leaves a
+// single division per reconstruction (the 1/10 of d_r cancels).
+template <typename R>
+__device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
+{
+    const R eps = R(1e-6);
+    const R k13 = R(13.0 / 12.0);
+    const R P0 = R(2) * a - R(7) * b + R(11) * c;   // stencil {i-2, i-1, i}
+    const R P1 = -b + R(5) * c + R(2) * d;          // stencil {i-1, i, i+1}
+    const R P2 = R(2) * c + R(5) * d - e;           // stencil {i, i+1, i+2}
+    const R x0 = a - R(2) * b + c, y0 = a - R(4) * b + R(3) * c;
+    const R x1 = b - R(2) * c + d, y1 = b - d;
+    const R x2 = c - R(2) * d + e, y2 = R(3) * c - R(4) * d + e;
+    R s0 = eps + k13 * x0 * x0 + R(0.25) * y0 * y0;
+    R s1 = eps + k13 * x1 * x1 + R(0.25) * y1 * y1;
+    R s2 = eps + k13 * x2 * x2 + R(0.25) * y2 * y2;
+    s0 *= s0;
+    s1 *= s1;
+    s2 *= s2;
+    const R t0 = s1 * s2;              // d_0 = 1  (x 1/10)
+    const R t1 = R(6) * (s0 * s2);     // d_1 = 6
+    const R t2 = R(3) * (s0 * s1);     // d_2 = 3
+    return (P0 * t0 + P1 * t1 + P2 * t2) / (R(6) * (t0 + t1 + t2));
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide max; every thread returns the result.  Contains one barrier.
+template <typename R>
+__device__ __forceinline__ R block_max(R v, R *red)
+{
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    R r = red[0];
+    for (int k = 1; k < nw; ++k) r = fmax(r, red[k]);
+    return r;
+}
+
+template <typename R, int SCHEME, int FLUX, int CPT>
+struct Slab {
+    R *qa;        // nx + 6: f^+ (split form) or the stage state (state form)
+    R *qb;        // nx + 6: f^- (split form)
+    R *qf;        // nx + 1: interface fluxes, qf[i+1] = F_{i+1/2}, qf[0] = F_{-1/2}
+    R *red;       // NWARP_MAX
+    int nx;
+    int numflux;
+    R dxinv;
+
+    __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
+        : nx(nx_), numflux(numflux_), dxinv(dxinv_)
+    {
+        qa = reinterpret_cast<R *>(smem);
+        qb = qa + (nx + 2 * GHOST);
+        qf = qb + (nx + 2 * GHOST);
+        red = qf + (nx + 2 * GHOST);
+    }
+
+    __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
+
+    // store cell i (and its periodic ghost copy) into slot i + GHOST
+    __device__ __forceinline__ void put(R *arr, int i, R v) const
+    {
+        arr[i + GHOST] = v;
+        if (i < GHOST) arr[i + GHOST + nx] = v;
+        if (i >= nx - GHOST) arr[i + GHOST - nx] = v;
+    }
+
+    // left-biased reconstruction at i+1/2 from slots around s = i + GHOST
+    __device__ __forceinline__ R rec_minus(const R *q, int s) const
+    {
+        if (SCHEME == SCH_FO_FE) return q[s];
+        return weno5_left<R>(q[s - 2], q[s - 1], q[s], q[s + 1], q[s + 2]);
+    }
+    // right-biased reconstruction at i+1/2: the mirrored stencil
+    __device__ __forceinline__ R rec_plus(const R *q, int s) const
+    {
+        if (SCHEME == SCH_FO_FE) return q[s + 1];
+        return weno5_left<R>(q[s + 3], q[s + 2], q[s + 1], q[s], q[s - 1]);
+    }
+
+    __device__ __forceinline__ void put_flux(int i, R F) const
+    {
+        qf[i + 1] = F;
+        if (i == nx - 1) qf[0] = F;
+    }
+
+    // Interface fluxes F_{i+1/2} of the stage input w into qf (Sec. 2.1.2).
+    // Ends with a barrier after which qf is complete.
+    __device__ __forceinline__ void fluxes(const R (&w)[CPT])
+    {
+        __syncthreads();   // previous readers of qa/qb/qf/red are done
+        if (numflux == NF_SPLIT) {
+            R alpha = R(1);
+            if (FLUX == FLX_BURGERS) {
+                R v = R(0);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (cell(c) < nx) v = fmax(v, phys_speed<FLUX>(w[c]));
+                alpha = block_max(v, red);
+            }
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) {
+                    const R f = phys_flux<FLUX>(w[c]);
+                    put(qa, i, R(0.5) * (f + alpha * w[c]));
+                    put(qb, i, R(0.5) * (f - alpha * w[c]));
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) put_flux(i, rec_minus(qa, i + GHOST) + rec_plus(qb, i + GHOST));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) put(qa, i, w[c]);
+            }
+            __syncthreads();
+            // u^-_{i+1/2} parked in qb[i], u^+_{i+1/2} in qf[i+1]; each thread
+            // reads back only its own slots, then overwrites qf[i+1] with F
+            R v = R(0);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) {
+                    const R um = rec_minus(qa, i + GHOST);
+                    const R up = rec_plus(qa, i + GHOST);
+                    qb[i] = um;
+                    qf[i + 1] = up;
+                    v = fmax(v, fmax(phys_speed<FLUX>(um), phys_speed<FLUX>(up)));
+                }
+            }
+            R alpha = R(1);
+            if (FLUX == FLX_BURGERS) alpha = block_max(v, red);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) {
+                    const R um = qb[i], up = qf[i + 1];
+                    put_flux(i, R(0.5) * (phys_flux<FLUX>(up) + phys_flux<FLUX>(um)) -
+                                    R(0.5) * alpha * (up - um));
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // A_i(w) = -(F_{i+1/2} - F_{i-1/2}) / dx for owned slot c (Eq. spaceDisc);
+    // valid after fluxes().
+    __device__ __forceinline__ R A(int c) const
+    {
+        const int i = cell(c);
+        return -(qf[i + 1] - qf[i]) * dxinv;
+    }
+
+    // u <- Phi(u) with step dt: SSPRK3 (Eq. SSPRK3) or forward Euler (Eq. SSPRK1)
+    __device__ __forceinline__ void step(R (&u)[CPT], R dt)
+    {
+        if (SCHEME == SCH_FO_FE) {
+            fluxes(u);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c)
+                if (cell(c) < nx) u[c] = u[c] + dt * A(c);
+            return;
+        }
+        R w[CPT];
+        fluxes(u);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? u[c] + dt * A(c) : R(0);
+        fluxes(w);
+        const R q = R(0.25) * dt;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (cell(c) < nx) w[c] = R(0.75) * u[c] + R(0.25) * w[c] + q * A(c);
+        fluxes(w);
+        const R t = R(2.0 / 3.0) * dt;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (cell(c) < nx) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * w[c] + t * A(c);
+    }
+
+    __device__ __forceinline__ void load(R (&u)[CPT], const R *__restrict__ row) const
+    {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int i = cell(c);
+            u[c] = (i < nx) ? row[i] : R(0);
+        }
+    }
+    __device__ __forceinline__ void store(const R (&u)[CPT], R *__restrict__ row) const
+    {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int i = cell(c);
+            if (i < nx) row[i] = u[c];
+        }
+    }
+    __device__ __forceinline__ void add(R (&u)[CPT], const R *__restrict__ row) const
+    {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int i = cell(c);
+            if (i < nx) u[c] += row[i];
+        }
+    }
+};
+
+// shared-memory bytes of one slab
+template <typename R>
+inline size_t slab_smem_bytes(int nx)
+{
+    return sizeof(R) * (3 * (size_t)(nx + 2 * GHOST) + NWARP_MAX);
+}
+
+}  // namespace mgrit

@@ -1,0 +1,176 @@
+"""Thin ctypes binding of libmgrit.so (C ABI declared in include/mgrit.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  The module-level functions carry the C names; ``Solver`` is a
+small convenience wrapper taking torch CUDA tensors (torch supplies device
+memory and streams).  If libmgrit.so is missing, loading raises: there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmgrit.so")
+
+OK, EINVAL, ECUDA, ENOMEM, EDIVERGED, ENOTCONV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+WENO5_SSPRK3, FO_FE = 0, 1
+BURGERS, ADVECTION = 0, 1
+LF_SPLIT, LF_STATE = 0, 1
+RELAX_F, RELAX_FCF = 0, 1
+GUESS_EQ17, GUESS_INJECT = 0, 1
+STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM",
+                EDIVERGED: "EDIVERGED", ENOTCONV: "ENOTCONV", ETIMEOUT: "ETIMEOUT"}
+
+
+class mgrit_params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_double), ("L", ctypes.c_double), ("relax", ctypes.c_int),
+                ("cycle", ctypes.c_int), ("guess", ctypes.c_int), ("numflux", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class mgrit_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("res_hist", ctypes.c_double * 256), ("t_total_ms", ctypes.c_double),
+                ("cell_updates", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGS = {
+    "mgrit_default_params": (None, [ctypes.POINTER(mgrit_params)]),
+    "mgrit_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _I]),
+    "mgrit_set_params": (_I, [_P, ctypes.POINTER(mgrit_params)]),
+    "mgrit_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(mgrit_stats)]),
+    "mgrit_run_cycles": (_I, [_P, _P, _I, _P]),
+    "mgrit_copy_cpoints": (_I, [_P, _P, _P]),
+    "mgrit_serial_step": (_I, [_P, _P, _P, _I, _P]),
+    "mgrit_residual": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
+    "mgrit_launch_kernel": (_I, [_P, _I, _I, _I, _P]),
+    "mgrit_cycle_cell_updates": (_D, [_P]),
+    "mgrit_last_error": (ctypes.c_char_p, [_P]),
+    "mgrit_destroy": (None, [_P]),
+}
+
+
+def load():
+    """Load libmgrit.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libmgrit.so not built: run __graft_entry__.build() "
+                          "(paper_2104_09404_gb300/build.py); there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    # module-level access to the C entry points under their own names
+    if name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+class MGRITError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Solver:
+    """MGRIT solver for one problem size (wraps one mgrit_ctx)."""
+
+    def __init__(self, nx, nt, m, levels, scheme=WENO5_SSPRK3, flux=BURGERS, **params):
+        lib = load()
+        h = _P()
+        st = lib.mgrit_create(ctypes.byref(h), nx, nt, m, levels, scheme, flux)
+        if st != OK:
+            raise MGRITError(st, lib.mgrit_last_error(None).decode())
+        self._h = h
+        self.nx, self.nt, self.m, self.levels = nx, nt, m, levels
+        self.scheme, self.flux = scheme, flux
+        self.params = mgrit_params()
+        lib.mgrit_default_params(ctypes.byref(self.params))
+        if params:
+            self.set_params(**params)
+
+    def _check(self, st, allowed=(OK,)):
+        if st not in allowed:
+            raise MGRITError(st, load().mgrit_last_error(self._h).decode())
+        return st
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if not hasattr(self.params, k):
+                raise KeyError(k)
+            setattr(self.params, k, v)
+        self._check(load().mgrit_set_params(self._h, ctypes.byref(self.params)))
+
+    def solve(self, u0, want_uC=True, stream=None):
+        """Returns (status, uT, uC or None, stats); status is OK, EDIVERGED or ENOTCONV."""
+        import torch
+        nC = self.nt // self.m
+        uT = torch.empty(self.nx, dtype=torch.float64, device=u0.device)
+        uC = torch.empty((nC + 1, self.nx), dtype=torch.float64, device=u0.device) if want_uC else None
+        stats = mgrit_stats()
+        st = load().mgrit_solve(self._h, _ptr(u0), _ptr(uC), _ptr(uT), _stream_handle(stream),
+                                ctypes.byref(stats))
+        self._check(st, (OK, EDIVERGED, ENOTCONV))
+        return st, uT, uC, stats
+
+    def run_cycles(self, u0, ncycles, stream=None):
+        self._check(load().mgrit_run_cycles(self._h, _ptr(u0), ncycles, _stream_handle(stream)))
+
+    def cpoints(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.nt // self.m + 1, self.nx), dtype=torch.float64, device="cuda")
+        self._check(load().mgrit_copy_cpoints(self._h, _ptr(out), _stream_handle(stream)))
+        return out
+
+    def serial_step(self, u0, nsteps, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(u0)
+        self._check(load().mgrit_serial_step(self._h, _ptr(u0), _ptr(out), nsteps,
+                                             _stream_handle(stream)))
+        return out
+
+    def residual(self, uC, stream=None):
+        v = ctypes.c_double(0.0)
+        self._check(load().mgrit_residual(self._h, _ptr(uC), ctypes.byref(v), _stream_handle(stream)))
+        return v.value
+
+    def launch_kernel(self, which, level, reps=1, stream=None):
+        self._check(load().mgrit_launch_kernel(self._h, which, level, reps, _stream_handle(stream)))
+
+    def cycle_cell_updates(self):
+        return load().mgrit_cycle_cell_updates(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mgrit_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,103 @@
+"""The C-ABI library loads and exports every symbol include/mgrit.h declares,
+and its host-side argument checks work without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mgrit_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_09404_gb300 import build as B, mgrit as M
+    if not os.path.exists(M.LIB_PATH):
+        B.build()
+    return M.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("mgrit_create", "mgrit_set_params", "mgrit_solve", "mgrit_serial_step",
+                     "mgrit_residual", "mgrit_last_error", "mgrit_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_2104_09404_gb300 import mgrit as M
+    assert set(declared_symbols()) <= set(M._SIGS)
+
+
+def test_default_params(lib):
+    from paper_2104_09404_gb300 import mgrit as M
+    p = M.mgrit_params()
+    lib.mgrit_default_params(ctypes.byref(p))
+    assert (p.T, p.L, p.relax, p.cycle, p.guess, p.numflux) == (1.0, 1.0, 1, 0, 0, 0)
+    assert p.tol == 1e-10 and p.max_iter == 64 and p.precision == 64
+
+
+@pytest.mark.parametrize("args,frag", [
+    ((128, 256, 1, 2, 0, 0), "m must"),
+    ((128, 256, 4, 1, 0, 0), "levels"),
+    ((128, 250, 4, 2, 0, 0), "divisible"),
+    ((128, 16, 4, 4, 0, 0), "divisible"),
+    ((4, 256, 4, 2, 0, 0), "nx too small"),
+    ((2, 256, 4, 2, 1, 0), "nx too small"),
+    ((128, 256, 4, 2, 7, 0), "scheme"),
+    ((128, 256, 4, 2, 0, 9), "flux"),
+    ((1 << 15, 256, 4, 2, 0, 0), "slab limit"),
+])
+def test_create_rejects_bad_arguments(lib, args, frag):
+    from paper_2104_09404_gb300 import mgrit as M
+    h = ctypes.c_void_p()
+    st = lib.mgrit_create(ctypes.byref(h), *args)
+    assert st == M.EINVAL
+    assert not h.value
+    assert frag in lib.mgrit_last_error(None).decode()
+
+
+def test_create_set_params_destroy_without_gpu(lib):
+    from paper_2104_09404_gb300 import mgrit as M
+    h = ctypes.c_void_p()
+    assert lib.mgrit_create(ctypes.byref(h), 100, 64, 4, 3, 0, 0) == M.OK
+    p = M.mgrit_params()
+    lib.mgrit_default_params(ctypes.byref(p))
+    p.T = 0.5
+    assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK
+    for field, bad in (("relax", 3), ("cycle", 1), ("guess", 2), ("numflux", 5),
+                       ("tol", -1.0), ("max_iter", 1000), ("precision", 16), ("T", 0.0)):
+        q = M.mgrit_params.from_buffer_copy(p)
+        setattr(q, field, bad)
+        assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field
+    # 3 levels, m = 4: (2*4 + 1) * 16 + (2*4 + 1 + 3) * 4 + 4 steps per cycle at FCF
+    assert lib.mgrit_cycle_cell_updates(h) == 100 * ((2 * 4 + 1) * 16 + (2 * 4 + 1 + 3) * 4 + 4)
+    lib.mgrit_destroy(h)
+    lib.mgrit_destroy(None)
+
+
+def test_null_arguments_are_rejected(lib):
+    from paper_2104_09404_gb300 import mgrit as M
+    assert lib.mgrit_create(None, 100, 64, 4, 3, 0, 0) == M.EINVAL
+    assert lib.mgrit_solve(None, None, None, None, None, None) == M.EINVAL
+    assert lib.mgrit_serial_step(None, None, None, 1, None) == M.EINVAL
+    h = ctypes.c_void_p()
+    assert lib.mgrit_create(ctypes.byref(h), 100, 64, 4, 3, 0, 0) == M.OK
+    assert lib.mgrit_solve(h, None, None, None, None, None) == M.EINVAL
+    assert lib.mgrit_copy_cpoints(h, None, None) == M.EINVAL
+    lib.mgrit_destroy(h)

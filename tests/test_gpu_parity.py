@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar (FP64): relative max-norm difference <= 1e-11 and an identical MGRIT
+iteration count / outcome; residual histories agree to rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2104_09404_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_09404_gb300 import build as B, mgrit
+    B.build()
+    mgrit.load()
+    return mgrit
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def relerr(got, ref):
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+# ---------------------------------------------------------------- stepping ---
+
+SERIAL_CASES = [
+    # nx, scheme, flux, numflux, nsteps, T
+    (128, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_LF_SPLIT, 256, 0.5),
+    (100, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_LF_SPLIT, 50, 0.1),
+    (1000, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION, O.NUMFLUX_LF_SPLIT, 40, 0.05),
+    (5, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_LF_SPLIT, 10, 0.01),
+    (777, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_LF_STATE, 30, 0.05),
+    (64, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION, O.NUMFLUX_LF_STATE, 30, 0.3),
+    (3, O.SCHEME_FO_FE, O.FLUX_BURGERS, O.NUMFLUX_LF_SPLIT, 20, 0.01),
+    (257, O.SCHEME_FO_FE, O.FLUX_ADVECTION, O.NUMFLUX_LF_SPLIT, 100, 0.2),
+    (300, O.SCHEME_FO_FE, O.FLUX_BURGERS, O.NUMFLUX_LF_STATE, 100, 0.2),
+    (4096, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_LF_SPLIT, 64, 64 / 16384),
+    (8192, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_LF_SPLIT, 8, 8 / 32768),
+    (6000, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION, O.NUMFLUX_LF_SPLIT, 8, 8 / 24000),
+]
+
+
+@pytest.mark.parametrize("nx,scheme,flux,numflux,nsteps,T", SERIAL_CASES)
+def test_serial_stepping_parity(M, nx, scheme, flux, numflux, nsteps, T):
+    u0 = inputs.fourier_ic(nx, seed=nx)
+    # dt = T / nt comes from the context: nt = nsteps, two levels with m = 2
+    s = M.Solver(nx, nsteps, 2, 2, scheme, flux, T=T, numflux=numflux)
+    out = s.serial_step(dev(u0), nsteps)
+    torch.cuda.synchronize()
+    ref = O.serial(u0, T / nsteps, nsteps, scheme, flux, numflux)
+    assert relerr(out.cpu().numpy(), ref) <= RTOL
+
+
+def test_serial_in_place(M):
+    nx, n, T = 200, 16, 0.02
+    u0 = inputs.sine_ic(nx)
+    s = M.Solver(nx, n, 2, 2, T=T)
+    u = dev(u0)
+    s.serial_step(u, n, out=u)
+    torch.cuda.synchronize()
+    assert relerr(u.cpu().numpy(), O.serial(u0, T / n, n)) <= RTOL
+
+
+# ------------------------------------------------------------------- MGRIT ---
+
+def near_tol(hist, tol):
+    return bool(np.any(np.abs(np.asarray(hist) - tol) <= 1e-3 * tol))
+
+
+MGRIT_CASES = [
+    # name, nx, nt, m, L, T, kw (scheme, flux, numflux, relax, guess), seed (None = sine)
+    ("c1-as-stated", 128, 256, 4, 2, 0.5, {}, None),
+    ("c1-cfl-capped", 128, 256, 4, 2, 0.25, {}, None),
+    ("c1-F", 128, 256, 4, 2, 0.25, dict(relax=O.RELAX_F), None),
+    ("multilevel-L3", 64, 256, 2, 3, 0.2, {}, None),
+    ("multilevel-L4-F", 64, 256, 2, 4, 0.2, dict(relax=O.RELAX_F), None),
+    ("inject", 64, 256, 2, 3, 0.2, dict(guess=O.GUESS_INJECT), None),
+    ("ragged-advection", 100, 128, 4, 3, 0.1, dict(flux=O.FLUX_ADVECTION), 3),
+    ("state-form", 64, 128, 2, 3, 0.15, dict(numflux=O.NUMFLUX_LF_STATE), 4),
+    ("fo-fe", 96, 256, 4, 2, 0.1, dict(scheme=O.SCHEME_FO_FE), 5),
+    ("fo-fe-advection-L3", 80, 256, 4, 3, 0.05, dict(scheme=O.SCHEME_FO_FE, flux=O.FLUX_ADVECTION), 6),
+    ("fourier-256", 256, 1024, 4, 3, 0.05, {}, 7),
+    ("m8-coarsest-1-step", 32, 64, 8, 3, 0.05, {}, 8),
+    ("nx5", 5, 32, 2, 3, 0.02, {}, 9),
+]
+
+
+def run_pair(M, nx, nt, m, L, T, kw, seed, max_iter=40, tol=1e-10):
+    u0 = inputs.sine_ic(nx) if seed is None else inputs.fourier_ic(nx, seed=seed)
+    scheme = kw.get("scheme", O.SCHEME_WENO5_SSPRK3)
+    flux = kw.get("flux", O.FLUX_BURGERS)
+    params = dict(T=T, tol=tol, max_iter=max_iter, numflux=kw.get("numflux", 0),
+                  relax=kw.get("relax", O.RELAX_FCF), guess=kw.get("guess", O.GUESS_EQ17))
+    s = M.Solver(nx, nt, m, L, scheme, flux, **params)
+    st, uT, uC, stats = s.solve(dev(u0))
+    torch.cuda.synchronize()
+    ref = O.mgrit(u0, nt, m, L, T, scheme=scheme, flux=flux, numflux=params["numflux"],
+                  relax=params["relax"], guess=params["guess"], tol=tol, max_iter=max_iter)
+    return st, uT.cpu().numpy(), uC.cpu().numpy(), stats, ref, s, u0
+
+
+@pytest.mark.parametrize("name,nx,nt,m,L,T,kw,seed", MGRIT_CASES, ids=[c[0] for c in MGRIT_CASES])
+def test_mgrit_parity(M, name, nx, nt, m, L, T, kw, seed):
+    st, uT, uC, stats, ref, _, _ = run_pair(M, nx, nt, m, L, T, kw, seed)
+    hist = np.array(stats.res_hist[: stats.iters + 1])
+    if near_tol(ref["res_hist"], 1e-10):
+        pytest.skip("oracle residual within 1e-3 of tol: iteration count not decidable")
+    assert st == ref["status"], (st, ref["status"], hist, ref["res_hist"])
+    assert stats.iters == ref["iters"]
+    finite = np.isfinite(ref["res_hist"])
+    np.testing.assert_allclose(hist[finite], ref["res_hist"][finite], rtol=1e-8, atol=1e-13)
+    if np.all(np.isfinite(ref["uC"])):
+        assert relerr(uC, ref["uC"]) <= RTOL
+        assert relerr(uT, ref["uT"]) <= RTOL
+
+
+def test_c1_as_stated_diverges_like_the_oracle(M):
+    st, _, _, stats, ref, _, _ = run_pair(M, 128, 256, 4, 2, 0.5, {}, None)
+    assert ref["status"] == O.EDIVERGED
+    assert st == M.EDIVERGED and stats.iters == ref["iters"]
+
+
+def test_converged_mgrit_matches_gpu_serial(M):
+    nx, nt, m, L, T = 128, 256, 4, 2, 0.25
+    st, uT, uC, stats, ref, s, u0 = run_pair(M, nx, nt, m, L, T, {}, None)
+    assert st == M.OK
+    ser = s.serial_step(dev(u0), nt).cpu().numpy()
+    assert np.abs(uT - ser).max() < 1e-8
+
+
+def test_run_cycles_matches_solve(M):
+    nx, nt, m, L, T = 64, 256, 2, 3, 0.2
+    u0 = dev(inputs.fourier_ic(nx, seed=11))
+    a = M.Solver(nx, nt, m, L, T=T, tol=0.0, max_iter=2)
+    st, _, uC, _ = a.solve(u0)
+    assert st == M.ENOTCONV
+    b = M.Solver(nx, nt, m, L, T=T)
+    b.run_cycles(u0, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(b.cpoints(), uC)
+
+
+def test_solve_is_deterministic(M):
+    nx, nt, m, L, T = 256, 1024, 4, 3, 0.05
+    u0 = dev(inputs.fourier_ic(nx, seed=12))
+    s = M.Solver(nx, nt, m, L, T=T)
+    _, uT1, uC1, st1 = s.solve(u0)
+    _, uT2, uC2, st2 = s.solve(u0)
+    assert torch.equal(uC1, uC2) and torch.equal(uT1, uT2)
+    assert list(st1.res_hist[: st1.iters + 1]) == list(st2.res_hist[: st2.iters + 1])
+
+
+def test_nan_input_reports_divergence(M):
+    s = M.Solver(64, 64, 4, 2, T=0.1)
+    st, _, _, stats = s.solve(torch.full((64,), float("nan"), dtype=torch.float64, device="cuda"))
+    assert st == M.EDIVERGED and stats.iters == 0
+
+
+# ---------------------------------------------------------------- residual ---
+
+@pytest.mark.parametrize("nx,nt,m", [(64, 64, 4), (130, 96, 8), (2048, 64, 4)])
+def test_residual_parity(M, nx, nt, m):
+    T = 0.02
+    u0 = inputs.fourier_ic(nx, seed=nx)
+    traj = O.serial(u0, T / nt, nt, store_all=True)
+    uC = traj[::m].copy()
+    s = M.Solver(nx, nt, m, 2, T=T)
+    assert s.residual(dev(uC)) < 1e-13
+    rng = np.random.default_rng(0)
+    uC[1:] += 1e-4 * rng.standard_normal(uC[1:].shape)
+    got = s.residual(dev(uC))
+    ref = O.residual(uC, nt, m, T)
+    assert got == pytest.approx(ref, rel=1e-10)
+
+
+# ------------------------------------------------- full size (bench config) ---
+
+C2 = dict(nx=4096, nt=16384, m=4, L=6, T=1.0)
+
+
+def test_full_size_first_relaxation_and_residual(M):
+    # cycle 0 starts from C-points all equal to u0, so after FCF every
+    # C-point j >= 1 is Phi^m(u0) and r^1 = 0, r^i = Phi^2m(u0) - Phi^m(u0)
+    # for i >= 2: both computable by the oracle in a few steps
+    nx, nt, m, L, T = C2["nx"], C2["nt"], C2["m"], C2["L"], C2["T"]
+    u0 = inputs.fourier_ic(nx, seed=0)
+    s = M.Solver(nx, nt, m, L, T=T, max_iter=0)
+    st, uT, uC, stats = s.solve(dev(u0))
+    assert st in (M.ENOTCONV, M.EDIVERGED)
+    uC = uC.cpu().numpy()
+    dt = T / nt
+    a = O.serial(u0, dt, m)
+    b = O.serial(a, dt, m)
+    np.testing.assert_array_equal(uC[0], u0)
+    rows = np.r_[1, 2, 777, nt // m // 2, nt // m]
+    for j in rows:
+        assert relerr(uC[j], a) <= RTOL
+    nC = nt // m
+    ref_r0 = np.sqrt(nC - 1) * np.linalg.norm(b - a)
+    assert stats.res_hist[0] == pytest.approx(ref_r0, rel=1e-9)
+
+
+def test_full_size_serial_prefix(M):
+    nx, nt, T = C2["nx"], C2["nt"], C2["T"]
+    u0 = inputs.fourier_ic(nx, seed=0)
+    n = 512
+    s = M.Solver(nx, nt, C2["m"], C2["L"], T=T)
+    out = s.serial_step(dev(u0), n).cpu().numpy()
+    assert relerr(out, O.serial(u0, T / nt, n)) <= RTOL
+
+
+def test_full_size_cycles_conserve_mass(M):
+    # a CFL-stable variant of the bench workload: every iterate keeps the
+    # cell sum of u0 at every C-point (periodic flux differences telescope)
+    nx, nt, m = C2["nx"], C2["nt"], C2["m"]
+    u0 = inputs.fourier_ic(nx, seed=1)
+    s = M.Solver(nx, nt, m, 2, T=0.25, tol=0.0, max_iter=2)
+    st, uT, uC, stats = s.solve(dev(u0))
+    uC = uC.cpu().numpy()
+    assert np.all(np.isfinite(uC))
+    assert np.abs(uC.sum(axis=1) - u0.sum()).max() < 1e-9
