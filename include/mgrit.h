@@ -148,7 +148,8 @@ int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void 
  * time it with CUDA events.  which = 0: level-`level` relaxation;
  * 1: level-`level` residual/restriction; 2: coarsest solve;
  * 3: level-`level` interpolation (level >= 1).  Requires a prior
- * mgrit_solve or mgrit_run_cycles.  Asynchronous.
+ * mgrit_solve or mgrit_run_cycles (ncycles = 0 is enough: it allocates the
+ * workspaces and loads the initial iterate).  Asynchronous.
  */
 int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *stream);
 

@@ -46,7 +46,8 @@ struct mgrit_ctx {
     double dt_l[MAXLEV];
     Launch ln;
     bool alloc;
-    bool have_state;
+    bool prepared;     // workspaces, graphs and an initial iterate exist
+    bool have_state;   // a level-0 relaxation has produced newC[0]
     int device;
     double *u[MAXLEV], *g[MAXLEV];
     double *newC[MAXLEV], *phirow[MAXLEV], *cstep[MAXLEV];
@@ -403,7 +404,9 @@ static int prepare(mgrit_ctx *ctx, const double *u0_dev, cudaStream_t s)
     int st;
     if ((st = ensure_alloc(ctx))) return st;
     if ((st = ensure_graphs(ctx))) return st;
-    return init_iterate(ctx, u0_dev, s);
+    if ((st = init_iterate(ctx, u0_dev, s))) return st;
+    ctx->prepared = true;
+    return MGRIT_OK;
 }
 
 extern "C" int mgrit_solve(mgrit_ctx *ctx, const double *u0_dev, double *uC_out_dev,
@@ -531,7 +534,7 @@ extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm
 extern "C" int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *stream)
 {
     if (!ctx) return MGRIT_EINVAL;
-    if (!ctx->have_state) return fail(ctx, MGRIT_EINVAL, "no solve has run on this context");
+    if (!ctx->prepared) return fail(ctx, MGRIT_EINVAL, "no solve has run on this context");
     if (reps < 0) return fail(ctx, MGRIT_EINVAL, "reps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     const int L = ctx->L;

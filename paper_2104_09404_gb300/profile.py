@@ -1,0 +1,42 @@
+"""Launch one kernel of the V-cycle for profiling (e.g. under ncu).
+
+    python -m paper_2104_09404_gb300.profile --case c2 --kernel relax --level 0 --reps 1
+
+Cases: c2 = nx 4096, nt 16384, m 4, 6 levels, T 1 (the benchmark workload);
+small = nx 4096, nt 2048, m 4, 4 levels, T 0.125 (same kernel shape, 513
+CTAs).  The context is prepared with zero cycles (workspaces allocated,
+level-0 C-points = u0), then the chosen kernel is launched `reps` times; it
+is the first launch of that kernel in the process.
+"""
+import argparse
+import sys
+
+CASES = {
+    "c2": dict(nx=4096, nt=16384, m=4, levels=6, T=1.0),
+    "small": dict(nx=4096, nt=2048, m=4, levels=4, T=0.125),
+    "c1": dict(nx=128, nt=256, m=4, levels=2, T=0.5),
+}
+KERNELS = {"relax": 0, "restrict": 1, "coarsest": 2, "interp": 3}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--case", default="c2", choices=sorted(CASES))
+    p.add_argument("--kernel", default="relax", choices=sorted(KERNELS))
+    p.add_argument("--level", type=int, default=0)
+    p.add_argument("--reps", type=int, default=1)
+    a = p.parse_args(argv)
+    import torch
+    from . import inputs, mgrit
+    c = CASES[a.case]
+    s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"])
+    u0 = torch.as_tensor(inputs.fourier_ic(c["nx"], seed=0), device="cuda")
+    s.run_cycles(u0, 0)
+    s.launch_kernel(KERNELS[a.kernel], a.level, a.reps)
+    torch.cuda.synchronize()
+    print("launched %s level %d x%d on case %s" % (a.kernel, a.level, a.reps, a.case))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
