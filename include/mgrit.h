@@ -153,6 +153,38 @@ int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void 
  */
 int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *stream);
 
+/*
+ * Allocation-free variant of mgrit_residual (the paper has no counterpart:
+ * this is a deployment convenience).  Some callers cannot call cudaMalloc:
+ * code that runs while the application owns all device memory through its
+ * own pool or fixed budget (a plugin inside a host framework), code that must
+ * not trigger the allocator's implicit device synchronisation inside a
+ * latency-critical loop, and code that only has a stream and pointers handed
+ * to it.  This entry point needs no context and allocates nothing: the Phi^m
+ * rows and norm partials it needs live in one static device array of
+ * MGRIT_STATIC_SCRATCH_DOUBLES + 2048 doubles (16 MiB + 16 KiB), which every
+ * GPU that loads the library holds until the process exits.
+ *
+ *   uC_dev   (nt/m + 1) x nx C-point states (device, caller-owned, read only)
+ *   norm_dev one device double that receives ||r||_2, with r as in
+ *            mgrit_residual (caller-owned output)
+ *   the other arguments as in mgrit_create / mgrit_params (dx = L/nx,
+ *   dt = T/nt).
+ *
+ * Returns MGRIT_EINVAL for bad arguments or when (nt/m + 1) * nx exceeds
+ * MGRIT_STATIC_SCRATCH_DOUBLES (nothing is launched), MGRIT_ECUDA if a
+ * launch fails.  Asynchronous on `stream`; the caller reads norm_dev after
+ * synchronising.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture.  Every call shares the one array, so calls
+ * that overlap on the GPU (other streams, other host threads) race; each
+ * call overwrites every scratch value it reads before reading it, so no
+ * state carries over between calls.
+ */
+#define MGRIT_STATIC_SCRATCH_DOUBLES (1 << 21)
+int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numflux, double T,
+                          double L, const double *uC_dev, double *norm_dev, void *stream);
+
 /* Cells x Phi applications of one V-cycle (for throughput figures). */
 double mgrit_cycle_cell_updates(const mgrit_ctx *ctx);
 

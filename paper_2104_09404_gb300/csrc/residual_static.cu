@@ -1,0 +1,131 @@
+// mgrit_residual_static: the level-0 residual norm without any device
+// allocation, for callers that cannot call cudaMalloc.
+//
+// It runs the same kernels as mgrit_residual (k_slab in relaxation mode for
+// the Phi^m rows, k_restrict for the squared residual partials, k_norm for
+// the sum), but their scratch lives in one file-scope device array instead
+// of context buffers.  The array is part of this library's device image, so
+// every GPU that loads the library holds it until the process exits.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/mgrit.h"
+#include "kernel_table.cuh"
+#include "restrict.cuh"
+
+using namespace mgrit;
+
+namespace {
+
+// Phi^m rows: (nt/m + 1) x nx doubles at most; then the norm partials.
+constexpr size_t ROWS_MAX = (size_t)MGRIT_STATIC_SCRATCH_DOUBLES;
+constexpr size_t PARTIALS_MAX = 2048;
+
+static __device__ __align__(256) double g_static_scratch[ROWS_MAX + PARTIALS_MAX];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_setup_mutex;
+double *g_scratch_addr[MAX_DEVICES];   // device address of g_static_scratch, per device
+
+// Host code may not use &g_static_scratch (that is a host-side stand-in);
+// the device address is looked up once per device with it current.
+cudaError_t scratch_address(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+const void *select_slab(int nx, int scheme, int flux, int *threads)
+{
+    KernelTable t;
+    memset(&t, 0, sizeof t);
+    fill_f64_weno_burgers(t);
+    fill_f64_weno_advection(t);
+    fill_f64_fo(t);
+    for (int ci = 0; ci < NCPT; ++ci) {
+        const int need = (nx + CPT_VALUES[ci] - 1) / CPT_VALUES[ci];
+        if (need <= MAX_THREADS) {
+            *threads = ((need + 31) / 32) * 32;
+            return t.slab64[scheme][flux][ci];
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numflux,
+                                     double T, double L, const double *uC_dev, double *norm_dev,
+                                     void *stream)
+{
+    if (!uC_dev || !norm_dev) return MGRIT_EINVAL;
+    if (scheme != MGRIT_WENO5_SSPRK3 && scheme != MGRIT_FO_FE) return MGRIT_EINVAL;
+    if (flux != MGRIT_BURGERS && flux != MGRIT_ADVECTION) return MGRIT_EINVAL;
+    if (numflux != MGRIT_LF_SPLIT && numflux != MGRIT_LF_STATE) return MGRIT_EINVAL;
+    if (m < 2 || nt < m || nt % m) return MGRIT_EINVAL;
+    if (nx < (scheme == MGRIT_WENO5_SSPRK3 ? 5 : 3)) return MGRIT_EINVAL;
+    if (!(T > 0) || !(L > 0) || !std::isfinite(T) || !std::isfinite(L)) return MGRIT_EINVAL;
+    const int nC = nt / m;
+    if ((size_t)(nC + 1) * (size_t)nx > ROWS_MAX) return MGRIT_EINVAL;   // beyond the scratch
+    const size_t smem = slab_smem_bytes<double>(nx);
+    if (smem > 227 * 1024) return MGRIT_EINVAL;
+    int threads = 0;
+    const void *slab = select_slab(nx, scheme, flux, &threads);
+    if (!slab) return MGRIT_EINVAL;
+    const int blocks = restrict_blocks(nC, nx);
+    if ((size_t)blocks > PARTIALS_MAX) return MGRIT_EINVAL;
+
+    double *scratch = nullptr;
+    if (scratch_address(&scratch) != cudaSuccess) return MGRIT_ECUDA;
+    double *rows = scratch;
+    double *partials = scratch + ROWS_MAX;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaFuncSetAttribute(slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return MGRIT_ECUDA;
+
+    // rows 1..nC <- Phi_0^m(uC row j-1); every row and partial read below is
+    // written first by this call, so nothing needs clearing
+    SlabArgs<double> a;
+    memset(&a, 0, sizeof a);
+    a.mode = MODE_RELAX;
+    a.nx = nx;
+    a.m = m;
+    a.nC = nC;
+    a.fcf = 0;
+    a.numflux = numflux;
+    a.dxinv = nx / L;
+    a.dt = T / nt;
+    a.uC = uC_dev;
+    a.strideC = nx;
+    a.phirow = rows;
+    void *args[] = {&a};
+    if (cudaLaunchKernel(slab, dim3(nC), dim3(threads), args, smem, s) != cudaSuccess)
+        return MGRIT_ECUDA;
+
+    RestrictArgs r;
+    memset(&r, 0, sizeof r);
+    r.newC = uC_dev;
+    r.phirow = rows;
+    r.partials = partials;
+    r.nx = nx;
+    r.m = m;
+    r.nC = nC;
+    if (launch_restrict(r, blocks, s) != cudaSuccess) return MGRIT_ECUDA;
+    if (launch_norm(partials, blocks, norm_dev, s) != cudaSuccess) return MGRIT_ECUDA;
+    return MGRIT_OK;
+}

@@ -49,6 +49,7 @@ _SIGS = {
     "mgrit_serial_step": (_I, [_P, _P, _P, _I, _P]),
     "mgrit_residual": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "mgrit_launch_kernel": (_I, [_P, _I, _I, _I, _P]),
+    "mgrit_residual_static": (_I, [_I, _I, _I, _I, _I, _I, _D, _D, _P, _P, _P]),
     "mgrit_cycle_cell_updates": (_D, [_P]),
     "mgrit_last_error": (ctypes.c_char_p, [_P]),
     "mgrit_destroy": (None, [_P]),
