@@ -10,6 +10,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmgrit.so")
+# MGRIT_DEBUG variant: bounds checks on every shared/global index (prints and
+# skips a bad access instead of faulting)
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libmgrit_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
@@ -32,15 +36,19 @@ def nvcc():
     return exe
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile every .cu under csrc/ and link libmgrit.so (static cudart)."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=(), debug=False):
+    """Compile every .cu under csrc/ and link libmgrit.so (static cudart);
+    debug=True builds libmgrit_debug.so with -DMGRIT_DEBUG."""
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra = tuple(extra) + ("-DMGRIT_DEBUG",)
+    os.makedirs(bdir, exist_ok=True)
     srcs = sources()
     hdr = _headers_mtime()
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(bdir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
             jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
@@ -58,13 +66,14 @@ def build(force=False, verbose=False, extra=()):
             outs = list(ex.map(run, jobs))
     else:
         outs = []
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if jobs or not os.path.exists(lib):
+        tmp = lib + ".tmp.%d" % os.getpid()
         run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     return "".join(outs)
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=("-Xptxas", "-v") if "--ptxas" in sys.argv else ()))
+                extra=("-Xptxas", "-v") if "--ptxas" in sys.argv else (),
+                debug="--debug" in sys.argv))

@@ -283,6 +283,9 @@ static cudaError_t enqueue_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
     a.newC = ctx->newC[l];
     a.phirow = ctx->phirow[l];
     a.cstep = ctx->cstep[l];
+    a.nrows_uC = a.nrows_newC = a.nrows_phirow = a.nC + 1;
+    a.nrows_cstep = a.nC;
+    a.nrows_g = ctx->nt_l[l] + 1;
     return launch1(ctx->ln.slab, a.nC + 1, ctx->ln, s, &a);
 }
 
@@ -296,6 +299,7 @@ static cudaError_t enqueue_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
     a.gn = ctx->g[l + 1];
     a.un = ctx->u[l + 1];
     a.partials = l == 0 ? ctx->partials : nullptr;
+    a.nrows_g = ctx->nt_l[l] + 1;
     a.nx = ctx->nx;
     a.m = ctx->m;
     a.nC = ctx->nC_l[l];
@@ -312,6 +316,7 @@ static cudaError_t enqueue_coarse(mgrit_ctx *ctx, cudaStream_t s)
     a.g = ctx->g[l];
     a.rows = ctx->u[l];
     a.nsteps = ctx->nt_l[l];
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
     return launch1(ctx->ln.slab, 1, ctx->ln, s, &a);
 }
 
@@ -321,6 +326,8 @@ static cudaError_t enqueue_interp(mgrit_ctx *ctx, int l, cudaStream_t s)
     a.uC = ctx->u[l + 1];
     a.g = ctx->g[l];
     a.rows = ctx->u[l];
+    a.nrows_uC = a.nC + 1;
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
     return launch1(ctx->ln.slab, a.nC, ctx->ln, s, &a);
 }
 
@@ -514,6 +521,7 @@ extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm
     a.strideC = ctx->nx;
     a.fcf = 0;
     a.phirow = ctx->resid_rows;
+    a.nrows_uC = a.nrows_phirow = a.nC + 1;
     CK(launch1(ctx->ln.slab, a.nC, ctx->ln, s, &a));
     RestrictArgs r;
     memset(&r, 0, sizeof r);

@@ -12,9 +12,18 @@ namespace mgrit {
 
 enum { MODE_RELAX = 0, MODE_INTERP = 1, MODE_SEQ = 2 };
 
+// Row r of a [rows][nx] array with `nrows` rows; MGRIT_DEBUG builds check r
+// and return null (the access is then skipped) when it is out of range.
 template <typename T>
-__device__ __forceinline__ T *rowp(T *base, long long r, int nx)
+__device__ __forceinline__ T *rowp(T *base, long long r, int nx, long long nrows)
 {
+#ifdef MGRIT_DEBUG
+    if (r < 0 || r >= nrows) {
+        printf("MGRIT_DEBUG row %lld of %lld block %d thread %d\n", r, nrows, (int)blockIdx.x,
+               (int)threadIdx.x);
+        return nullptr;
+    }
+#endif
     return base + r * (long long)nx;
 }
 
@@ -36,6 +45,8 @@ struct SlabArgs {
     const R *src;
     R *rows;
     R *out;
+    // row extents of the arrays above (checked by MGRIT_DEBUG builds)
+    long long nrows_uC, nrows_newC, nrows_phirow, nrows_cstep, nrows_g, nrows_rows;
 };
 
 template <typename R, int SCHEME, int FLUX, int CPT>
@@ -49,29 +60,29 @@ __device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const
     const int nx = a.nx, m = a.m;
     R u[CPT];
     if (j == 0 || !a.fcf) {
-        S.load(u, a.uC + (long long)j * a.strideC);
+        S.load(u, rowp(a.uC, j, (int)a.strideC, a.nrows_uC));
     } else {
-        S.load(u, a.uC + (long long)(j - 1) * a.strideC);
+        S.load(u, rowp(a.uC, j - 1, (int)a.strideC, a.nrows_uC));
         for (int r = 1; r <= m; ++r) {
             S.step(u, a.dt);
-            if (a.g) S.add(u, rowp(a.g, (long long)m * (j - 1) + r, nx));
+            if (a.g) S.add(u, rowp(a.g, (long long)m * (j - 1) + r, nx, a.nrows_g));
         }
     }
-    if (a.newC) S.store(u, rowp(a.newC, j, nx));
+    if (a.newC) S.store(u, rowp(a.newC, j, nx, a.nrows_newC));
     if (j == a.nC) return;
     if (a.cstep) {
         // coarse step of the FAS term; u is then re-read from the row this
         // thread just stored (its own cells), which saves CPT registers
         S.step(u, a.dtc);
-        S.store(u, rowp(a.cstep, j, nx));
-        S.load(u, rowp(a.newC, j, nx));
+        S.store(u, rowp(a.cstep, j, nx, a.nrows_cstep));
+        S.load(u, rowp(a.newC, j, nx, a.nrows_newC));
     }
     for (int r = 1; r < m; ++r) {
         S.step(u, a.dt);
-        if (a.g) S.add(u, rowp(a.g, (long long)m * j + r, nx));
+        if (a.g) S.add(u, rowp(a.g, (long long)m * j + r, nx, a.nrows_g));
     }
     S.step(u, a.dt);
-    S.store(u, rowp(a.phirow, j + 1, nx));
+    S.store(u, rowp(a.phirow, j + 1, nx, a.nrows_phirow));
 }
 
 template <typename R, int SCHEME, int FLUX, int CPT>
@@ -81,16 +92,16 @@ __device__ __forceinline__ void interp_chunk(Slab<R, SCHEME, FLUX, CPT> &S, cons
     const int j = blockIdx.x;
     const int nx = a.nx, m = a.m;
     R u[CPT];
-    S.load(u, rowp(a.uC, j, nx));
-    S.store(u, rowp(a.rows, (long long)m * j, nx));
+    S.load(u, rowp(a.uC, j, nx, a.nrows_uC));
+    S.store(u, rowp(a.rows, (long long)m * j, nx, a.nrows_rows));
     for (int r = 1; r < m; ++r) {
         S.step(u, a.dt);
-        S.add(u, rowp(a.g, (long long)m * j + r, nx));
-        S.store(u, rowp(a.rows, (long long)m * j + r, nx));
+        S.add(u, rowp(a.g, (long long)m * j + r, nx, a.nrows_g));
+        S.store(u, rowp(a.rows, (long long)m * j + r, nx, a.nrows_rows));
     }
     if (j == a.nC - 1) {   // the last C-point of the level
-        S.load(u, rowp(a.uC, a.nC, nx));
-        S.store(u, rowp(a.rows, (long long)m * a.nC, nx));
+        S.load(u, rowp(a.uC, a.nC, nx, a.nrows_uC));
+        S.store(u, rowp(a.rows, (long long)m * a.nC, nx, a.nrows_rows));
     }
 }
 
@@ -103,8 +114,8 @@ __device__ __forceinline__ void seq_march(Slab<R, SCHEME, FLUX, CPT> &S, const S
     S.load(u, a.src);
     for (int i = 1; i <= a.nsteps; ++i) {
         S.step(u, a.dt);
-        if (a.g) S.add(u, rowp(a.g, i, nx));
-        if (a.rows) S.store(u, rowp(a.rows, i, nx));
+        if (a.g) S.add(u, rowp(a.g, i, nx, a.nrows_g));
+        if (a.rows) S.store(u, rowp(a.rows, i, nx, a.nrows_rows));
     }
     if (a.out) S.store(u, a.out);
 }

@@ -113,6 +113,7 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     a.uC = uC_dev;
     a.strideC = nx;
     a.phirow = rows;
+    a.nrows_uC = a.nrows_phirow = nC + 1;
     void *args[] = {&a};
     if (cudaLaunchKernel(slab, dim3(nC), dim3(threads), args, smem, s) != cudaSuccess)
         return MGRIT_ECUDA;

@@ -9,6 +9,10 @@
 // order, so the norm is bitwise reproducible from run to run.
 #include "restrict.cuh"
 
+#ifdef MGRIT_DEBUG
+#include <cstdio>
+#endif
+
 namespace mgrit {
 
 __global__ void __launch_bounds__(RESTRICT_THREADS) k_restrict(RestrictArgs a)
@@ -21,6 +25,12 @@ __global__ void __launch_bounds__(RESTRICT_THREADS) k_restrict(RestrictArgs a)
         const long long i = 1 + e / a.nx;
         const long long c = e - (i - 1) * a.nx;
         const long long at = i * a.nx + c;
+#ifdef MGRIT_DEBUG
+        if (a.g && (long long)a.m * i >= a.nrows_g) {
+            printf("MGRIT_DEBUG restrict g row %lld of %lld\n", (long long)a.m * i, a.nrows_g);
+            continue;
+        }
+#endif
         const double gl = a.g ? a.g[(long long)a.m * i * a.nx + c] : 0.0;
         const double phi = a.phirow[at];
         const double uc = a.newC[at];

@@ -12,6 +12,7 @@ struct RestrictArgs {
     double *gn;            // level-(l+1) g rows, or null
     double *un;            // level-(l+1) u rows, or null
     double *partials;      // per-block sums of r^2, or null
+    long long nrows_g;     // rows of g (checked by MGRIT_DEBUG builds)
     int nx, m, nC, guess;
 };
 

@@ -14,6 +14,9 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#ifdef MGRIT_DEBUG
+#include <cstdio>
+#endif
 
 namespace mgrit {
 
@@ -23,6 +26,21 @@ enum { NF_SPLIT = 0, NF_STATE = 1 };
 
 constexpr int GHOST = 3;
 constexpr int NWARP_MAX = 32;
+
+// MGRIT_DEBUG builds check every shared-memory index and every global row
+// index against its array's extent; a violation is printed once per thread
+// and the access is skipped (shared reads then see element 0), so a bad
+// index is reported instead of faulting.
+#ifdef MGRIT_DEBUG
+#define MGRIT_SH(arr, idx, lim)                                                              \
+    (*((unsigned)(idx) < (unsigned)(lim)                                                       \
+           ? &(arr)[(idx)]                                                                     \
+           : (printf("MGRIT_DEBUG smem %s[%d] limit %d block %d thread %d\n", #arr, (int)(idx), \
+                     (int)(lim), (int)blockIdx.x, (int)threadIdx.x),                           \
+              &(arr)[0])))
+#else
+#define MGRIT_SH(arr, idx, lim) ((arr)[(idx)])
+#endif
 
 // Physical flux (Sec. 2, Eq. burgers) and |eigenvalue| of its Jacobian.
 template <int FLUX, typename R>
@@ -36,36 +54,53 @@ __device__ __forceinline__ R phys_speed(R u)
     return FLUX == FLX_BURGERS ? fabs(u) : R(1);
 }
 
+// num / den for a positive, normal den.  FP64: the hardware reciprocal
+// estimate (rcp.approx.ftz.f64), one Newton-Raphson step r <- r + r(1 - den r),
+// then one correction of the quotient q <- q + r(num - den q) (the residual
+// num - den q is exact with an FMA).  The estimate's ~2^-20 relative error
+// becomes ~2^-40 after the Newton step and below 2^-53 after the correction:
+// within an ulp or two of the correctly rounded quotient, with no slow path
+// for special operands (a NaN or Inf operand propagates).  FP32: IEEE division.
+__device__ __forceinline__ double quotient(double num, double den)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(den));
+    r = fma(r, fma(-den, r, 1.0), r);
+    const double q = num * r;
+    return fma(r, fma(-den, q, num), q);
+}
+__device__ __forceinline__ float quotient(float num, float den) { return num / den; }
+
 // WENO5-JS value left of the interface i+1/2 from (a..e) = q_{i-2..i+2}
-// (Sec. 2.1.1, k = 2).  Candidate values P_r (times 6), smoothness
-// indicators in the expanded form 13/12 (2nd difference)^2 + 1/4 (1st
-// difference)^2 (equal to the quadratic forms B_r of the paper), weights
-// alpha_r = d_r / (eps + beta_r)^2 with d = (1, 6, 3)/10 for the stencils
-// ending at i, i+1, i+2.  The weight normalisation is done over a common
-// denominator: multiplying numerator and denominator of
-// sum_r alpha_r p_r / sum_r alpha_r by prod_r (eps + beta_r)^2 leaves a
-// single division per reconstruction (the 1/10 of d_r cancels).
+// (Sec. 2.1.1, k = 2), evaluated with few FP64 operations:
+//  - candidate values times 6, with the linear weights d = (1, 6, 3)/10 of
+//    the stencils ending at i, i+1, i+2 folded in (the 1/10 cancels);
+//  - smoothness indicators in the expanded form 13/12 D2^2 + 1/4 D1^2 (equal
+//    to the paper's quadratic forms B_r), carried as 4 (eps + beta), which
+//    scales every weight by the same factor;
+//  - the normalisation sum_r alpha_r p_r / sum_r alpha_r over the common
+//    denominator prod_r (eps + beta_r)^2: one division per reconstruction.
 template <typename R>
 __device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
 {
-    const R eps = R(1e-6);
-    const R k13 = R(13.0 / 12.0);
-    const R P0 = R(2) * a - R(7) * b + R(11) * c;   // stencil {i-2, i-1, i}
-    const R P1 = -b + R(5) * c + R(2) * d;          // stencil {i-1, i, i+1}
-    const R P2 = R(2) * c + R(5) * d - e;           // stencil {i, i+1, i+2}
+    const R eps4 = R(4e-6);
+    const R k133 = R(13.0 / 3.0);
+    const R P0 = R(2) * a - R(7) * b + R(11) * c;          // 6 p, stencil {i-2, i-1, i}, d = 1
+    const R P1 = R(-6) * b + R(30) * c + R(12) * d;        // 36 p, stencil {i-1, i, i+1}, d = 6
+    const R P2 = R(6) * c + R(15) * d - R(3) * e;          // 18 p, stencil {i, i+1, i+2}, d = 3
     const R x0 = a - R(2) * b + c, y0 = a - R(4) * b + R(3) * c;
     const R x1 = b - R(2) * c + d, y1 = b - d;
     const R x2 = c - R(2) * d + e, y2 = R(3) * c - R(4) * d + e;
-    R s0 = eps + k13 * x0 * x0 + R(0.25) * y0 * y0;
-    R s1 = eps + k13 * x1 * x1 + R(0.25) * y1 * y1;
-    R s2 = eps + k13 * x2 * x2 + R(0.25) * y2 * y2;
+    R s0 = k133 * x0 * x0 + (y0 * y0 + eps4);              // 4 (eps + beta_0)
+    R s1 = k133 * x1 * x1 + (y1 * y1 + eps4);
+    R s2 = k133 * x2 * x2 + (y2 * y2 + eps4);
     s0 *= s0;
     s1 *= s1;
     s2 *= s2;
-    const R t0 = s1 * s2;              // d_0 = 1  (x 1/10)
-    const R t1 = R(6) * (s0 * s2);     // d_1 = 6
-    const R t2 = R(3) * (s0 * s1);     // d_2 = 3
-    return (P0 * t0 + P1 * t1 + P2 * t2) / (R(6) * (t0 + t1 + t2));
+    const R t0 = s1 * s2, t1 = s0 * s2, t2 = s0 * s1;
+    const R num = P0 * t0 + P1 * t1 + P2 * t2;
+    const R den = R(6) * t0 + R(36) * t1 + R(18) * t2;
+    return quotient(num, den);
 }
 
 template <typename R>
@@ -81,11 +116,11 @@ template <typename R>
 __device__ __forceinline__ R block_max(R v, R *red)
 {
     v = warp_max(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) MGRIT_SH(red, threadIdx.x >> 5, NWARP_MAX) = v;
     __syncthreads();
     const int nw = blockDim.x >> 5;
     R r = red[0];
-    for (int k = 1; k < nw; ++k) r = fmax(r, red[k]);
+    for (int k = 1; k < nw; ++k) r = fmax(r, MGRIT_SH(red, k, NWARP_MAX));
     return r;
 }
 
@@ -109,31 +144,34 @@ struct Slab {
     }
 
     __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
+    __device__ __forceinline__ int lim() const { return nx + 2 * GHOST; }   // extent of qa, qb, qf
 
     // store cell i (and its periodic ghost copy) into slot i + GHOST
     __device__ __forceinline__ void put(R *arr, int i, R v) const
     {
-        arr[i + GHOST] = v;
-        if (i < GHOST) arr[i + GHOST + nx] = v;
-        if (i >= nx - GHOST) arr[i + GHOST - nx] = v;
+        MGRIT_SH(arr, i + GHOST, lim()) = v;
+        if (i < GHOST) MGRIT_SH(arr, i + GHOST + nx, lim()) = v;
+        if (i >= nx - GHOST) MGRIT_SH(arr, i + GHOST - nx, lim()) = v;
     }
 
     // left-biased reconstruction at i+1/2 from slots around s = i + GHOST
     __device__ __forceinline__ R rec_minus(const R *q, int s) const
     {
-        if (SCHEME == SCH_FO_FE) return q[s];
-        return weno5_left<R>(q[s - 2], q[s - 1], q[s], q[s + 1], q[s + 2]);
+        if (SCHEME == SCH_FO_FE) return MGRIT_SH(q, s, lim());
+        return weno5_left<R>(MGRIT_SH(q, s - 2, lim()), MGRIT_SH(q, s - 1, lim()), MGRIT_SH(q, s, lim()),
+                             MGRIT_SH(q, s + 1, lim()), MGRIT_SH(q, s + 2, lim()));
     }
     // right-biased reconstruction at i+1/2: the mirrored stencil
     __device__ __forceinline__ R rec_plus(const R *q, int s) const
     {
-        if (SCHEME == SCH_FO_FE) return q[s + 1];
-        return weno5_left<R>(q[s + 3], q[s + 2], q[s + 1], q[s], q[s - 1]);
+        if (SCHEME == SCH_FO_FE) return MGRIT_SH(q, s + 1, lim());
+        return weno5_left<R>(MGRIT_SH(q, s + 3, lim()), MGRIT_SH(q, s + 2, lim()), MGRIT_SH(q, s + 1, lim()),
+                             MGRIT_SH(q, s, lim()), MGRIT_SH(q, s - 1, lim()));
     }
 
     __device__ __forceinline__ void put_flux(int i, R F) const
     {
-        qf[i + 1] = F;
+        MGRIT_SH(qf, i + 1, nx + 1) = F;
         if (i == nx - 1) qf[0] = F;
     }
 
@@ -155,9 +193,18 @@ struct Slab {
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) {
-                    const R f = phys_flux<FLUX>(w[c]);
-                    put(qa, i, R(0.5) * (f + alpha * w[c]));
-                    put(qb, i, R(0.5) * (f - alpha * w[c]));
+                    // f^{+/-} = (f(w) +/- alpha w)/2; for Burgers (w/2)(w/2 +/- alpha)
+                    R fp, fm;
+                    if (FLUX == FLX_BURGERS) {
+                        const R hw = R(0.5) * w[c];
+                        fp = hw * (hw + alpha);
+                        fm = hw * (hw - alpha);
+                    } else {
+                        fp = R(0.5) * (w[c] + alpha * w[c]);
+                        fm = R(0.5) * (w[c] - alpha * w[c]);
+                    }
+                    put(qa, i, fp);
+                    put(qb, i, fm);
                 }
             }
             __syncthreads();
@@ -182,8 +229,8 @@ struct Slab {
                 if (i < nx) {
                     const R um = rec_minus(qa, i + GHOST);
                     const R up = rec_plus(qa, i + GHOST);
-                    qb[i] = um;
-                    qf[i + 1] = up;
+                    MGRIT_SH(qb, i, nx) = um;
+                    MGRIT_SH(qf, i + 1, nx + 1) = up;
                     v = fmax(v, fmax(phys_speed<FLUX>(um), phys_speed<FLUX>(up)));
                 }
             }
@@ -193,7 +240,7 @@ struct Slab {
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) {
-                    const R um = qb[i], up = qf[i + 1];
+                    const R um = MGRIT_SH(qb, i, nx), up = MGRIT_SH(qf, i + 1, nx + 1);
                     put_flux(i, R(0.5) * (phys_flux<FLUX>(up) + phys_flux<FLUX>(um)) -
                                     R(0.5) * alpha * (up - um));
                 }
@@ -202,42 +249,44 @@ struct Slab {
         __syncthreads();
     }
 
-    // A_i(w) = -(F_{i+1/2} - F_{i-1/2}) / dx for owned slot c (Eq. spaceDisc);
-    // valid after fluxes().
-    __device__ __forceinline__ R A(int c) const
+    // F_{i-1/2} - F_{i+1/2} for owned slot c: A_i(w) = that / dx (Eq. spaceDisc);
+    // valid after fluxes()
+    __device__ __forceinline__ R dF(int c) const
     {
         const int i = cell(c);
-        return -(qf[i + 1] - qf[i]) * dxinv;
+        return MGRIT_SH(qf, i, nx + 1) - MGRIT_SH(qf, i + 1, nx + 1);
     }
 
     // u <- Phi(u) with step dt: SSPRK3 (Eq. SSPRK3) or forward Euler (Eq. SSPRK1)
     __device__ __forceinline__ void step(R (&u)[CPT], R dt)
     {
+        const R h = dt * dxinv;   // dt A_i = h (F_{i-1/2} - F_{i+1/2})
         if (SCHEME == SCH_FO_FE) {
             fluxes(u);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < nx) u[c] = u[c] + dt * A(c);
+                if (cell(c) < nx) u[c] = u[c] + h * dF(c);
             return;
         }
         R w[CPT];
         fluxes(u);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? u[c] + dt * A(c) : R(0);
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? u[c] + h * dF(c) : R(0);
         fluxes(w);
-        const R q = R(0.25) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) w[c] = R(0.75) * u[c] + R(0.25) * w[c] + q * A(c);
+            if (cell(c) < nx) w[c] = R(0.75) * u[c] + R(0.25) * (w[c] + h * dF(c));
         fluxes(w);
-        const R t = R(2.0 / 3.0) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * w[c] + t * A(c);
+            if (cell(c) < nx) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * (w[c] + h * dF(c));
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *__restrict__ row) const
     {
+#ifdef MGRIT_DEBUG
+        if (!row) return;
+#endif
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);
@@ -246,6 +295,9 @@ struct Slab {
     }
     __device__ __forceinline__ void store(const R (&u)[CPT], R *__restrict__ row) const
     {
+#ifdef MGRIT_DEBUG
+        if (!row) return;
+#endif
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);
@@ -254,6 +306,9 @@ struct Slab {
     }
     __device__ __forceinline__ void add(R (&u)[CPT], const R *__restrict__ row) const
     {
+#ifdef MGRIT_DEBUG
+        if (!row) return;
+#endif
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);

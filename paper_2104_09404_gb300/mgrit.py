@@ -10,7 +10,9 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libmgrit.so")
+# MGRIT_DEBUG=1 selects the bounds-checked build libmgrit_debug.so
+LIB_PATH = os.path.join(PKG, "libmgrit_debug.so" if os.environ.get("MGRIT_DEBUG") == "1"
+                        else "libmgrit.so")
 
 OK, EINVAL, ECUDA, ENOMEM, EDIVERGED, ENOTCONV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 WENO5_SSPRK3, FO_FE = 0, 1
