@@ -185,6 +185,13 @@ int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *st
 int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numflux, double T,
                           double L, const double *uC_dev, double *norm_dev, void *stream);
 
+/* Launch shape chosen for this context (for reports and tests):
+ * what = 0: cells per thread of the slab kernel; 1: threads per CTA;
+ * 2: CTAs per thread-block cluster used for sequential stepping (the
+ * coarsest solve and mgrit_serial_step; 1 = a single CTA), known after the
+ * first call that allocates (0 before).  -1 for an unknown `what`. */
+int mgrit_query(const mgrit_ctx *ctx, int what);
+
 /* Cells x Phi applications of one V-cycle (for throughput figures). */
 double mgrit_cycle_cell_updates(const mgrit_ctx *ctx);
 

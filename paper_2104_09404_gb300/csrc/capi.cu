@@ -37,6 +37,14 @@ struct Launch {
     size_t smem;
 };
 
+// sequential stepping on a thread-block cluster (coarsest solve, serial stepper)
+struct ClusterLaunch {
+    const void *fn;     // k_seq_cluster instance; null: single-CTA k_slab
+    int K;              // CTAs in the cluster
+    int threads;
+    size_t smem;
+};
+
 }  // namespace
 
 struct mgrit_ctx {
@@ -45,6 +53,7 @@ struct mgrit_ctx {
     int nt_l[MAXLEV], nC_l[MAXLEV];
     double dt_l[MAXLEV];
     Launch ln;
+    ClusterLaunch lc;
     bool alloc;
     bool prepared;     // workspaces, graphs and an initial iterate exist
     bool have_state;   // a level-0 relaxation has produced newC[0]
@@ -227,6 +236,70 @@ static int dalloc(mgrit_ctx *ctx, double **ptr, size_t rows)
     return MGRIT_OK;
 }
 
+// Cluster size for sequential stepping: the largest power of two K <= 16
+// leaving at least 256 cells per CTA, reduced until the device can co-schedule
+// one cluster of that shape.  nx < 512 keeps the single-CTA kernel.
+static void choose_cluster(mgrit_ctx *ctx)
+{
+    ctx->lc.fn = nullptr;
+    const int nx = ctx->nx;
+    int K = 1;
+    while (K < CLUSTER_MAX && nx / (2 * K) >= 256) K *= 2;
+    for (; K >= 2; K /= 2) {
+        const int nmax = (nx + K - 1) / K;
+        const int cpt = nmax <= MAX_THREADS ? 1 : 2;
+        if (nmax > 2 * MAX_THREADS) break;
+        const void *fn = table().seqc64[ctx->scheme][ctx->flux][cpt - 1];
+        const size_t smem = cluster_smem_bytes<double>(nx, K);
+        const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+            continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+            continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(K);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = K;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        ctx->lc.fn = fn;
+        ctx->lc.K = K;
+        ctx->lc.threads = threads;
+        ctx->lc.smem = smem;
+        return;
+    }
+    cudaGetLastError();   // clear a refused attribute or occupancy query
+}
+
+static cudaError_t launch_seq(const mgrit_ctx *ctx, cudaStream_t s, SlabArgs<double> *a)
+{
+    if (!ctx->lc.fn) return launch1(ctx->ln.slab, 1, ctx->ln, s, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctx->lc.K);
+    cfg.blockDim = dim3(ctx->lc.threads);
+    cfg.dynamicSmemBytes = ctx->lc.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ctx->lc.K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void *args[] = {a};
+    return cudaLaunchKernelExC(&cfg, ctx->lc.fn, args);
+}
+
 static int ensure_alloc(mgrit_ctx *ctx)
 {
     if (ctx->alloc) return MGRIT_OK;
@@ -251,6 +324,7 @@ static int ensure_alloc(mgrit_ctx *ctx)
     CK(cudaEventCreate(&ctx->ev1));
     CK(cudaFuncSetAttribute(ctx->ln.slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)ctx->ln.smem));
+    choose_cluster(ctx);
     ctx->alloc = true;
     return MGRIT_OK;
 }
@@ -317,7 +391,7 @@ static cudaError_t enqueue_coarse(mgrit_ctx *ctx, cudaStream_t s)
     a.rows = ctx->u[l];
     a.nsteps = ctx->nt_l[l];
     a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
-    return launch1(ctx->ln.slab, 1, ctx->ln, s, &a);
+    return launch_seq(ctx, s, &a);
 }
 
 static cudaError_t enqueue_interp(mgrit_ctx *ctx, int l, cudaStream_t s)
@@ -504,7 +578,7 @@ extern "C" int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *u
     a.src = u0_dev;
     a.out = uT_dev;
     a.nsteps = nsteps;
-    CK(launch1(ctx->ln.slab, 1, ctx->ln, (cudaStream_t)stream, &a));
+    CK(launch_seq(ctx, (cudaStream_t)stream, &a));
     return MGRIT_OK;
 }
 
@@ -568,6 +642,17 @@ extern "C" int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int rep
         }
     }
     return MGRIT_OK;
+}
+
+extern "C" int mgrit_query(const mgrit_ctx *ctx, int what)
+{
+    if (!ctx) return -1;
+    switch (what) {
+    case 0: return ctx->ln.cpt;
+    case 1: return ctx->ln.threads;
+    case 2: return ctx->alloc ? (ctx->lc.fn ? ctx->lc.K : 1) : 0;
+    default: return -1;
+    }
 }
 
 extern "C" const char *mgrit_last_error(const mgrit_ctx *ctx)

@@ -1,6 +1,6 @@
 // Table of slab-kernel instances, indexed by [scheme][flux][cells-per-thread].
 #pragma once
-#include "kernels.cuh"
+#include "cluster_seq.cuh"
 
 namespace mgrit {
 
@@ -10,6 +10,7 @@ constexpr int MAX_THREADS = 512;   // matches __launch_bounds__ of k_slab
 
 struct KernelTable {
     const void *slab64[2][2][NCPT];
+    const void *seqc64[2][2][2];   // k_seq_cluster, cells per thread 1 or 2
 };
 
 template <typename R, int S, int F>
@@ -20,6 +21,13 @@ void fill_sf(const void *(&t)[2][2][NCPT])
     t[S][F][2] = (const void *)&k_slab<R, S, F, 4>;
     t[S][F][3] = (const void *)&k_slab<R, S, F, 8>;
     t[S][F][4] = (const void *)&k_slab<R, S, F, 16>;
+}
+
+template <typename R, int S, int F>
+void fill_cluster(const void *(&t)[2][2][2])
+{
+    t[S][F][0] = (const void *)&k_seq_cluster<R, S, F, 1>;
+    t[S][F][1] = (const void *)&k_seq_cluster<R, S, F, 2>;
 }
 
 // one translation unit per (precision, scheme, flux), compiled in parallel

@@ -54,22 +54,12 @@ __device__ __forceinline__ R phys_speed(R u)
     return FLUX == FLX_BURGERS ? fabs(u) : R(1);
 }
 
-// num / den for a positive, normal den.  FP64: the hardware reciprocal
-// estimate (rcp.approx.ftz.f64), one Newton-Raphson step r <- r + r(1 - den r),
-// then one correction of the quotient q <- q + r(num - den q) (the residual
-// num - den q is exact with an FMA).  The estimate's ~2^-20 relative error
-// becomes ~2^-40 after the Newton step and below 2^-53 after the correction:
-// within an ulp or two of the correctly rounded quotient, with no slow path
-// for special operands (a NaN or Inf operand propagates).  FP32: IEEE division.
-__device__ __forceinline__ double quotient(double num, double den)
+// num / den of the weight normalisation (IEEE division in both precisions).
+template <typename R>
+__device__ __forceinline__ R quotient(R num, R den)
 {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(den));
-    r = fma(r, fma(-den, r, 1.0), r);
-    const double q = num * r;
-    return fma(r, fma(-den, q, num), q);
+    return num / den;
 }
-__device__ __forceinline__ float quotient(float num, float den) { return num / den; }
 
 // WENO5-JS value left of the interface i+1/2 from (a..e) = q_{i-2..i+2}
 // (Sec. 2.1.1, k = 2), evaluated with few FP64 operations:

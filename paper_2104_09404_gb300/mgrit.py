@@ -53,6 +53,7 @@ _SIGS = {
     "mgrit_launch_kernel": (_I, [_P, _I, _I, _I, _P]),
     "mgrit_residual_static": (_I, [_I, _I, _I, _I, _I, _I, _D, _D, _P, _P, _P]),
     "mgrit_cycle_cell_updates": (_D, [_P]),
+    "mgrit_query": (_I, [_P, _I]),
     "mgrit_last_error": (ctypes.c_char_p, [_P]),
     "mgrit_destroy": (None, [_P]),
 }
@@ -166,6 +167,11 @@ class Solver:
 
     def cycle_cell_updates(self):
         return load().mgrit_cycle_cell_updates(self._h)
+
+    def query(self, what):
+        """0: cells per thread, 1: threads per CTA, 2: cluster size of the
+        sequential stepper (0 before the first allocating call)."""
+        return load().mgrit_query(self._h, what)
 
     def close(self):
         if getattr(self, "_h", None):

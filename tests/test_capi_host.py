@@ -85,6 +85,8 @@ def test_create_set_params_destroy_without_gpu(lib):
         q = M.mgrit_params.from_buffer_copy(p)
         setattr(q, field, bad)
         assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field
+    assert lib.mgrit_query(h, 0) == 1 and lib.mgrit_query(h, 1) == 128   # 100 cells, 1 per thread
+    assert lib.mgrit_query(h, 2) == 0 and lib.mgrit_query(h, 9) == -1    # nothing allocated yet
     # 3 levels, m = 4: (2*4 + 1) * 16 + (2*4 + 1 + 3) * 4 + 4 steps per cycle at FCF
     assert lib.mgrit_cycle_cell_updates(h) == 100 * ((2 * 4 + 1) * 16 + (2 * 4 + 1 + 3) * 4 + 4)
     lib.mgrit_destroy(h)

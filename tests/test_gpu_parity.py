@@ -74,6 +74,17 @@ def test_serial_stepping_parity(M, nx, scheme, flux, numflux, nsteps, cfl):
     assert relerr(out.cpu().numpy(), ref) <= RTOL
 
 
+@pytest.mark.parametrize("nx,K", [(256, 1), (512, 2), (1000, 2), (2048, 8), (4096, 16), (8192, 16)])
+def test_sequential_stepper_cluster_shape(M, nx, K):
+    # the serial stepper and the coarsest solve spread one slab over a
+    # cluster of K CTAs (at least 256 cells each); a silent fallback to one
+    # CTA would show here
+    s = M.Solver(nx, 16, 2, 2, T=0.01)
+    s.serial_step(dev(inputs.sine_ic(nx)), 2)
+    torch.cuda.synchronize()
+    assert s.query(2) == K
+
+
 def test_serial_in_place(M):
     nx, n, T = 200, 16, 0.02
     u0 = inputs.sine_ic(nx)
