@@ -137,15 +137,9 @@ struct ClusterSlab {
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < n) {
-                    R p, q;
-                    if (FLUX == FLX_BURGERS) {
-                        const R hw = R(0.5) * w[c];
-                        p = hw * (hw + alpha);
-                        q = hw * (hw - alpha);
-                    } else {
-                        p = R(0.5) * (w[c] + alpha * w[c]);
-                        q = R(0.5) * (w[c] - alpha * w[c]);
-                    }
+                    const R f = phys_flux<FLUX>(w[c]);
+                    const R p = R(0.5) * (f + alpha * w[c]);
+                    const R q = R(0.5) * (f - alpha * w[c]);
                     MGRIT_SH(fp, i + GHOST, lim()) = p;
                     MGRIT_SH(fm, i + GHOST, lim()) = q;
                 }
@@ -197,35 +191,36 @@ struct ClusterSlab {
         __syncthreads();
     }
 
-    __device__ __forceinline__ R dF(int c) const
+    __device__ __forceinline__ R A(int c) const
     {
         const int i = cell(c);
-        return MGRIT_SH(qf, i, nmax + 2) - MGRIT_SH(qf, i + 1, nmax + 2);
+        return -(MGRIT_SH(qf, i + 1, nmax + 2) - MGRIT_SH(qf, i, nmax + 2)) * dxinv;
     }
 
     // u <- Phi(u); stage buffers alternate with the global stage counter
     __device__ __forceinline__ void step(R (&u)[CPT], R dt, int &stage)
     {
-        const R h = dt * dxinv;
         if (SCHEME == SCH_FO_FE) {
             fluxes(u, (stage++) & 1);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < n) u[c] = u[c] + h * dF(c);
+                if (cell(c) < n) u[c] = u[c] + dt * A(c);
             return;
         }
         R w[CPT];
         fluxes(u, (stage++) & 1);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < n) ? u[c] + h * dF(c) : R(0);
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < n) ? u[c] + dt * A(c) : R(0);
         fluxes(w, (stage++) & 1);
+        const R q = R(0.25) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) w[c] = R(0.75) * u[c] + R(0.25) * (w[c] + h * dF(c));
+            if (cell(c) < n) w[c] = R(0.75) * u[c] + R(0.25) * w[c] + q * A(c);
         fluxes(w, (stage++) & 1);
+        const R t = R(2.0 / 3.0) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * (w[c] + h * dF(c));
+            if (cell(c) < n) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * w[c] + t * A(c);
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *row) const
@@ -239,11 +234,11 @@ struct ClusterSlab {
         for (int c = 0; c < CPT; ++c)
             if (cell(c) < n) row[lo + cell(c)] = u[c];
     }
-    __device__ __forceinline__ void add(R (&u)[CPT], const R *row) const
+    __device__ __forceinline__ void add(R (&u)[CPT], const double *row) const
     {
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) u[c] += row[lo + cell(c)];
+            if (cell(c) < n) u[c] = R((double)u[c] + row[lo + cell(c)]);
     }
 };
 

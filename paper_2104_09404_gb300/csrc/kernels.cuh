@@ -39,7 +39,7 @@ struct SlabArgs {
     R *newC;              // relaxed C-points, rows 0..nC (null: not stored)
     R *phirow;            // row j+1 = Phi_l(u^{m(j+1)-1})
     R *cstep;             // row j = Phi_{l+1}(newC_j), j < nC (null: skipped; needs newC)
-    const R *g;           // level right-hand side rows, or null (zero)
+    const double *g;      // level right-hand side rows (FP64 in every precision), or null (zero)
     // MODE_SEQ: start state src, rows 1..nsteps out in rows (optional), final in out
     // MODE_INTERP: fine rows out in rows
     const R *src;

@@ -54,43 +54,36 @@ __device__ __forceinline__ R phys_speed(R u)
     return FLUX == FLX_BURGERS ? fabs(u) : R(1);
 }
 
-// num / den of the weight normalisation (IEEE division in both precisions).
-template <typename R>
-__device__ __forceinline__ R quotient(R num, R den)
-{
-    return num / den;
-}
-
 // WENO5-JS value left of the interface i+1/2 from (a..e) = q_{i-2..i+2}
-// (Sec. 2.1.1, k = 2), evaluated with few FP64 operations:
-//  - candidate values times 6, with the linear weights d = (1, 6, 3)/10 of
-//    the stencils ending at i, i+1, i+2 folded in (the 1/10 cancels);
-//  - smoothness indicators in the expanded form 13/12 D2^2 + 1/4 D1^2 (equal
-//    to the paper's quadratic forms B_r), carried as 4 (eps + beta), which
-//    scales every weight by the same factor;
-//  - the normalisation sum_r alpha_r p_r / sum_r alpha_r over the common
-//    denominator prod_r (eps + beta_r)^2: one division per reconstruction.
+// (Sec. 2.1.1, k = 2).  Candidate values P_r (times 6), smoothness
+// indicators in the expanded form 13/12 (2nd difference)^2 + 1/4 (1st
+// difference)^2 (equal to the quadratic forms B_r of the paper), weights
+// alpha_r = d_r / (eps + beta_r)^2 with d = (1, 6, 3)/10 for the stencils
+// ending at i, i+1, i+2.  The weight normalisation is done over a common
+// denominator: multiplying numerator and denominator of
+// sum_r alpha_r p_r / sum_r alpha_r by prod_r (eps + beta_r)^2 leaves a
+// single division per reconstruction (the 1/10 of d_r cancels).
 template <typename R>
 __device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
 {
-    const R eps4 = R(4e-6);
-    const R k133 = R(13.0 / 3.0);
-    const R P0 = R(2) * a - R(7) * b + R(11) * c;          // 6 p, stencil {i-2, i-1, i}, d = 1
-    const R P1 = R(-6) * b + R(30) * c + R(12) * d;        // 36 p, stencil {i-1, i, i+1}, d = 6
-    const R P2 = R(6) * c + R(15) * d - R(3) * e;          // 18 p, stencil {i, i+1, i+2}, d = 3
+    const R eps = R(1e-6);
+    const R k13 = R(13.0 / 12.0);
+    const R P0 = R(2) * a - R(7) * b + R(11) * c;   // stencil {i-2, i-1, i}
+    const R P1 = -b + R(5) * c + R(2) * d;          // stencil {i-1, i, i+1}
+    const R P2 = R(2) * c + R(5) * d - e;           // stencil {i, i+1, i+2}
     const R x0 = a - R(2) * b + c, y0 = a - R(4) * b + R(3) * c;
     const R x1 = b - R(2) * c + d, y1 = b - d;
     const R x2 = c - R(2) * d + e, y2 = R(3) * c - R(4) * d + e;
-    R s0 = k133 * x0 * x0 + (y0 * y0 + eps4);              // 4 (eps + beta_0)
-    R s1 = k133 * x1 * x1 + (y1 * y1 + eps4);
-    R s2 = k133 * x2 * x2 + (y2 * y2 + eps4);
+    R s0 = eps + k13 * x0 * x0 + R(0.25) * y0 * y0;
+    R s1 = eps + k13 * x1 * x1 + R(0.25) * y1 * y1;
+    R s2 = eps + k13 * x2 * x2 + R(0.25) * y2 * y2;
     s0 *= s0;
     s1 *= s1;
     s2 *= s2;
-    const R t0 = s1 * s2, t1 = s0 * s2, t2 = s0 * s1;
-    const R num = P0 * t0 + P1 * t1 + P2 * t2;
-    const R den = R(6) * t0 + R(36) * t1 + R(18) * t2;
-    return quotient(num, den);
+    const R t0 = s1 * s2;              // d_0 = 1  (x 1/10)
+    const R t1 = R(6) * (s0 * s2);     // d_1 = 6
+    const R t2 = R(3) * (s0 * s1);     // d_2 = 3
+    return (P0 * t0 + P1 * t1 + P2 * t2) / (R(6) * (t0 + t1 + t2));
 }
 
 template <typename R>
@@ -183,18 +176,9 @@ struct Slab {
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) {
-                    // f^{+/-} = (f(w) +/- alpha w)/2; for Burgers (w/2)(w/2 +/- alpha)
-                    R fp, fm;
-                    if (FLUX == FLX_BURGERS) {
-                        const R hw = R(0.5) * w[c];
-                        fp = hw * (hw + alpha);
-                        fm = hw * (hw - alpha);
-                    } else {
-                        fp = R(0.5) * (w[c] + alpha * w[c]);
-                        fm = R(0.5) * (w[c] - alpha * w[c]);
-                    }
-                    put(qa, i, fp);
-                    put(qb, i, fm);
+                    const R f = phys_flux<FLUX>(w[c]);
+                    put(qa, i, R(0.5) * (f + alpha * w[c]));
+                    put(qb, i, R(0.5) * (f - alpha * w[c]));
                 }
             }
             __syncthreads();
@@ -239,37 +223,38 @@ struct Slab {
         __syncthreads();
     }
 
-    // F_{i-1/2} - F_{i+1/2} for owned slot c: A_i(w) = that / dx (Eq. spaceDisc);
-    // valid after fluxes()
-    __device__ __forceinline__ R dF(int c) const
+    // A_i(w) = -(F_{i+1/2} - F_{i-1/2}) / dx for owned slot c (Eq. spaceDisc);
+    // valid after fluxes().
+    __device__ __forceinline__ R A(int c) const
     {
         const int i = cell(c);
-        return MGRIT_SH(qf, i, nx + 1) - MGRIT_SH(qf, i + 1, nx + 1);
+        return -(MGRIT_SH(qf, i + 1, nx + 1) - MGRIT_SH(qf, i, nx + 1)) * dxinv;
     }
 
     // u <- Phi(u) with step dt: SSPRK3 (Eq. SSPRK3) or forward Euler (Eq. SSPRK1)
     __device__ __forceinline__ void step(R (&u)[CPT], R dt)
     {
-        const R h = dt * dxinv;   // dt A_i = h (F_{i-1/2} - F_{i+1/2})
         if (SCHEME == SCH_FO_FE) {
             fluxes(u);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < nx) u[c] = u[c] + h * dF(c);
+                if (cell(c) < nx) u[c] = u[c] + dt * A(c);
             return;
         }
         R w[CPT];
         fluxes(u);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? u[c] + h * dF(c) : R(0);
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? u[c] + dt * A(c) : R(0);
         fluxes(w);
+        const R q = R(0.25) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) w[c] = R(0.75) * u[c] + R(0.25) * (w[c] + h * dF(c));
+            if (cell(c) < nx) w[c] = R(0.75) * u[c] + R(0.25) * w[c] + q * A(c);
         fluxes(w);
+        const R t = R(2.0 / 3.0) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * (w[c] + h * dF(c));
+            if (cell(c) < nx) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * w[c] + t * A(c);
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *__restrict__ row) const
@@ -294,7 +279,9 @@ struct Slab {
             if (i < nx) row[i] = u[c];
         }
     }
-    __device__ __forceinline__ void add(R (&u)[CPT], const R *__restrict__ row) const
+    // u += g row; g is kept in FP64 (the FAS tau term), so an FP32 sweep adds
+    // in FP64 and rounds the sum once
+    __device__ __forceinline__ void add(R (&u)[CPT], const double *__restrict__ row) const
     {
 #ifdef MGRIT_DEBUG
         if (!row) return;
@@ -302,7 +289,7 @@ struct Slab {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);
-            if (i < nx) u[c] += row[i];
+            if (i < nx) u[c] = R((double)u[c] + row[i]);
         }
     }
 };
