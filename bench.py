@@ -51,6 +51,8 @@ FLOPS_PER_CELL_UPDATE = 486
 # FP64 peak of the SIMT pipe, from the unit counts and clocks: 152 SMs x
 # 2.07 GHz x 4 FP64 FLOP/clk/SM (the nominal 1.25 TFLOP/s FP64 rate).
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) per level-0 relaxation launch from an ncu
 # capture, keyed by a hash of the kernel sources it was taken on; reported
@@ -352,6 +354,33 @@ def run_mgrit(args):
                "rel_max_diff_vs_serial_uT": err}
         sc.close()
 
+    # ---- the same workload with FP32 sweeps (precision = 32) ---------------
+    s32 = mgrit.Solver(W["nx"], W["nt"], W["m"], W["levels"], T=W["T"], precision=32)
+    for _ in range(3):
+        s32.run_cycles(u0, 1)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        s32.run_cycles(u0, 1)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms32 = a.elapsed_time(b)
+    s32.run_cycles(u0, 0)
+    s32.launch_kernel(0, 0, 1)
+    torch.cuda.synchronize()
+    a.record(stream)
+    s32.launch_kernel(0, 0, reps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    relax32_ms = a.elapsed_time(b) / reps
+    ach32 = FLOPS_PER_CELL_UPDATE * relax0_updates / (relax32_ms / 1e3) / 1e12
+    fp32 = {"value": per_cycle * args.steps / (ms32 / 1e3), "unit": "cell-updates/s",
+            "ms_per_step": ms32 / args.steps, "relax_l0_ms": relax32_ms,
+            "roofline": {"bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS,
+                         "peak_source": "derived FP32 SIMT rate: 152 SMs x 128 lanes x 2 x 2.07 GHz"}}
+    s32.close()
+
     if rank != 0:
         if ws > 1:
             tdist.destroy_process_group()
@@ -394,6 +423,7 @@ def run_mgrit(args):
                        "cluster_ctas": s.query(2)},
         "mgrit_outcome_as_stated": outcome,
         "time_to_tol_cfl_capped": ttt,
+        "fp32_sweeps": fp32,
     }
     print(json.dumps(line))
     if ws > 1:

@@ -17,8 +17,8 @@
  * (Eq. interpolation).
  *
  * Conventions for every entry point:
- *  - Arrays are FP64, row-major [time][cell]; one row is nx contiguous cell
- *    values (cell i covers [i dx, (i+1) dx)).  Pointers named *_dev are
+ *  - Arrays passed in and out are FP64, row-major [time][cell]; one row is nx
+ *    contiguous cell values (cell i covers [i dx, (i+1) dx)).  Pointers named *_dev are
  *    device pointers on the current CUDA device; the caller allocates and
  *    owns them.  The context owns all level workspaces and CUDA graphs.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
@@ -68,7 +68,13 @@ typedef struct {
     int numflux;     /* MGRIT_LF_SPLIT (default) / MGRIT_LF_STATE */
     double tol;      /* stop when the level-0 residual 2-norm < tol (default 1e-10) */
     int max_iter;    /* cycles before MGRIT_ENOTCONV (default 64, at most 254) */
-    int precision;   /* 64: every sweep in FP64 (the only value accepted) */
+    int precision;   /* 64: every sweep in FP64 (default when nx fits an FP64 slab).
+                        32: relaxation and interpolation sweeps in FP32; the FAS
+                        tau term (g rows), residual, norm, convergence test and
+                        the coarsest sequential solve stay FP64.  The FP64
+                        residual of an FP32 iteration levels off near FP32
+                        rounding, so a solve also stops (MGRIT_OK, stats.stagnated
+                        = 1) once two cycles reduce it by less than 10 %. */
 } mgrit_params;
 
 typedef struct {
@@ -78,6 +84,7 @@ typedef struct {
                              relaxation of cycle k, k = 0..iters */
     double t_total_ms;    /* device time of the solve (CUDA events) */
     double cell_updates;  /* cells x Phi applications executed on the GPU */
+    int stagnated;        /* 1 if an FP32-sweep solve stopped on stagnation */
 } mgrit_stats;
 
 /* Fill *p with the defaults listed in mgrit_params. */
@@ -129,6 +136,7 @@ int mgrit_copy_cpoints(mgrit_ctx *ctx, double *uC_out_dev, void *stream);
 /*
  * Sequential fine time-stepping: uT_dev = Phi_0^nsteps(u0_dev), i.e. forward
  * substitution of Eq. (monolithicSystem).  Baseline for time-to-tolerance.
+ * Steps in the context's sweep precision (FP32 rounds u0 once on entry).
  * u0_dev and uT_dev hold nx values and may alias.  Asynchronous.
  */
 int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *uT_dev, int nsteps,
@@ -137,8 +145,10 @@ int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *uT_dev, int 
 /*
  * Level-0 residual 2-norm of given C-point states uC_dev ((nt/m+1) x nx):
  *   ||r||_2,  r^i = Phi_0^m(u^{m(i-1)}) - u^{mi},  i = 1..nt/m
- * (the fine-level residual of the Schur system, Eq. schurComplement).
- * Writes the host double *norm_out; synchronises `stream`.
+ * (the fine-level residual of the Schur system, Eq. schurComplement),
+ * always with the FP64 operator (also for an FP32-sweep context, so it
+ * measures FP32 results against the FP64 discrete system).  Requires nx to
+ * fit an FP64 slab.  Writes the host double *norm_out; synchronises `stream`.
  */
 int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void *stream);
 

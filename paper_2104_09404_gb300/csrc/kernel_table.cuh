@@ -1,16 +1,19 @@
-// Table of slab-kernel instances, indexed by [scheme][flux][cells-per-thread].
+// Table of kernel instances, indexed by [scheme][flux][cells-per-thread].
 #pragma once
 #include "cluster_seq.cuh"
 
 namespace mgrit {
 
-constexpr int NCPT = 5;
-constexpr int CPT_VALUES[NCPT] = {1, 2, 4, 8, 16};
+constexpr int NCPT = 6;
+constexpr int CPT_VALUES[NCPT] = {1, 2, 4, 8, 16, 32};
+constexpr int NCPT64 = 5;          // FP64 slabs stop at 16 cells per thread (nx <= 8192)
 constexpr int MAX_THREADS = 512;   // matches __launch_bounds__ of k_slab
 
 struct KernelTable {
     const void *slab64[2][2][NCPT];
+    const void *slab32[2][2][NCPT];
     const void *seqc64[2][2][2];   // k_seq_cluster, cells per thread 1 or 2
+    const void *seqc32[2][2][2];
 };
 
 template <typename R, int S, int F>
@@ -21,6 +24,13 @@ void fill_sf(const void *(&t)[2][2][NCPT])
     t[S][F][2] = (const void *)&k_slab<R, S, F, 4>;
     t[S][F][3] = (const void *)&k_slab<R, S, F, 8>;
     t[S][F][4] = (const void *)&k_slab<R, S, F, 16>;
+}
+
+template <int S, int F>
+void fill_sf32(const void *(&t)[2][2][NCPT])
+{
+    fill_sf<float, S, F>(t);
+    t[S][F][5] = (const void *)&k_slab<float, S, F, 32>;
 }
 
 template <typename R, int S, int F>
@@ -34,5 +44,18 @@ void fill_cluster(const void *(&t)[2][2][2])
 void fill_f64_weno_burgers(KernelTable &t);
 void fill_f64_weno_advection(KernelTable &t);
 void fill_f64_fo(KernelTable &t);
+void fill_f32_weno_burgers(KernelTable &t);
+void fill_f32_weno_advection(KernelTable &t);
+void fill_f32_fo(KernelTable &t);
+
+inline void fill_all(KernelTable &t)
+{
+    fill_f64_weno_burgers(t);
+    fill_f64_weno_advection(t);
+    fill_f64_fo(t);
+    fill_f32_weno_burgers(t);
+    fill_f32_weno_advection(t);
+    fill_f32_fo(t);
+}
 
 }  // namespace mgrit

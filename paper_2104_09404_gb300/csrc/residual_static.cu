@@ -53,10 +53,8 @@ const void *select_slab(int nx, int scheme, int flux, int *threads)
 {
     KernelTable t;
     memset(&t, 0, sizeof t);
-    fill_f64_weno_burgers(t);
-    fill_f64_weno_advection(t);
-    fill_f64_fo(t);
-    for (int ci = 0; ci < NCPT; ++ci) {
+    fill_all(t);
+    for (int ci = 0; ci < NCPT64; ++ci) {
         const int need = (nx + CPT_VALUES[ci] - 1) / CPT_VALUES[ci];
         if (need <= MAX_THREADS) {
             *threads = ((need + 31) / 32) * 32;

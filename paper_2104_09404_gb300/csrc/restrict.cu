@@ -15,9 +15,17 @@
 
 namespace mgrit {
 
+// S: precision of the relaxation outputs; U: precision of the next level's
+// state rows.  Every sum is formed in FP64 (the tau-correction of the FAS
+// right-hand side, the residual and its norm stay FP64 in FP32-sweep mode).
+template <typename S, typename U>
 __global__ void __launch_bounds__(RESTRICT_THREADS) k_restrict(RestrictArgs a)
 {
     __shared__ double red[RESTRICT_THREADS / 32];
+    const S *newC = static_cast<const S *>(a.newC);
+    const S *phirow = static_cast<const S *>(a.phirow);
+    const S *cstep = static_cast<const S *>(a.cstep);
+    U *un = static_cast<U *>(a.un);
     const long long n = (long long)a.nC * a.nx;
     double acc = 0.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -32,13 +40,13 @@ __global__ void __launch_bounds__(RESTRICT_THREADS) k_restrict(RestrictArgs a)
         }
 #endif
         const double gl = a.g ? a.g[(long long)a.m * i * a.nx + c] : 0.0;
-        const double phi = a.phirow[at];
-        const double uc = a.newC[at];
+        const double phi = (double)phirow[at];
+        const double uc = (double)newC[at];
         const double r = phi + gl - uc;
         acc += r * r;
-        if (a.cstep) {
-            a.gn[at] = gl + phi - a.cstep[(i - 1) * a.nx + c];
-            a.un[at] = a.guess == 0 ? phi + gl : uc;
+        if (cstep) {
+            a.gn[at] = gl + phi - (double)cstep[(i - 1) * a.nx + c];
+            un[at] = (U)(a.guess == 0 ? phi + gl : uc);
         }
     }
     if (a.partials) {
@@ -69,13 +77,30 @@ __global__ void __launch_bounds__(256) k_norm(const double *partials, int n, dou
     if (threadIdx.x == 0) *out = sqrt(red[0]);
 }
 
-// rows [0, nrows) of dst = src
-__global__ void k_broadcast_row(const double *src, double *dst, int nx, long long nrows)
+// rows [0, nrows) of dst = src (one FP64 row), converted to T
+template <typename T>
+__global__ void k_broadcast_row(const double *src, T *dst, int nx, long long nrows)
 {
     const long long n = nrows * nx;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
-        dst[e] = src[e % nx];
+        dst[e] = (T)src[e % nx];
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A *src, B *dst, long long n)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        dst[e] = (B)src[e];
+}
+
+static int stream_blocks(long long n)
+{
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
 }
 
 int restrict_blocks(int nC, int nx)
@@ -90,7 +115,12 @@ int restrict_blocks(int nC, int nx)
 
 cudaError_t launch_restrict(const RestrictArgs &a, int blocks, cudaStream_t s)
 {
-    k_restrict<<<blocks, RESTRICT_THREADS, 0, s>>>(a);
+    if (!a.state_f32)
+        k_restrict<double, double><<<blocks, RESTRICT_THREADS, 0, s>>>(a);
+    else if (a.un_f32)
+        k_restrict<float, float><<<blocks, RESTRICT_THREADS, 0, s>>>(a);
+    else
+        k_restrict<float, double><<<blocks, RESTRICT_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -100,14 +130,33 @@ cudaError_t launch_norm(const double *partials, int n, double *out, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_broadcast_row(const double *src, double *dst, int nx, long long nrows,
-                                 cudaStream_t s)
+cudaError_t launch_broadcast_row(const double *src, void *dst, int dst_f32, int nx,
+                                 long long nrows, cudaStream_t s)
 {
-    long long n = nrows * nx;
-    long long b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    k_broadcast_row<<<(int)b, 256, 0, s>>>(src, dst, nx, nrows);
+    const int b = stream_blocks(nrows * nx);
+    if (dst_f32)
+        k_broadcast_row<float><<<b, 256, 0, s>>>(src, static_cast<float *>(dst), nx, nrows);
+    else
+        k_broadcast_row<double><<<b, 256, 0, s>>>(src, static_cast<double *>(dst), nx, nrows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void *src, int src_f32, void *dst, int dst_f32, long long n,
+                           cudaStream_t s)
+{
+    const int b = stream_blocks(n);
+    if (src_f32 && dst_f32)
+        k_convert<float, float><<<b, 256, 0, s>>>(static_cast<const float *>(src),
+                                                  static_cast<float *>(dst), n);
+    else if (src_f32)
+        k_convert<float, double><<<b, 256, 0, s>>>(static_cast<const float *>(src),
+                                                   static_cast<double *>(dst), n);
+    else if (dst_f32)
+        k_convert<double, float><<<b, 256, 0, s>>>(static_cast<const double *>(src),
+                                                   static_cast<float *>(dst), n);
+    else
+        k_convert<double, double><<<b, 256, 0, s>>>(static_cast<const double *>(src),
+                                                    static_cast<double *>(dst), n);
     return cudaGetLastError();
 }
 

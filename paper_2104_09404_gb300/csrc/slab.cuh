@@ -126,6 +126,8 @@ struct Slab {
         red = qf + (nx + 2 * GHOST);
     }
 
+    static constexpr int RECON_UNROLL = sizeof(R) == 4 ? 1 : CPT;
+
     __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
     __device__ __forceinline__ int lim() const { return nx + 2 * GHOST; }   // extent of qa, qb, qf
 
@@ -182,7 +184,9 @@ struct Slab {
                 }
             }
             __syncthreads();
-#pragma unroll
+            // this loop touches no register array, so FP32 slabs keep it rolled
+            // (fewer live registers for 16-32 cells per thread); FP64 unrolls it
+#pragma unroll(RECON_UNROLL)
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) put_flux(i, rec_minus(qa, i + GHOST) + rec_plus(qb, i + GHOST));

@@ -33,7 +33,7 @@ class mgrit_params(ctypes.Structure):
 class mgrit_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("res_hist", ctypes.c_double * 256), ("t_total_ms", ctypes.c_double),
-                ("cell_updates", ctypes.c_double)]
+                ("cell_updates", ctypes.c_double), ("stagnated", ctypes.c_int)]
 
 
 _lib = None

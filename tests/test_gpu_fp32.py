@@ -1,0 +1,139 @@
+"""FP32-sweep mode (precision = 32): relaxation and interpolation in FP32,
+FP64 tau-correction, residual, norm and coarsest solve.  Results are compared
+with the FP64 oracle within the stated FP32 bounds:
+  relative max-norm error <= 1e-4 and relative L1 error <= 5e-5
+for the CFL-stable cases below (up to ~500 steps).  FP32 rounding is ~6e-8 per operation; a few
+hundred steps accumulate ~1e-6 relative in smooth regions, and up to ~5e-5
+next to a shock, where the WENO weights amplify rounding of the smoothness
+indicators (measured: 5.1e-5 max / 5.5e-6 L1 for 256 steps past shock
+formation; 4.6e-5 max / 1.5e-5 L1 for 512 steps at nx = 16384, roughly
+n x 6e-8 for n steps)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2104_09404_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MAX_REL = 1e-4
+L1_REL = 5e-5
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_09404_gb300 import build as B, mgrit
+    B.build()
+    mgrit.load()
+    return mgrit
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def errs(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    mx = np.abs(got - ref).max() / np.abs(ref).max()
+    l1 = np.abs(got - ref).sum() / np.abs(ref).sum()
+    return mx, l1
+
+
+@pytest.mark.parametrize("nx,scheme,flux,numflux,nsteps,cfl", [
+    (128, 0, 0, 0, 256, 0.3),
+    (1000, 0, 1, 0, 64, 0.5),
+    (4096, 0, 0, 0, 64, 0.4),
+    (777, 0, 0, 1, 40, 0.4),
+    (300, 1, 0, 0, 100, 0.5),
+    (16384, 0, 0, 0, 8, 0.3),
+])
+def test_fp32_serial_against_fp64_oracle(M, nx, scheme, flux, numflux, nsteps, cfl):
+    u0 = inputs.fourier_ic(nx, seed=nx)
+    speed = np.abs(u0).max() if flux == 0 else 1.0
+    T = cfl * nsteps / (nx * speed)
+    s = M.Solver(nx, nsteps, 2, 2, scheme, flux, T=T, numflux=numflux, precision=32)
+    out = s.serial_step(dev(u0), nsteps).cpu().numpy()
+    ref = O.serial(u0, T / nsteps, nsteps, scheme, flux, numflux)
+    mx, l1 = errs(out, ref)
+    print("fp32 serial nx=%d: max %.2e L1 %.2e" % (nx, mx, l1))
+    assert mx <= MAX_REL and l1 <= L1_REL
+
+
+@pytest.mark.parametrize("nx,nt,m,L,T,kw", [
+    (128, 256, 4, 2, 0.25, {}),
+    (64, 256, 2, 3, 0.2, {}),
+    (256, 1024, 4, 3, 0.05, {}),
+    (96, 256, 4, 2, 0.1, dict(scheme=1)),
+    (100, 128, 4, 3, 0.1, dict(flux=1)),
+])
+def test_fp32_mgrit_against_fp64_oracle(M, nx, nt, m, L, T, kw):
+    u0 = inputs.sine_ic(nx) if nx in (128, 64) else inputs.fourier_ic(nx, seed=nx)
+    scheme, flux = kw.get("scheme", 0), kw.get("flux", 0)
+    s = M.Solver(nx, nt, m, L, scheme, flux, T=T, precision=32, max_iter=60)
+    st, uT, uC, stats = s.solve(dev(u0))
+    assert st == M.OK
+    ref = O.mgrit(u0, nt, m, L, T, scheme=scheme, flux=flux, tol=1e-10, max_iter=60)
+    assert ref["status"] == O.OK
+    mx, l1 = errs(uC.cpu().numpy(), ref["uC"])
+    print("fp32 mgrit nx=%d L=%d: %d cycles (stagnated %d, r=%.2e), max %.2e L1 %.2e"
+          % (nx, L, stats.iters, stats.stagnated, stats.res_hist[stats.iters], mx, l1))
+    assert mx <= MAX_REL and l1 <= L1_REL
+    # the FP64 residual of the FP32 result is at FP32 rounding level
+    assert s.residual(uC) < 1e-4
+
+
+def test_fp32_mgrit_converges_to_fp32_serial(M):
+    nx, nt, m, L, T = 128, 256, 4, 2, 0.25
+    u0 = dev(inputs.sine_ic(nx))
+    s = M.Solver(nx, nt, m, L, T=T, precision=32)
+    st, uT, _, stats = s.solve(u0)
+    ser = s.serial_step(u0, nt)
+    torch.cuda.synchronize()
+    assert st == M.OK
+    assert float((uT - ser).abs().max()) < 5e-5
+
+
+def test_precision_switch_on_one_context(M):
+    nx, nt, m, L, T = 64, 256, 2, 3, 0.2
+    u0 = inputs.sine_ic(nx)
+    s = M.Solver(nx, nt, m, L, T=T)
+    st64, _, uC64, _ = s.solve(dev(u0))
+    s.set_params(precision=32)
+    st32, _, uC32, stats32 = s.solve(dev(u0))
+    s.set_params(precision=64)
+    st64b, _, uC64b, _ = s.solve(dev(u0))
+    assert st64 == st32 == st64b == M.OK
+    assert torch.equal(uC64, uC64b)
+    ref = O.mgrit(u0, nt, m, L, T)
+    assert np.abs(uC64.cpu().numpy() - ref["uC"]).max() <= 1e-11 * np.abs(ref["uC"]).max()
+    assert errs(uC32.cpu().numpy(), ref["uC"])[0] <= MAX_REL
+
+
+def test_fp32_only_size_refuses_fp64(M):
+    # nx = 16384 fits one CTA only in FP32 (its FP64 coarsest solve runs on a
+    # thread-block cluster): FP64 sweeps are refused with a clear error
+    T = 64 * 0.3 / 16384
+    s = M.Solver(16384, 64, 8, 2, T=T, precision=32)
+    with pytest.raises(M.MGRITError):
+        s.set_params(precision=64)
+    with pytest.raises(M.MGRITError):
+        M.Solver(16384, 64, 8, 2, T=T)          # default FP64 sweeps
+
+
+def test_fp32_large_slab_mgrit_small_horizon(M):
+    # the mixed-precision shape (nx = 16384, m = 8, 3 levels) on a short
+    # horizon, with the coarsest CFL kept at 0.77 (fine CFL 0.012)
+    nx, nt, m, L = 16384, 512, 8, 3
+    u0 = inputs.sine_ic(nx)
+    T = 0.012 * nt / (nx * np.abs(u0).max())
+    s = M.Solver(nx, nt, m, L, T=T, precision=32, max_iter=30)
+    st, uT, uC, stats = s.solve(dev(u0))
+    assert st == M.OK
+    # reference: FP64 oracle serial stepping to T (512 steps at nx 16384)
+    ref = O.serial(u0, T / nt, nt)
+    mx, l1 = errs(uT.cpu().numpy(), ref)
+    print("fp32 c4-shape: %d cycles, max %.2e L1 %.2e" % (stats.iters, mx, l1))
+    assert mx <= MAX_REL and l1 <= L1_REL
