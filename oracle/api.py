@@ -53,6 +53,12 @@ def _load():
         lib.orc_residual.argtypes = [I, I, I, I, I, I, D, D, P, P]
         lib.orc_vcycles.restype = I
         lib.orc_vcycles.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, P, P, P]
+        lib.orc_weno5_left_grad.restype = None
+        lib.orc_weno5_left_grad.argtypes = [P, P]
+        lib.orc_step_vjp.restype = None
+        lib.orc_step_vjp.argtypes = [I, D, D, I, I, P, P, P]
+        lib.orc_adjoint_serial.restype = None
+        lib.orc_adjoint_serial.argtypes = [I, D, D, I, I, I, P, P, P]
         lib.orc_num_threads.restype = I
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -154,3 +160,28 @@ def vcycles(u0, nt, m, levels, T, ncycles, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX
     if st != OK:
         raise ValueError("orc_vcycles: invalid arguments")
     return uC, hist[:ncycles]
+
+
+def weno5_left_grad(q5):
+    """d q^-_{i+1/2} / d q_{i-2..i+2}."""
+    q = _f64(q5)
+    g = np.zeros(5)
+    _load().orc_weno5_left_grad(_ptr(q), _ptr(g))
+    return g
+
+
+def step_vjp(u, lam, dt, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS, Lx=1.0):
+    """Phi'(u)^T lam for one step (split numerical flux)."""
+    u, lam = _f64(u), _f64(lam)
+    out = np.zeros_like(u)
+    _load().orc_step_vjp(u.size, Lx, dt, scheme, flux, _ptr(u), _ptr(lam), _ptr(out))
+    return out
+
+
+def adjoint_serial(u0, lamT, dt, nsteps, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS, Lx=1.0):
+    """dJ/du0 given dJ/du(T) = lamT, through nsteps serial steps."""
+    u0, lamT = _f64(u0), _f64(lamT)
+    out = np.zeros_like(u0)
+    _load().orc_adjoint_serial(u0.size, Lx, dt, nsteps, scheme, flux, _ptr(u0), _ptr(lamT),
+                               _ptr(out))
+    return out

@@ -225,6 +225,168 @@ static void phi_step(int nx, double dx, double dt, int scheme, int flux, int num
 }
 
 /* ====================================================================== */
+/* Discrete adjoint of the stepper (vector-Jacobian products), by the     */
+/* chain rule through Eq. (SSPRK3)/(SSPRK1), Eq. (spaceDisc), the global  */
+/* Lax-Friedrichs splitting and the WENO weights of Eqs. (C),(B),(omega).  */
+/* The paper has no adjoint; this is the gradient of J(u^{nt}) with       */
+/* respect to u^0 for the discrete scheme above (split numerical flux).   */
+/* ====================================================================== */
+
+/* d q^-_{i+1/2} / d q[k], k = 0..4, for the reconstruction weno5_left:
+ *   W = sum_r w_r p_r, w_r = a_r / sum a, a_r = d_r/(eps + beta_r)^2
+ *   dW = sum_r w_r dp_r + (1/sum a) sum_r (p_r - W) da_r,
+ *   da_r = -2 d_r/(eps + beta_r)^3 dbeta_r, dbeta_r = (B_r + B_r^T) s / 6 */
+static void weno5_left_grad(const double q[5], double grad[5])
+{
+    double p[3], beta[3], alpha[3], dadb[3], asum = 0.0, w = 0.0;
+    double dp[3][5], db[3][5];
+    memset(dp, 0, sizeof dp);
+    memset(db, 0, sizeof db);
+    for (int r = 0; r < 3; ++r) {
+        const double *s = &q[2 - r];
+        p[r] = (TAB_C[r][0] * s[0] + TAB_C[r][1] * s[1] + TAB_C[r][2] * s[2]) / 6.0;
+        double qf = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                qf += s[a] * TAB_B[r][a][b] * s[b];
+        beta[r] = qf / 6.0;
+        for (int a = 0; a < 3; ++a) {
+            dp[r][2 - r + a] = TAB_C[r][a] / 6.0;
+            double g = 0.0;
+            for (int b = 0; b < 3; ++b) g += (TAB_B[r][a][b] + TAB_B[r][b][a]) * s[b];
+            db[r][2 - r + a] = g / 6.0;
+        }
+        double den = WENO_EPS + beta[r];
+        alpha[r] = (TAB_D[r] / 10.0) / (den * den);
+        dadb[r] = -2.0 * (TAB_D[r] / 10.0) / (den * den * den);
+        asum += alpha[r];
+    }
+    for (int r = 0; r < 3; ++r) w += alpha[r] / asum * p[r];
+    for (int k = 0; k < 5; ++k) {
+        double g = 0.0;
+        for (int r = 0; r < 3; ++r)
+            g += alpha[r] / asum * dp[r][k] + (p[r] - w) * dadb[r] * db[r][k] / asum;
+        grad[k] = g;
+    }
+}
+
+/* out += A'(w)^T mu for the split numerical flux (alpha = max|f'(w_j)|,
+ * differentiated at its first maximiser) */
+static void spatial_op_vjp(int nx, double dx, int scheme, int flux, const double *w,
+                           const double *mu, double *out, double *work /* 5*nx */)
+{
+    int k = scheme_k(scheme);
+    double *fp = work, *fm = work + nx, *muF = work + 2 * nx, *mufp = work + 3 * nx,
+           *mufm = work + 4 * nx;
+    double alpha = 0.0;
+    int kstar = -1;
+    for (int j = 0; j < nx; ++j) {
+        double sp = fabs(phys_speed(flux, w[j]));
+        if (sp > alpha) { alpha = sp; kstar = j; }
+    }
+    for (int j = 0; j < nx; ++j) {
+        fp[j] = 0.5 * (phys_flux(flux, w[j]) + alpha * w[j]);
+        fm[j] = 0.5 * (phys_flux(flux, w[j]) - alpha * w[j]);
+        mufp[j] = mufm[j] = 0.0;
+    }
+    /* A_i = -(F_i - F_{i-1})/dx with F_i = F_{i+1/2} */
+    for (int i = 0; i < nx; ++i) muF[i] = (mu[wrap(i + 1, nx)] - mu[i]) / dx;
+    for (int i = 0; i < nx; ++i) {
+        if (k == 0) {
+            mufp[i] += muF[i];
+            mufm[wrap(i + 1, nx)] += muF[i];
+            continue;
+        }
+        double s[5], g[5];
+        for (int j = 0; j < 5; ++j) s[j] = fp[wrap(i - 2 + j, nx)];
+        weno5_left_grad(s, g);
+        for (int j = 0; j < 5; ++j) mufp[wrap(i - 2 + j, nx)] += muF[i] * g[j];
+        for (int j = 0; j < 5; ++j) s[j] = fm[wrap(i + 3 - j, nx)];
+        weno5_left_grad(s, g);
+        for (int j = 0; j < 5; ++j) mufm[wrap(i + 3 - j, nx)] += muF[i] * g[j];
+    }
+    double mualpha = 0.0;
+    for (int j = 0; j < nx; ++j) {
+        double fprime = flux == ORC_FLUX_BURGERS ? w[j] : 1.0;
+        out[j] += mufp[j] * 0.5 * (fprime + alpha) + mufm[j] * 0.5 * (fprime - alpha);
+        mualpha += 0.5 * w[j] * (mufp[j] - mufm[j]);
+    }
+    if (flux == ORC_FLUX_BURGERS && kstar >= 0 && w[kstar] != 0.0)
+        out[kstar] += mualpha * (w[kstar] > 0.0 ? 1.0 : -1.0);
+}
+
+/* lam_out = Phi'(u)^T lam (step dt) */
+static void phi_step_vjp(int nx, double dx, double dt, int scheme, int flux, const double *u,
+                         const double *lam, double *lam_out, double *work /* 12*nx */)
+{
+    double *A = work, *u1 = work + nx, *u2 = work + 2 * nx, *t = work + 3 * nx,
+           *l2 = work + 4 * nx, *l1 = work + 5 * nx, *w5 = work + 6 * nx, *w3 = work + 11 * nx;
+    (void)w3;
+    if (scheme == ORC_SCHEME_FO_FE) {
+        for (int i = 0; i < nx; ++i) { lam_out[i] = lam[i]; t[i] = dt * lam[i]; }
+        spatial_op_vjp(nx, dx, scheme, flux, u, t, lam_out, w5);
+        return;
+    }
+    /* forward stages (Eq. SSPRK3) */
+    spatial_op(nx, dx, scheme, flux, ORC_NUMFLUX_LF_SPLIT, u, A, w5);
+    for (int i = 0; i < nx; ++i) u1[i] = u[i] + dt * A[i];
+    spatial_op(nx, dx, scheme, flux, ORC_NUMFLUX_LF_SPLIT, u1, A, w5);
+    for (int i = 0; i < nx; ++i)
+        u2[i] = 3.0 / 4.0 * u[i] + 1.0 / 4.0 * u1[i] + 1.0 / 4.0 * dt * A[i];
+    /* stage 3: out = u/3 + 2/3 u2 + 2/3 dt A(u2) */
+    for (int i = 0; i < nx; ++i) {
+        lam_out[i] = 1.0 / 3.0 * lam[i];
+        l2[i] = 2.0 / 3.0 * lam[i];
+        t[i] = 2.0 / 3.0 * dt * lam[i];
+    }
+    spatial_op_vjp(nx, dx, scheme, flux, u2, t, l2, w5);
+    /* stage 2: u2 = 3/4 u + 1/4 u1 + 1/4 dt A(u1) */
+    for (int i = 0; i < nx; ++i) {
+        lam_out[i] += 3.0 / 4.0 * l2[i];
+        l1[i] = 1.0 / 4.0 * l2[i];
+        t[i] = 1.0 / 4.0 * dt * l2[i];
+    }
+    spatial_op_vjp(nx, dx, scheme, flux, u1, t, l1, w5);
+    /* stage 1: u1 = u + dt A(u) */
+    for (int i = 0; i < nx; ++i) {
+        lam_out[i] += l1[i];
+        t[i] = dt * l1[i];
+    }
+    spatial_op_vjp(nx, dx, scheme, flux, u, t, lam_out, w5);
+}
+
+void orc_weno5_left_grad(const double *q5, double *grad5) { weno5_left_grad(q5, grad5); }
+
+void orc_step_vjp(int nx, double Lx, double dt, int scheme, int flux, const double *u,
+                  const double *lam, double *lam_out)
+{
+    double *work = malloc(sizeof(double) * 12 * (size_t)nx);
+    phi_step_vjp(nx, Lx / nx, dt, scheme, flux, u, lam, lam_out, work);
+    free(work);
+}
+
+/* dJ/du^0 for J = J(u^{nsteps}) given lamT = dJ/du^{nsteps}: forward serial
+ * stepping stores every state, then lam^n = Phi'(u^n)^T lam^{n+1}. */
+void orc_adjoint_serial(int nx, double Lx, double dt, int nsteps, int scheme, int flux,
+                        const double *u0, const double *lamT, double *lam0)
+{
+    double *traj = malloc(sizeof(double) * (size_t)(nsteps + 1) * nx);
+    double *work = malloc(sizeof(double) * 12 * (size_t)nx);
+    double *a = malloc(sizeof(double) * (size_t)nx), *b = malloc(sizeof(double) * (size_t)nx);
+    memcpy(traj, u0, sizeof(double) * (size_t)nx);
+    for (int n = 0; n < nsteps; ++n)
+        phi_step(nx, Lx / nx, dt, scheme, flux, ORC_NUMFLUX_LF_SPLIT, traj + (size_t)n * nx,
+                 traj + (size_t)(n + 1) * nx, work);
+    memcpy(a, lamT, sizeof(double) * (size_t)nx);
+    for (int n = nsteps - 1; n >= 0; --n) {
+        phi_step_vjp(nx, Lx / nx, dt, scheme, flux, traj + (size_t)n * nx, a, b, work);
+        double *t = a; a = b; b = t;
+    }
+    memcpy(lam0, a, sizeof(double) * (size_t)nx);
+    free(traj); free(work); free(a); free(b);
+}
+
+/* ====================================================================== */
 /* Exported single-step pieces (pinned individually by the tests).        */
 /* ====================================================================== */
 
