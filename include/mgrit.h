@@ -205,6 +205,61 @@ int mgrit_query(const mgrit_ctx *ctx, int what);
 /* Cells x Phi applications of one V-cycle (for throughput figures). */
 double mgrit_cycle_cell_updates(const mgrit_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems advanced together (the paper treats
+ * one problem at a time; batching is a throughput feature of this library).
+ * Every instance has its own nx, nt, m, levels, flux and T (WENO5/SSPRK3
+ * only); the other parameters are shared.  Each phase of the V-cycle is one
+ * launch per launch class (flux x CTA shape) over the work items of all
+ * instances, and a cycle is two CUDA graphs, as for one instance.
+ * ------------------------------------------------------------------------ */
+typedef struct mgrit_batch mgrit_batch;
+
+typedef struct {
+    int nx, nt, m, levels;   /* as in mgrit_create */
+    int scheme;              /* MGRIT_WENO5_SSPRK3 */
+    int flux;                /* MGRIT_BURGERS / MGRIT_ADVECTION */
+    double T;                /* final time of this instance */
+} mgrit_instance;
+
+/* Create a batch of n instances (nx <= 8192 each; params may be NULL for
+ * defaults; params->T is ignored, each instance has its own).  Allocates
+ * every instance's workspaces on the current device and captures the
+ * graphs.  MGRIT_EINVAL names the offending instance in mgrit_last_error(NULL). */
+int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst, int n,
+                       const mgrit_params *params);
+
+/* Exactly ncycles V-cycles of every instance from u0_dev[i] (host array of n
+ * device pointers).  Asynchronous. */
+int mgrit_batch_run_cycles(mgrit_batch *b, const double *const *u0_dev, int ncycles, void *stream);
+
+/* Solve every instance with the stopping rules of mgrit_solve, applied per
+ * instance; an instance that has stopped is masked out on the device while
+ * the others continue.  uT_dev[i] (may be NULL) receives u(T) of instance i;
+ * status[i], iters[i], final_res[i] (each may be NULL) the per-instance
+ * outcome.  Synchronises `stream` once per cycle. */
+int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const *uT_dev,
+                      int *status, int *iters, double *final_res, void *stream);
+
+/* Autotuner: for each group of instances with equal (flux, nx), time the
+ * level-0 relaxation with 1x, 2x and 4x the minimal cells per thread and
+ * keep the fastest CTA shape; the graphs are rebuilt.  reps >= 1 timed
+ * launches per candidate.  Synchronises `stream`. */
+int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, void *stream);
+
+/* Cells x Phi applications of one V-cycle of all instances. */
+double mgrit_batch_cycle_cell_updates(const mgrit_batch *b);
+
+/* what = 0: cells per thread, 1: threads per CTA, 2: levels of instance i. */
+int mgrit_batch_query(const mgrit_batch *b, int instance, int what);
+
+/* C-points of instance i after its last level-0 relaxation (as
+ * mgrit_copy_cpoints). */
+int mgrit_batch_copy_cpoints(mgrit_batch *b, int instance, double *uC_out_dev, void *stream);
+
+const char *mgrit_batch_last_error(const mgrit_batch *b);
+void mgrit_batch_destroy(mgrit_batch *b);
+
 /* One-line description of the last error on ctx (or of the last failed
  * mgrit_create when ctx is NULL). */
 const char *mgrit_last_error(const mgrit_ctx *ctx);

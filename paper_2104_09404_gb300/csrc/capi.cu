@@ -44,6 +44,7 @@ struct Launch {
 struct ClusterLaunch {
     const void *fn;     // k_seq_cluster instance; null: single-CTA k_slab
     int K;              // CTAs in the cluster
+    int cpt;            // cells per thread (1 or 2)
     int threads;
     size_t smem;
 };
@@ -329,6 +330,7 @@ static void choose_cluster(mgrit_ctx *ctx, int f32, ClusterLaunch *lc)
         }
         lc->fn = fn;
         lc->K = K;
+        lc->cpt = cpt;
         lc->threads = threads;
         lc->smem = smem;
         return;
@@ -427,8 +429,10 @@ static const void *cpoint_source(const mgrit_ctx *ctx, int l)
     return ctx->u[l];
 }
 
+// argument blocks of the level kernels (shared by the single-instance graphs
+// and the batched launches)
 template <typename R>
-static cudaError_t enqueue_relax_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln)
+static SlabArgs<R> relax_args(const mgrit_ctx *ctx, int l)
 {
     SlabArgs<R> a = base_args<R>(ctx, MODE_RELAX, l);
     a.uC = static_cast<const R *>(cpoint_source(ctx, l));
@@ -440,16 +444,10 @@ static cudaError_t enqueue_relax_t(mgrit_ctx *ctx, int l, cudaStream_t s, const 
     a.nrows_uC = a.nrows_newC = a.nrows_phirow = a.nC + 1;
     a.nrows_cstep = a.nC;
     a.nrows_g = ctx->nt_l[l] + 1;
-    return launch1(ln.slab, a.nC + 1, ln, s, &a);
+    return a;
 }
 
-static cudaError_t enqueue_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
-{
-    return ctx->f32 ? enqueue_relax_t<float>(ctx, l, s, ctx->ln32)
-                    : enqueue_relax_t<double>(ctx, l, s, ctx->ln64);
-}
-
-static cudaError_t enqueue_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
+static RestrictArgs restrict_args(const mgrit_ctx *ctx, int l)
 {
     RestrictArgs a;
     memset(&a, 0, sizeof a);
@@ -467,6 +465,50 @@ static cudaError_t enqueue_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
     a.guess = ctx->p.guess;
     a.state_f32 = ctx->f32;
     a.un_f32 = level_f32(ctx, l + 1);
+    return a;
+}
+
+static SlabArgs<double> coarse_args(const mgrit_ctx *ctx)
+{
+    const int l = ctx->L - 1;
+    SlabArgs<double> a = base_args<double>(ctx, MODE_SEQ, l);
+    a.src = ctx->g[l];
+    a.g = ctx->g[l];
+    a.rows = static_cast<double *>(ctx->u[l]);
+    a.nsteps = ctx->nt_l[l];
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    return a;
+}
+
+template <typename R>
+static SlabArgs<R> interp_args(const mgrit_ctx *ctx, int l)
+{
+    SlabArgs<R> a = base_args<R>(ctx, MODE_INTERP, l);
+    const void *coarse = (l + 1 == ctx->L - 1 && ctx->f32) ? (const void *)ctx->u32c : ctx->u[l + 1];
+    a.uC = static_cast<const R *>(coarse);
+    a.g = ctx->g[l];
+    a.rows = static_cast<R *>(ctx->u[l]);
+    a.nrows_uC = a.nC + 1;
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    return a;
+}
+
+template <typename R>
+static cudaError_t enqueue_relax_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln)
+{
+    SlabArgs<R> a = relax_args<R>(ctx, l);
+    return launch1(ln.slab, a.nC + 1, ln, s, &a);
+}
+
+static cudaError_t enqueue_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
+{
+    return ctx->f32 ? enqueue_relax_t<float>(ctx, l, s, ctx->ln32)
+                    : enqueue_relax_t<double>(ctx, l, s, ctx->ln64);
+}
+
+static cudaError_t enqueue_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
+{
+    RestrictArgs a = restrict_args(ctx, l);
     const int blocks = l == 0 ? ctx->nparts : restrict_blocks(a.nC, a.nx);
     return launch_restrict(a, blocks, s);
 }
@@ -476,12 +518,7 @@ static cudaError_t enqueue_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
 static cudaError_t enqueue_coarse(mgrit_ctx *ctx, cudaStream_t s)
 {
     const int l = ctx->L - 1;
-    SlabArgs<double> a = base_args<double>(ctx, MODE_SEQ, l);
-    a.src = ctx->g[l];
-    a.g = ctx->g[l];
-    a.rows = static_cast<double *>(ctx->u[l]);
-    a.nsteps = ctx->nt_l[l];
-    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    SlabArgs<double> a = coarse_args(ctx);
     cudaError_t e = launch_seq(ctx->lc64, ctx->ln64, s, &a);
     if (e != cudaSuccess || !ctx->f32) return e;
     return launch_convert(ctx->u[l], 0, ctx->u32c, 1, (long long)(ctx->nt_l[l] + 1) * ctx->nx, s);
@@ -490,13 +527,7 @@ static cudaError_t enqueue_coarse(mgrit_ctx *ctx, cudaStream_t s)
 template <typename R>
 static cudaError_t enqueue_interp_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln)
 {
-    SlabArgs<R> a = base_args<R>(ctx, MODE_INTERP, l);
-    const void *coarse = (l + 1 == ctx->L - 1 && ctx->f32) ? (const void *)ctx->u32c : ctx->u[l + 1];
-    a.uC = static_cast<const R *>(coarse);
-    a.g = ctx->g[l];
-    a.rows = static_cast<R *>(ctx->u[l]);
-    a.nrows_uC = a.nC + 1;
-    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    SlabArgs<R> a = interp_args<R>(ctx, l);
     return launch1(ln.slab, a.nC, ln, s, &a);
 }
 
@@ -804,4 +835,632 @@ extern "C" void mgrit_destroy(mgrit_ctx *ctx)
     if (!ctx) return;
     free_workspaces(ctx);
     delete ctx;
+}
+
+// ===========================================================================
+// Batches: many independent instances (uneven nx, nt, levels, flux) advanced
+// together.  Each instance keeps its own level workspaces (an mgrit_ctx);
+// every phase of the V-cycle is one batched launch per launch class, with a
+// block map telling each CTA its instance and chunk.  Phases are ordered by
+// level depth: relaxation + restriction of depth d for every instance that
+// has a level d below its coarsest, then every coarsest solve, then the
+// interpolations from the deepest depth up.  A device-side mask lets
+// converged instances skip all work while the others continue.
+// ===========================================================================
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "batch_table.cuh"
+
+namespace {
+
+struct BLaunch {
+    int kind;           // 0 slab kernel, 1 restriction, 2 norm, 3 FP64 -> FP32 conversion,
+                        // 4 cluster sequential kernel (un_f32 holds the cluster size)
+    const void *fn;     // slab kernel instance
+    int threads;
+    size_t smem;
+    int nblocks;
+    int state_f32, un_f32;
+    void *d_args;
+    BatchItem *d_map;
+};
+
+const BatchTable &btable()
+{
+    static BatchTable t = [] {
+        BatchTable k;
+        memset(&k, 0, sizeof k);
+        fill_batch_f32(k);
+        fill_batch_f64(k);
+        return k;
+    }();
+    return t;
+}
+
+int cpt_index(int cpt)
+{
+    for (int i = 0; i < NCPT; ++i)
+        if (CPT_VALUES[i] == cpt) return i;
+    return -1;
+}
+
+}  // namespace
+
+struct mgrit_batch {
+    int n;
+    mgrit_params p;
+    std::vector<mgrit_ctx *> ctx;
+    std::vector<int> cpt;        // cells per thread of the sweep kernels, per instance
+    std::vector<int> cpt64;      // cells per thread of the FP64 coarsest solve, per instance
+    int maxL;
+    int *d_active;
+    int *h_active;
+    double *d_norms;
+    double *h_norms;
+    std::vector<BLaunch> A, B;
+    std::vector<void *> tables;  // device launch tables
+    cudaGraphExec_t gA, gB;
+    cudaStream_t cap;
+    char err[256];
+};
+
+static int bfail(mgrit_batch *b, int code, const char *fmt, ...)
+{
+    char *buf = b ? b->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define BCK(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? MGRIT_ENOMEM : MGRIT_ECUDA, \
+                         "%s: %s", #call, cudaGetErrorString(e_));                       \
+    } while (0)
+
+static int threads_for(int nx, int cpt) { return (((nx + cpt - 1) / cpt + 31) / 32) * 32; }
+
+static void batch_free_tables(mgrit_batch *b)
+{
+    if (b->gA) cudaGraphExecDestroy(b->gA);
+    if (b->gB) cudaGraphExecDestroy(b->gB);
+    b->gA = b->gB = nullptr;
+    for (void *p : b->tables) cudaFree(p);
+    b->tables.clear();
+    b->A.clear();
+    b->B.clear();
+}
+
+template <typename T>
+static int upload(mgrit_batch *b, const std::vector<T> &v, T **out)
+{
+    BCK(cudaMalloc((void **)out, sizeof(T) * std::max<size_t>(v.size(), 1)));
+    b->tables.push_back(*out);
+    if (!v.empty()) BCK(cudaMemcpy(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return MGRIT_OK;
+}
+
+// one launch per (flux, cells per thread, threads) class of slab work items
+template <typename R>
+struct SlabGroups {
+    struct G {
+        std::vector<SlabArgs<R>> args;
+        std::vector<BatchItem> map;
+        int nx_max = 0;
+    };
+    std::map<std::tuple<int, int, int>, G> g;
+
+    void add(int inst, int flux, int cpt, const SlabArgs<R> &a, int nitems)
+    {
+        G &grp = g[std::make_tuple(flux, cpt, threads_for(a.nx, cpt))];
+        const int ai = (int)grp.args.size();
+        grp.args.push_back(a);
+        for (int j = 0; j < nitems; ++j) grp.map.push_back(BatchItem{ai, j, inst, 0});
+        grp.nx_max = std::max(grp.nx_max, a.nx);
+    }
+
+    int emit(mgrit_batch *b, std::vector<BLaunch> &out)
+    {
+        for (auto &kv : g) {
+            const int flux = std::get<0>(kv.first), cpt = std::get<1>(kv.first);
+            G &grp = kv.second;
+            BLaunch L;
+            memset(&L, 0, sizeof L);
+            L.kind = 0;
+            L.fn = sizeof(R) == 4 ? btable().slab32[flux][cpt_index(cpt)]
+                                  : btable().slab64[flux][cpt_index(cpt)];
+            L.threads = std::get<2>(kv.first);
+            L.smem = slab_smem_bytes<R>(grp.nx_max);
+            L.nblocks = (int)grp.map.size();
+            SlabArgs<R> *da;
+            int st;
+            if ((st = upload(b, grp.args, &da))) return st;
+            if ((st = upload(b, grp.map, &L.d_map))) return st;
+            L.d_args = da;
+            BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            out.push_back(L);
+        }
+        return MGRIT_OK;
+    }
+};
+
+static int emit_restrict(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
+{
+    std::map<std::pair<int, int>, std::pair<std::vector<RestrictBatchArgs>, std::vector<BatchItem>>> grp;
+    for (int i = 0; i < b->n; ++i) {
+        mgrit_ctx *c = b->ctx[i];
+        if (depth > c->L - 2) continue;
+        RestrictBatchArgs ra;
+        ra.r = restrict_args(c, depth);
+        ra.nblocks = depth == 0 ? c->nparts : restrict_blocks(ra.r.nC, ra.r.nx);
+        auto &e = grp[std::make_pair(ra.r.state_f32, ra.r.un_f32)];
+        const int ai = (int)e.first.size();
+        e.first.push_back(ra);
+        for (int k = 0; k < ra.nblocks; ++k) e.second.push_back(BatchItem{ai, 0, i, k});
+    }
+    for (auto &kv : grp) {
+        BLaunch L;
+        memset(&L, 0, sizeof L);
+        L.kind = 1;
+        L.state_f32 = kv.first.first;
+        L.un_f32 = kv.first.second;
+        L.nblocks = (int)kv.second.second.size();
+        RestrictBatchArgs *da;
+        int st;
+        if ((st = upload(b, kv.second.first, &da))) return st;
+        if ((st = upload(b, kv.second.second, &L.d_map))) return st;
+        L.d_args = da;
+        out.push_back(L);
+    }
+    return MGRIT_OK;
+}
+
+template <typename R>
+static int emit_relax(mgrit_batch *b, int depth, std::vector<BLaunch> &out,
+                      const std::vector<int> *only = nullptr)
+{
+    SlabGroups<R> sg;
+    for (int i = 0; i < b->n; ++i) {
+        mgrit_ctx *c = b->ctx[i];
+        if (depth > c->L - 2) continue;
+        if (only && std::find(only->begin(), only->end(), i) == only->end()) continue;
+        SlabArgs<R> a = relax_args<R>(c, depth);
+        sg.add(i, c->flux, b->cpt[i], a, a.nC + 1);
+    }
+    return sg.emit(b, out);
+}
+
+template <typename R>
+static int emit_interp(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
+{
+    SlabGroups<R> sg;
+    for (int i = 0; i < b->n; ++i) {
+        mgrit_ctx *c = b->ctx[i];
+        if (depth < 1 || depth > c->L - 2) continue;
+        SlabArgs<R> a = interp_args<R>(c, depth);
+        sg.add(i, c->flux, b->cpt[i], a, a.nC);
+    }
+    return sg.emit(b, out);
+}
+
+static int emit_coarse(mgrit_batch *b, std::vector<BLaunch> &out)
+{
+    SlabGroups<double> sg;
+    // cluster launches grouped by (flux, cells per thread, cluster size, threads)
+    std::map<std::tuple<int, int, int, int>, std::pair<std::vector<SlabArgs<double>>, std::vector<BatchItem>>> cg;
+    std::map<std::tuple<int, int, int, int>, size_t> csmem;
+    std::vector<ConvertBatchArgs> cv;
+    std::vector<BatchItem> cmap;
+    for (int i = 0; i < b->n; ++i) {
+        mgrit_ctx *c = b->ctx[i];
+        if (c->lc64.fn) {
+            const auto key = std::make_tuple(c->flux, c->lc64.cpt, c->lc64.K, c->lc64.threads);
+            auto &e = cg[key];
+            const int ai = (int)e.first.size();
+            e.first.push_back(coarse_args(c));
+            e.second.push_back(BatchItem{ai, 0, i, 0});
+            csmem[key] = std::max(csmem[key], c->lc64.smem);
+        } else {
+            sg.add(i, c->flux, b->cpt64[i], coarse_args(c), 1);
+        }
+        if (c->f32) {
+            const long long n = (long long)(c->nt_l[c->L - 1] + 1) * c->nx;
+            const int nb = (int)std::min<long long>((n + 255) / 256, 64);
+            const int ai = (int)cv.size();
+            cv.push_back(ConvertBatchArgs{static_cast<const double *>(c->u[c->L - 1]), c->u32c, n});
+            for (int k = 0; k < nb; ++k) cmap.push_back(BatchItem{ai, nb, i, k});
+        }
+    }
+    int st;
+    if ((st = sg.emit(b, out))) return st;
+    for (auto &kv : cg) {
+        BLaunch L;
+        memset(&L, 0, sizeof L);
+        L.kind = 4;
+        L.fn = btable().seqc64[std::get<0>(kv.first)][std::get<1>(kv.first) - 1];
+        L.un_f32 = std::get<2>(kv.first);   // cluster size
+        L.threads = std::get<3>(kv.first);
+        L.smem = csmem[kv.first];
+        L.nblocks = (int)kv.second.second.size() * L.un_f32;
+        SlabArgs<double> *da;
+        if ((st = upload(b, kv.second.first, &da))) return st;
+        if ((st = upload(b, kv.second.second, &L.d_map))) return st;
+        L.d_args = da;
+        if (L.un_f32 > 8) BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+        out.push_back(L);
+    }
+    if (!cv.empty()) {
+        BLaunch L;
+        memset(&L, 0, sizeof L);
+        L.kind = 3;
+        L.nblocks = (int)cmap.size();
+        ConvertBatchArgs *da;
+        if ((st = upload(b, cv, &da))) return st;
+        if ((st = upload(b, cmap, &L.d_map))) return st;
+        L.d_args = da;
+        out.push_back(L);
+    }
+    return MGRIT_OK;
+}
+
+static int emit_norm(mgrit_batch *b, std::vector<BLaunch> &out)
+{
+    std::vector<NormBatchArgs> na;
+    for (int i = 0; i < b->n; ++i)
+        na.push_back(NormBatchArgs{b->ctx[i]->partials, b->ctx[i]->nparts, b->d_norms + i});
+    BLaunch L;
+    memset(&L, 0, sizeof L);
+    L.kind = 2;
+    L.nblocks = b->n;
+    NormBatchArgs *da;
+    int st;
+    if ((st = upload(b, na, &da))) return st;
+    L.d_args = da;
+    out.push_back(L);
+    return MGRIT_OK;
+}
+
+static cudaError_t enqueue_blaunch(const mgrit_batch *b, const BLaunch &L, cudaStream_t s)
+{
+    switch (L.kind) {
+    case 0: {
+        const int *act = b->d_active;
+        void *d_args = L.d_args;
+        BatchItem *d_map = L.d_map;
+        void *args[] = {&d_args, &d_map, (void *)&act};
+        return cudaLaunchKernel(L.fn, dim3(L.nblocks), dim3(L.threads), args, L.smem, s);
+    }
+    case 1:
+        return launch_restrict_batch(static_cast<const RestrictBatchArgs *>(L.d_args), L.d_map,
+                                     L.nblocks, L.state_f32, L.un_f32, b->d_active, s);
+    case 2:
+        return launch_norm_batch(static_cast<const NormBatchArgs *>(L.d_args), L.nblocks,
+                                 b->d_active, s);
+    case 3:
+        return launch_convert_batch(static_cast<const ConvertBatchArgs *>(L.d_args), L.d_map,
+                                    L.nblocks, b->d_active, s);
+    default: {   // one cluster of L.un_f32 CTAs per item
+        const int *act = b->d_active;
+        void *d_args = L.d_args;
+        BatchItem *d_map = L.d_map;
+        void *args[] = {&d_args, &d_map, (void *)&act};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(L.nblocks);
+        cfg.blockDim = dim3(L.threads);
+        cfg.dynamicSmemBytes = L.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = L.un_f32;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, L.fn, args);
+    }
+    }
+}
+
+static int batch_capture(mgrit_batch *b, const std::vector<BLaunch> &ls, cudaGraphExec_t *out)
+{
+    cudaGraph_t graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (const BLaunch &L : ls)
+        if ((e = enqueue_blaunch(b, L, b->cap)) != cudaSuccess) break;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bfail(b, MGRIT_ECUDA, "batch graph capture: %s",
+                     cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, MGRIT_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    return MGRIT_OK;
+}
+
+static int batch_build(mgrit_batch *b)
+{
+    batch_free_tables(b);
+    const bool f32 = b->p.precision == 32;
+    int st;
+    // graph A: level-0 relaxation, restriction to level 1, norms
+    if ((st = f32 ? emit_relax<float>(b, 0, b->A) : emit_relax<double>(b, 0, b->A))) return st;
+    if ((st = emit_restrict(b, 0, b->A))) return st;
+    if ((st = emit_norm(b, b->A))) return st;
+    // graph B: deeper levels, coarsest solves, interpolation
+    for (int d = 1; d <= b->maxL - 2; ++d) {
+        if ((st = f32 ? emit_relax<float>(b, d, b->B) : emit_relax<double>(b, d, b->B))) return st;
+        if ((st = emit_restrict(b, d, b->B))) return st;
+    }
+    if ((st = emit_coarse(b, b->B))) return st;
+    for (int d = b->maxL - 2; d >= 1; --d)
+        if ((st = f32 ? emit_interp<float>(b, d, b->B) : emit_interp<double>(b, d, b->B))) return st;
+    if ((st = batch_capture(b, b->A, &b->gA))) return st;
+    return batch_capture(b, b->B, &b->gB);
+}
+
+extern "C" int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst, int n,
+                                  const mgrit_params *params)
+{
+    mgrit_batch *b = nullptr;
+    if (!out || !inst || n < 1) return bfail(b, MGRIT_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    mgrit_params p;
+    if (params) p = *params; else mgrit_default_params(&p);
+    b = new (std::nothrow) mgrit_batch();
+    if (!b) return bfail(nullptr, MGRIT_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->p = p;
+    b->maxL = 0;
+    b->d_active = nullptr;
+    b->h_active = nullptr;
+    b->d_norms = nullptr;
+    b->h_norms = nullptr;
+    b->gA = b->gB = nullptr;
+    b->cap = nullptr;
+    b->err[0] = 0;
+    int st = MGRIT_OK;
+    for (int i = 0; i < n && st == MGRIT_OK; ++i) {
+        const mgrit_instance &d = inst[i];
+        if (d.scheme != MGRIT_WENO5_SSPRK3) {
+            st = bfail(b, MGRIT_EINVAL, "instance %d: batches run WENO5/SSPRK3 only", i);
+            break;
+        }
+        mgrit_ctx *c = nullptr;
+        st = mgrit_create(&c, d.nx, d.nt, d.m, d.levels, d.scheme, d.flux);
+        if (st) {
+            bfail(b, st, "instance %d: %s", i, mgrit_last_error(nullptr));
+            break;
+        }
+        b->ctx.push_back(c);
+        mgrit_params pi = p;
+        pi.T = d.T;
+        if ((st = mgrit_set_params(c, &pi))) {
+            bfail(b, st, "instance %d: %s", i, c->err);
+            break;
+        }
+        const Launch &ln = p.precision == 32 ? c->ln32 : c->ln64;
+        if (cpt_index(ln.cpt) < 0 || cpt_index(ln.cpt) > 4 || !c->ln64.slab) {
+            st = bfail(b, MGRIT_EINVAL, "instance %d: nx = %d exceeds the batched slab limit", i, d.nx);
+            break;
+        }
+        b->cpt.push_back(ln.cpt);
+        b->cpt64.push_back(c->ln64.cpt);
+        b->maxL = std::max(b->maxL, d.levels);
+        if ((st = ensure_alloc(c))) {
+            bfail(b, st, "instance %d: %s", i, c->err);
+            break;
+        }
+    }
+    mgrit_batch *bb = b;
+    auto cleanup = [&]() { mgrit_batch_destroy(bb); };
+    if (st) {
+        // keep the message for mgrit_last_error(NULL)
+        snprintf(g_create_err, sizeof g_create_err, "%s", b->err);
+        cleanup();
+        return st;
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&b->d_active, sizeof(int) * n)) ||
+        (e = cudaMallocHost((void **)&b->h_active, sizeof(int) * n)) ||
+        (e = cudaMalloc((void **)&b->d_norms, sizeof(double) * n)) ||
+        (e = cudaMallocHost((void **)&b->h_norms, sizeof(double) * n)) ||
+        (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking))) {
+        snprintf(g_create_err, sizeof g_create_err, "batch allocation: %s", cudaGetErrorString(e));
+        cleanup();
+        return MGRIT_ENOMEM;
+    }
+    if ((st = batch_build(b))) {
+        snprintf(g_create_err, sizeof g_create_err, "%s", b->err);
+        cleanup();
+        return st;
+    }
+    *out = b;
+    return MGRIT_OK;
+}
+
+static int batch_init(mgrit_batch *b, const double *const *u0_dev, cudaStream_t s)
+{
+    if (!u0_dev) return bfail(b, MGRIT_EINVAL, "u0_dev is NULL");
+    for (int i = 0; i < b->n; ++i) {
+        if (!u0_dev[i]) return bfail(b, MGRIT_EINVAL, "u0_dev[%d] is NULL", i);
+        int st = init_iterate(b->ctx[i], u0_dev[i], s);
+        if (st) return bfail(b, st, "instance %d: %s", i, b->ctx[i]->err);
+        b->ctx[i]->prepared = true;
+        b->h_active[i] = 1;
+    }
+    BCK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int) * b->n, cudaMemcpyHostToDevice, s));
+    return MGRIT_OK;
+}
+
+extern "C" int mgrit_batch_run_cycles(mgrit_batch *b, const double *const *u0_dev, int ncycles,
+                                      void *stream)
+{
+    if (!b) return MGRIT_EINVAL;
+    if (ncycles < 0) return bfail(b, MGRIT_EINVAL, "ncycles must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = batch_init(b, u0_dev, s);
+    if (st) return st;
+    for (int k = 0; k < ncycles; ++k) {
+        BCK(cudaGraphLaunch(b->gA, s));
+        BCK(cudaGraphLaunch(b->gB, s));
+    }
+    for (int i = 0; i < b->n; ++i) b->ctx[i]->have_state = ncycles > 0;
+    return MGRIT_OK;
+}
+
+extern "C" int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const *uT_dev,
+                                 int *status, int *iters, double *final_res, void *stream)
+{
+    if (!b) return MGRIT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = batch_init(b, u0_dev, s);
+    if (st) return st;
+    const int n = b->n;
+    std::vector<double> r0(n, 0.0), rm1(n, 0.0), rm2(n, 0.0);
+    std::vector<int> stat(n, MGRIT_ENOTCONV), it(n, 0);
+    int remaining = n;
+    for (int k = 0; remaining > 0; ++k) {
+        BCK(cudaGraphLaunch(b->gA, s));
+        BCK(cudaMemcpyAsync(b->h_norms, b->d_norms, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        BCK(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i) {
+            if (!b->h_active[i]) continue;
+            const double rk = b->h_norms[i];
+            if (k == 0) r0[i] = rk;
+            int done = 0;
+            if (rk < b->p.tol) { stat[i] = MGRIT_OK; done = 1; }
+            else if (!std::isfinite(rk) || rk > 1e8 * r0[i]) { stat[i] = MGRIT_EDIVERGED; done = 1; }
+            else if (b->p.precision == 32 && k >= 2 && rk > 0.9 * rm2[i]) { stat[i] = MGRIT_OK; done = 1; }
+            else if (k >= b->p.max_iter) { stat[i] = MGRIT_ENOTCONV; done = 1; }
+            rm2[i] = rm1[i];
+            rm1[i] = rk;
+            it[i] = k;
+            if (final_res) final_res[i] = rk;
+            if (done) {
+                b->h_active[i] = 0;
+                --remaining;
+            }
+        }
+        if (remaining == 0) break;
+        BCK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        BCK(cudaGraphLaunch(b->gB, s));
+    }
+    for (int i = 0; i < n; ++i) {
+        b->ctx[i]->have_state = true;
+        if (uT_dev && uT_dev[i] && (st = copy_out(b->ctx[i], uT_dev[i], b->ctx[i]->nC_l[0], 1, s)))
+            return bfail(b, st, "instance %d: %s", i, b->ctx[i]->err);
+        if (status) status[i] = stat[i];
+        if (iters) iters[i] = it[i];
+    }
+    BCK(cudaStreamSynchronize(s));
+    return MGRIT_OK;
+}
+
+// Autotuner: for every group of instances with the same (flux, nx), time the
+// level-0 relaxation with 1x, 2x and 4x the minimal cells per thread (fewer,
+// fuller threads) and keep the fastest; then rebuild the batch graphs.
+extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps,
+                                    void *stream)
+{
+    if (!b) return MGRIT_EINVAL;
+    if (reps < 1) reps = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = batch_init(b, u0_dev, s);
+    if (st) return st;
+    const bool f32 = b->p.precision == 32;
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    for (int i = 0; i < b->n; ++i) groups[std::make_pair(b->ctx[i]->flux, b->ctx[i]->nx)].push_back(i);
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    for (auto &kv : groups) {
+        const std::vector<int> &ids = kv.second;
+        const int base = b->cpt[ids[0]];
+        int best = base;
+        float best_ms = 1e30f;
+        for (int mul = 1; mul <= 4; mul *= 2) {
+            const int cpt = base * mul;
+            if (cpt_index(cpt) < 0 || cpt_index(cpt) > 4) break;
+            for (int i : ids) b->cpt[i] = cpt;
+            std::vector<BLaunch> mine;   // the level-0 relaxation of this group only
+            const size_t keep = b->tables.size();
+            if ((st = f32 ? emit_relax<float>(b, 0, mine, &ids) : emit_relax<double>(b, 0, mine, &ids)))
+                break;
+            for (const BLaunch &L : mine) BCK(enqueue_blaunch(b, L, s));   // warm-up
+            BCK(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r)
+                for (const BLaunch &L : mine) BCK(enqueue_blaunch(b, L, s));
+            BCK(cudaEventRecord(e1, s));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            for (size_t t = keep; t < b->tables.size(); ++t) cudaFree(b->tables[t]);
+            b->tables.resize(keep);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cpt;
+            }
+        }
+        if (st) break;
+        for (int i : ids) b->cpt[i] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    return batch_build(b);
+}
+
+extern "C" double mgrit_batch_cycle_cell_updates(const mgrit_batch *b)
+{
+    if (!b) return 0.0;
+    double s = 0.0;
+    for (const mgrit_ctx *c : b->ctx) s += mgrit_cycle_cell_updates(c);
+    return s;
+}
+
+extern "C" int mgrit_batch_query(const mgrit_batch *b, int instance, int what)
+{
+    if (!b || instance < 0 || instance >= b->n) return -1;
+    switch (what) {
+    case 0: return b->cpt[instance];
+    case 1: return threads_for(b->ctx[instance]->nx, b->cpt[instance]);
+    case 2: return b->ctx[instance]->L;
+    default: return -1;
+    }
+}
+
+extern "C" int mgrit_batch_copy_cpoints(mgrit_batch *b, int instance, double *uC_out_dev, void *stream)
+{
+    if (!b || instance < 0 || instance >= b->n) return MGRIT_EINVAL;
+    return mgrit_copy_cpoints(b->ctx[instance], uC_out_dev, stream);
+}
+
+extern "C" const char *mgrit_batch_last_error(const mgrit_batch *b)
+{
+    return b ? b->err : g_create_err;
+}
+
+extern "C" void mgrit_batch_destroy(mgrit_batch *b)
+{
+    if (!b) return;
+    batch_free_tables(b);
+    for (mgrit_ctx *c : b->ctx) mgrit_destroy(c);
+    cudaFree(b->d_active);
+    cudaFree(b->d_norms);
+    if (b->h_active) cudaFreeHost(b->h_active);
+    if (b->h_norms) cudaFreeHost(b->h_norms);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
 }

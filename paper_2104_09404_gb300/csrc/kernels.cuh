@@ -50,13 +50,13 @@ struct SlabArgs {
 };
 
 template <typename R, int SCHEME, int FLUX, int CPT>
-__device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a)
+__device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a,
+                                            const int j)
 {
     // CTA j = 0..nC.  FCF: new C_j = (Phi_l + g) applied m times from the old
     // C_{j-1} (F- then C-relaxation of chunk j-1); F: C_j kept.  Then the
     // F-relaxation of chunk j from the new C_j.  Chunks are independent
     // (block-diagonal A_FF, Eq. AFF): no grid-wide synchronisation.
-    const int j = blockIdx.x;
     const int nx = a.nx, m = a.m;
     R u[CPT];
     if (j == 0 || !a.fcf) {
@@ -86,10 +86,10 @@ __device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const
 }
 
 template <typename R, int SCHEME, int FLUX, int CPT>
-__device__ __forceinline__ void interp_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a)
+__device__ __forceinline__ void interp_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a,
+                                             const int j)
 {
     // Eq. (interpolation): u_l^{mj} = u_{l+1}^j, u_l^{mj+r} = Phi_l(u_l^{mj+r-1}) + g_l^{mj+r}
-    const int j = blockIdx.x;
     const int nx = a.nx, m = a.m;
     R u[CPT];
     S.load(u, rowp(a.uC, j, nx, a.nrows_uC));
@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(512) k_slab(SlabArgs<R> a)
     extern __shared__ __align__(16) unsigned char smem[];
     Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
     if (a.mode == MODE_RELAX)
-        relax_chunk(S, a);
+        relax_chunk(S, a, (int)blockIdx.x);
     else if (a.mode == MODE_INTERP)
-        interp_chunk(S, a);
+        interp_chunk(S, a, (int)blockIdx.x);
     else
         seq_march(S, a);
 }

@@ -72,3 +72,25 @@ def levels_for(nt, m, max_coarse=16):
         n //= m
         k += 1
     return 1 + k
+
+
+def batch_workload(seed=0, n=64, m=4, cfl=0.375, K=8):
+    """Uneven batch of independent problems: nx drawn from {256, ..., 8192}
+    and nt from {1024, ..., 16384} (powers of two, uniform), the first half
+    Burgers and the second half linear advection, random Fourier u0 per
+    instance (seed * 1000 + i), coarsened until at most 16 C-points remain,
+    and dt = cfl * dx / max|u0| (advection: / 1), i.e. T = nt * dt.
+    Returns (list of instance dicts, list of u0 arrays)."""
+    rng = np.random.default_rng(seed)
+    nxs = 2 ** rng.integers(8, 14, size=n)
+    nts = 2 ** rng.integers(10, 15, size=n)
+    insts, u0s = [], []
+    for i in range(n):
+        nx, nt = int(nxs[i]), int(nts[i])
+        flux = 0 if i < n // 2 else 1
+        u0 = fourier_ic(nx, seed=seed * 1000 + i, K=K)
+        speed = float(np.abs(u0).max()) if flux == 0 else 1.0
+        T = nt * cfl * (1.0 / nx) / speed
+        insts.append(dict(nx=nx, nt=nt, m=m, levels=levels_for(nt, m), flux=flux, T=T))
+        u0s.append(u0)
+    return insts, u0s

@@ -36,6 +36,12 @@ class mgrit_stats(ctypes.Structure):
                 ("cell_updates", ctypes.c_double), ("stagnated", ctypes.c_int)]
 
 
+class mgrit_instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nt", ctypes.c_int), ("m", ctypes.c_int),
+                ("levels", ctypes.c_int), ("scheme", ctypes.c_int), ("flux", ctypes.c_int),
+                ("T", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -55,6 +61,16 @@ _SIGS = {
     "mgrit_cycle_cell_updates": (_D, [_P]),
     "mgrit_query": (_I, [_P, _I]),
     "mgrit_last_error": (ctypes.c_char_p, [_P]),
+    "mgrit_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(mgrit_instance), _I,
+                                ctypes.POINTER(mgrit_params)]),
+    "mgrit_batch_run_cycles": (_I, [_P, _P, _I, _P]),
+    "mgrit_batch_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "mgrit_batch_autotune": (_I, [_P, _P, _I, _P]),
+    "mgrit_batch_cycle_cell_updates": (_D, [_P]),
+    "mgrit_batch_query": (_I, [_P, _I, _I]),
+    "mgrit_batch_copy_cpoints": (_I, [_P, _I, _P, _P]),
+    "mgrit_batch_last_error": (ctypes.c_char_p, [_P]),
+    "mgrit_batch_destroy": (None, [_P]),
     "mgrit_destroy": (None, [_P]),
 }
 
@@ -176,6 +192,84 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             load().mgrit_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent instances advanced together (wraps one mgrit_batch).
+    `instances` is a list of dicts with nx, nt, m, levels, flux, T (and
+    optionally scheme); other parameters are shared keyword arguments."""
+
+    def __init__(self, instances, **params):
+        lib = load()
+        arr = (mgrit_instance * len(instances))()
+        for k, d in enumerate(instances):
+            arr[k] = mgrit_instance(d["nx"], d["nt"], d["m"], d["levels"],
+                                    d.get("scheme", WENO5_SSPRK3), d["flux"], d["T"])
+        p = mgrit_params()
+        lib.mgrit_default_params(ctypes.byref(p))
+        for k, v in params.items():
+            setattr(p, k, v)
+        h = _P()
+        st = lib.mgrit_batch_create(ctypes.byref(h), arr, len(instances), ctypes.byref(p))
+        if st != OK:
+            raise MGRITError(st, lib.mgrit_last_error(None).decode())
+        self._h = h
+        self.n = len(instances)
+        self.instances = list(instances)
+
+    def _check(self, st):
+        if st != OK:
+            raise MGRITError(st, load().mgrit_batch_last_error(self._h).decode())
+
+    @staticmethod
+    def _ptr_array(tensors):
+        arr = (ctypes.c_void_p * len(tensors))()
+        for k, t in enumerate(tensors):
+            arr[k] = t.data_ptr() if t is not None else None
+        return arr
+
+    def run_cycles(self, u0s, ncycles, stream=None):
+        self._check(load().mgrit_batch_run_cycles(self._h, self._ptr_array(u0s), ncycles,
+                                                  _stream_handle(stream)))
+
+    def autotune(self, u0s, reps=3, stream=None):
+        self._check(load().mgrit_batch_autotune(self._h, self._ptr_array(u0s), reps,
+                                                _stream_handle(stream)))
+
+    def solve(self, u0s, stream=None):
+        """Returns (uT list, status list, iters list, final residual list)."""
+        import torch
+        uTs = [torch.empty_like(u) for u in u0s]
+        st = (ctypes.c_int * self.n)()
+        it = (ctypes.c_int * self.n)()
+        res = (ctypes.c_double * self.n)()
+        self._check(load().mgrit_batch_solve(self._h, self._ptr_array(u0s), self._ptr_array(uTs),
+                                             st, it, res, _stream_handle(stream)))
+        return uTs, list(st), list(it), list(res)
+
+    def cpoints(self, i, stream=None):
+        import torch
+        d = self.instances[i]
+        out = torch.empty((d["nt"] // d["m"] + 1, d["nx"]), dtype=torch.float64, device="cuda")
+        self._check(load().mgrit_batch_copy_cpoints(self._h, i, _ptr(out), _stream_handle(stream)))
+        return out
+
+    def cycle_cell_updates(self):
+        return load().mgrit_batch_cycle_cell_updates(self._h)
+
+    def query(self, i, what):
+        return load().mgrit_batch_query(self._h, i, what)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mgrit_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,113 @@
+"""Batched instances (uneven nx, nt, levels and flux in one launch per phase):
+every instance must reproduce the single-instance solver, in FP64 and FP32
+sweeps, before and after the autotuner changes its CTA shape, and converged
+instances must be masked out while the others continue.  Batched and single
+launches run the same slab code; where a coarsest solve runs on a different
+kernel (single CTA vs cluster) the compiler may contract multiply-adds
+differently, so agreement is to 1e-12 relative (in practice bitwise)."""
+import numpy as np
+import pytest
+
+from paper_2104_09404_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_09404_gb300 import build as B, mgrit
+    B.build()
+    mgrit.load()
+    return mgrit
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+MIXED = [
+    dict(nx=64, nt=256, m=2, levels=3, flux=0, T=0.2),
+    dict(nx=100, nt=128, m=4, levels=3, flux=1, T=0.1),
+    dict(nx=512, nt=256, m=4, levels=2, flux=0, T=0.02),
+    dict(nx=777, nt=64, m=4, levels=3, flux=1, T=0.02),
+    dict(nx=128, nt=256, m=4, levels=2, flux=0, T=0.25),
+    dict(nx=2048, nt=128, m=2, levels=4, flux=0, T=0.004),
+]
+
+
+def single_cpoints(M, d, u0, ncycles, precision):
+    s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], precision=precision)
+    s.run_cycles(dev(u0), ncycles)
+    torch.cuda.synchronize()
+    return s.cpoints()
+
+
+def close(a, b):
+    return float((a - b).abs().max()) <= 1e-12 * float(b.abs().max())
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_cycles_match_single_instances(M, precision):
+    u0s = [inputs.fourier_ic(d["nx"], seed=k) for k, d in enumerate(MIXED)]
+    b = M.Batch(MIXED, precision=precision)
+    b.run_cycles([dev(u) for u in u0s], 2)
+    torch.cuda.synchronize()
+    for k, d in enumerate(MIXED):
+        ref = single_cpoints(M, d, u0s[k], 2, precision)
+        assert close(b.cpoints(k), ref), k
+
+
+def test_autotuned_shapes_give_identical_results(M):
+    u0s = [dev(inputs.fourier_ic(d["nx"], seed=10 + k)) for k, d in enumerate(MIXED)]
+    b = M.Batch(MIXED, precision=32)
+    b.run_cycles(u0s, 2)
+    torch.cuda.synchronize()
+    before = [b.cpoints(k) for k in range(len(MIXED))]
+    b.autotune(u0s, reps=2)
+    shapes = [(b.query(k, 0), b.query(k, 1)) for k in range(len(MIXED))]
+    assert all(c in (1, 2, 4, 8, 16) and 32 <= t <= 512 for c, t in shapes)
+    b.run_cycles(u0s, 2)
+    torch.cuda.synchronize()
+    for k in range(len(MIXED)):
+        assert torch.equal(b.cpoints(k), before[k]), k   # same kernels, other CTA shape
+
+
+def test_batch_solve_masks_converged_instances(M):
+    # instances converge after different numbers of cycles (two-level
+    # exactness bounds some by nt/m); each must match its own single solve
+    insts = [MIXED[0], MIXED[4], dict(nx=96, nt=64, m=4, levels=2, flux=1, T=0.05), MIXED[1]]
+    u0s = [inputs.fourier_ic(d["nx"], seed=20 + k) for k, d in enumerate(insts)]
+    b = M.Batch(insts, max_iter=40)
+    uTs, status, iters, res = b.solve([dev(u) for u in u0s])
+    assert len(set(iters)) > 1          # genuinely different stopping cycles
+    for k, d in enumerate(insts):
+        s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], max_iter=40)
+        st, uT, _, stats = s.solve(dev(u0s[k]))
+        assert status[k] == st and iters[k] == stats.iters, (k, status, iters)
+        assert close(uTs[k], uT), k
+        assert res[k] == pytest.approx(stats.res_hist[stats.iters], rel=1e-9, abs=1e-13)
+
+
+def test_batch_rejects_unsupported_instances(M):
+    with pytest.raises(M.MGRITError):
+        M.Batch([dict(nx=64, nt=64, m=2, levels=2, flux=0, T=0.1, scheme=1)])
+    with pytest.raises(M.MGRITError):
+        M.Batch([dict(nx=16384, nt=64, m=2, levels=2, flux=0, T=0.01)], precision=32)
+    with pytest.raises(M.MGRITError):
+        M.Batch([dict(nx=64, nt=60, m=4, levels=3, flux=0, T=0.1)])
+
+
+def test_uneven_batch_workload_runs(M):
+    # a reduced instance of the 64-instance uneven workload (8 instances)
+    insts, u0s = inputs.batch_workload(seed=3, n=8)
+    b = M.Batch(insts, precision=32)
+    b.run_cycles([dev(u) for u in u0s], 1)
+    torch.cuda.synchronize()
+    for k, d in enumerate(insts):
+        uC = b.cpoints(k)
+        assert uC.shape == (d["nt"] // d["m"] + 1, d["nx"])
+        # FP32 sweeps: the C-point rows hold u0 rounded to FP32
+        assert torch.equal(uC[0], dev(u0s[k]).float().double())
