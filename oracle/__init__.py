@@ -9,5 +9,5 @@ from .api import (  # noqa: F401
     NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE, RELAX_F, RELAX_FCF, GUESS_EQ17, GUESS_INJECT,
     OK, EINVAL, EDIVERGED, ENOTCONV,
     build, weno5_left, spatial_op, step, serial, mgrit, residual, num_threads, vcycles,
-    weno5_left_grad, step_vjp, adjoint_serial,
+    weno5_left_grad, step_vjp, adjoint_serial, adjoint_mgrit,
 )

@@ -59,6 +59,9 @@ def _load():
         lib.orc_step_vjp.argtypes = [I, D, D, I, I, P, P, P]
         lib.orc_adjoint_serial.restype = None
         lib.orc_adjoint_serial.argtypes = [I, D, D, I, I, I, P, P, P]
+        lib.orc_adjoint_mgrit.restype = I
+        lib.orc_adjoint_mgrit.argtypes = [I, I, I, I, I, I, D, D, I, I, D, I,
+                                          P, P, P, P, P, P]
         lib.orc_num_threads.restype = I
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -185,3 +188,22 @@ def adjoint_serial(u0, lamT, dt, nsteps, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_B
     _load().orc_adjoint_serial(u0.size, Lx, dt, nsteps, scheme, flux, _ptr(u0), _ptr(lamT),
                                _ptr(out))
     return out
+
+
+def adjoint_mgrit(uC, lamT, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
+                  relax=RELAX_FCF, guess=GUESS_EQ17, tol=1e-10, max_iter=64, Lx=1.0):
+    """Adjoint MGRIT backward in time from the forward C-point checkpoints uC
+    ((nt/m+1, nx)).  Returns a dict with status, iters, res_hist, lam0 and
+    lamC (row i = lam at forward point m*i)."""
+    uC, lamT = _f64(uC), _f64(lamT)
+    nx = lamT.size
+    lam0 = np.zeros(nx)
+    lamC = np.zeros((nt // m + 1, nx))
+    hist = np.zeros(max_iter + 2)
+    iters = ctypes.c_int(0)
+    st = _load().orc_adjoint_mgrit(nx, nt, m, levels, scheme, flux, Lx, T, relax, guess, tol,
+                                   max_iter, _ptr(uC), _ptr(lamT), _ptr(lam0), _ptr(lamC),
+                                   ctypes.cast(ctypes.pointer(iters), ctypes.c_void_p),
+                                   _ptr(hist))
+    k = iters.value
+    return dict(status=st, iters=k, res_hist=hist[:k + 1].copy(), lam0=lam0, lamC=lamC)

@@ -450,6 +450,12 @@ typedef struct {
     int nt[32];            /* steps on level l: nt / m^l */
     double *u[32];         /* (nt_l + 1) * nx */
     double *g[32];         /* (nt_l + 1) * nx */
+    /* adjoint mode: the propagator of step i on level l is the transposed
+     * linearisation Phi_l'(U)^T at the forward state U of fine index
+     * nt - i m^l (rows 0..nt-1 of traj), i.e. the same Algorithm 1 run
+     * backward in time on lam^n = Phi'(u^n)^T lam^{n+1} */
+    int adjoint;
+    const double *traj;
 } orc_mg;
 
 static double *row(double *base, int nx, int i) { return base + (size_t)i * nx; }
@@ -461,11 +467,25 @@ static double level_dt(const orc_mg *M, int l)
     return dt;
 }
 
+/* the level-l propagator of the step that ends at point i, applied to x:
+ * Phi_l(x), or in adjoint mode Phi_l'(U)^T x (work: 12*nx) */
+static void propagate(const orc_mg *M, int l, int i, const double *x, double *y, double *work)
+{
+    if (!M->adjoint) {
+        phi_step(M->nx, M->dx, level_dt(M, l), M->scheme, M->flux, M->numflux, x, y, work);
+        return;
+    }
+    long long s = 1;
+    for (int k = 0; k < l; ++k) s *= M->m;
+    const double *U = M->traj + (size_t)((long long)M->nt[0] - (long long)i * s) * M->nx;
+    phi_step_vjp(M->nx, M->dx, level_dt(M, l), M->scheme, M->flux, U, x, y, work);
+}
+
 /* Phi_l(x) + g_l^{i} into y */
 static void step_plus_g(const orc_mg *M, int l, const double *x, int gi, double *y,
                         double *work)
 {
-    phi_step(M->nx, M->dx, level_dt(M, l), M->scheme, M->flux, M->numflux, x, y, work);
+    propagate(M, l, gi, x, y, work);
     const double *g = row(M->g[l], M->nx, gi);
     for (int c = 0; c < M->nx; ++c) y[c] += g[c];
 }
@@ -480,7 +500,7 @@ static void f_relax(orc_mg *M, int l)
 #pragma omp parallel for schedule(static)
 #endif
     for (int j = 0; j < nc; ++j) {
-        double *work = malloc(sizeof(double) * 6 * (size_t)nx);
+        double *work = malloc(sizeof(double) * 12 * (size_t)nx);
         for (int r = 1; r < m; ++r)
             step_plus_g(M, l, row(M->u[l], nx, m * j + r - 1), m * j + r,
                         row(M->u[l], nx, m * j + r), work);
@@ -496,7 +516,7 @@ static void c_relax(orc_mg *M, int l)
 #pragma omp parallel for schedule(static)
 #endif
     for (int j = 1; j <= nc; ++j) {
-        double *work = malloc(sizeof(double) * 6 * (size_t)nx);
+        double *work = malloc(sizeof(double) * 12 * (size_t)nx);
         step_plus_g(M, l, row(M->u[l], nx, m * j - 1), m * j, row(M->u[l], nx, m * j), work);
         free(work);
     }
@@ -529,13 +549,12 @@ static double residual_restrict(orc_mg *M, int l, int do_restrict)
 #pragma omp parallel for schedule(static)
 #endif
     for (int i = 1; i <= nc; ++i) {
-        double *work = malloc(sizeof(double) * 6 * (size_t)nx);
+        double *work = malloc(sizeof(double) * 12 * (size_t)nx);
         double *phi = malloc(sizeof(double) * (size_t)nx);
         double *psi = malloc(sizeof(double) * (size_t)nx);
         const double *gl = row(M->g[l], nx, m * i);
         const double *ul = row(M->u[l], nx, m * i);
-        phi_step(nx, M->dx, level_dt(M, l), M->scheme, M->flux, M->numflux,
-                 row(M->u[l], nx, m * i - 1), phi, work);
+        propagate(M, l, m * i, row(M->u[l], nx, m * i - 1), phi, work);
         double s = 0.0;
         for (int c = 0; c < nx; ++c) {
             double r = phi[c] + gl[c] - ul[c];
@@ -543,8 +562,7 @@ static double residual_restrict(orc_mg *M, int l, int do_restrict)
         }
         rsq[i] = s;
         if (do_restrict) {
-            phi_step(nx, M->dx, level_dt(M, l + 1), M->scheme, M->flux, M->numflux,
-                     row(M->u[l], nx, m * (i - 1)), psi, work);
+            propagate(M, l + 1, i, row(M->u[l], nx, m * (i - 1)), psi, work);
             double *gc = row(M->g[l + 1], nx, i);
             double *uc = row(M->u[l + 1], nx, i);
             for (int c = 0; c < nx; ++c) {
@@ -568,7 +586,7 @@ static double residual_restrict(orc_mg *M, int l, int do_restrict)
 static void coarse_solve(orc_mg *M, int l)
 {
     int nx = M->nx;
-    double *work = malloc(sizeof(double) * 6 * (size_t)nx);
+    double *work = malloc(sizeof(double) * 12 * (size_t)nx);
     memcpy(row(M->u[l], nx, 0), row(M->g[l], nx, 0), sizeof(double) * (size_t)nx);
     for (int i = 1; i <= M->nt[l]; ++i)
         step_plus_g(M, l, row(M->u[l], nx, i - 1), i, row(M->u[l], nx, i), work);
@@ -629,6 +647,29 @@ static int mg_init(orc_mg *M, int nx, int nt, int m, int levels, int scheme, int
     return ORC_OK;
 }
 
+/* Cycle k: relax level 0, r_k = ||residual||; stop if r_k < tol; divergence
+ * if r_k is not finite or r_k > 1e8 r_0; give up after max_iter cycles;
+ * otherwise restrict, recurse, inject. */
+static int mg_loop(orc_mg *M, double tol, int max_iter, int *iters_out, double *res_hist)
+{
+    double r0 = 0.0;
+    int k = 0, st;
+    for (;; ++k) {
+        relax(M, 0);
+        double rk = sqrt(residual_restrict(M, 0, 0));
+        if (res_hist) res_hist[k] = rk;
+        if (k == 0) r0 = rk;
+        if (rk < tol) { st = ORC_OK; break; }
+        if (!isfinite(rk) || rk > 1e8 * r0) { st = ORC_EDIVERGED; break; }
+        if (k >= max_iter) { st = ORC_ENOTCONV; break; }
+        residual_restrict(M, 0, 1);
+        vcycle_from(M, 1);
+        interpolate(M, 0, 0);
+    }
+    if (iters_out) *iters_out = k;
+    return st;
+}
+
 /*
  * Full FAS MGRIT V-cycle solve.  Level-0 initial iterate: every C-point is
  * uC_init (if given, (nt/m+1)*nx) else u0; g_0 = [u0, 0, ..., 0].
@@ -654,22 +695,7 @@ int orc_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, int numfl
         memcpy(row(M.u[0], nx, i), src, rowb);
     }
     memcpy(row(M.u[0], nx, 0), u0, rowb);
-
-    double r0 = 0.0;
-    int k = 0;
-    for (;; ++k) {
-        relax(&M, 0);
-        double rk = sqrt(residual_restrict(&M, 0, 0));
-        if (res_hist) res_hist[k] = rk;
-        if (k == 0) r0 = rk;
-        if (rk < tol) { st = ORC_OK; break; }
-        if (!isfinite(rk) || rk > 1e8 * r0) { st = ORC_EDIVERGED; break; }
-        if (k >= max_iter) { st = ORC_ENOTCONV; break; }
-        residual_restrict(&M, 0, 1);
-        vcycle_from(&M, 1);
-        interpolate(&M, 0, 0);
-    }
-    if (iters_out) *iters_out = k;
+    st = mg_loop(&M, tol, max_iter, iters_out, res_hist);
     if (uC_out)
         for (int i = 0; i <= M.nt[0] / m; ++i)
             memcpy(uC_out + (size_t)i * nx, row(M.u[0], nx, m * i), rowb);
@@ -707,6 +733,59 @@ int orc_vcycles(int nx, int nt, int m, int levels, int scheme, int flux, int num
             memcpy(uC_out + (size_t)i * nx, row(M.u[0], nx, m * i), rowb);
     mg_free(&M);
     return ORC_OK;
+}
+
+/*
+ * Adjoint MGRIT: dJ/du^0 = lam^0 of lam^n = Phi'(u^n)^T lam^{n+1}, lam^nt =
+ * lamT, solved by the V-cycle above backward in time.  In reversed time
+ * k = nt - n the system is v^k = Phi'(u^{nt-k})^T v^{k-1}, v^0 = lamT: a
+ * linear forward-substitution system of the same block-bidiagonal form as
+ * Eq. (monolithicSystem), so Algorithm 1 applies unchanged with the
+ * propagator of step k on level l = Phi_l'(U)^T at the forward state of fine
+ * index nt - k m^l (the coarse operator linearised at the injected forward
+ * C-state).  The paper has no adjoint; this is its method applied to the
+ * adjoint system.
+ * The forward fine states are regenerated chunk by chunk from the forward
+ * C-point checkpoints uC ((nt/m+1)*nx): u^{mj+r} = Phi^r(uC_j), r < m.
+ * Split numerical flux only.  Outputs: lam0_out (nx) and, if given,
+ * lamC_out with row i = lam at forward point m*i, i = 0..nt/m.
+ */
+int orc_adjoint_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, double Lx,
+                      double T, int relax_kind, int guess, double tol, int max_iter,
+                      const double *uC, const double *lamT, double *lam0_out,
+                      double *lamC_out, int *iters_out, double *res_hist)
+{
+    orc_mg M;
+    int st = mg_init(&M, nx, nt, m, levels, scheme, flux, ORC_NUMFLUX_LF_SPLIT, Lx, T,
+                     relax_kind, guess);
+    if (st) return st;
+    size_t rowb = sizeof(double) * (size_t)nx;
+    double *traj = malloc(rowb * (size_t)nt);
+    if (!traj) { mg_free(&M); return ORC_ENOMEM; }
+    int nc = nt / m;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int j = 0; j < nc; ++j) {
+        double *work = malloc(sizeof(double) * 6 * (size_t)nx);
+        memcpy(row(traj, nx, m * j), uC + (size_t)j * nx, rowb);
+        for (int r = 1; r < m; ++r)
+            phi_step(nx, M.dx, M.dt0, scheme, flux, ORC_NUMFLUX_LF_SPLIT,
+                     row(traj, nx, m * j + r - 1), row(traj, nx, m * j + r), work);
+        free(work);
+    }
+    M.adjoint = 1;
+    M.traj = traj;
+    memcpy(row(M.g[0], nx, 0), lamT, rowb);
+    for (int i = 0; i <= M.nt[0]; ++i) memcpy(row(M.u[0], nx, i), lamT, rowb);
+    st = mg_loop(&M, tol, max_iter, iters_out, res_hist);
+    if (lam0_out) memcpy(lam0_out, row(M.u[0], nx, nt), rowb);
+    if (lamC_out)
+        for (int i = 0; i <= nc; ++i)
+            memcpy(lamC_out + (size_t)i * nx, row(M.u[0], nx, nt - m * i), rowb);
+    free(traj);
+    mg_free(&M);
+    return st;
 }
 
 /* ||r|| for given level-0 C-points uC ((nt/m+1)*nx): each chunk is stepped

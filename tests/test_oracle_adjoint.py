@@ -106,3 +106,73 @@ def test_gradient_of_objective_matches_central_differences(T):
         v = rng.standard_normal(nx)
         fd = (J(u0 + H * v) - J(u0 - H * v)) / (2 * H)
         assert abs(grad @ v - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.linalg.norm(grad) * np.linalg.norm(v))
+
+
+# ---- adjoint MGRIT (Algorithm 1 run backward in time on the adjoint system) ----
+
+def _forward(nx, nt, m, L, T, seed, scheme=O.SCHEME_WENO5_SSPRK3, flux=O.FLUX_BURGERS):
+    u0 = inputs.fourier_ic(nx, seed=seed)
+    f = O.mgrit(u0, nt, m, L, T, scheme=scheme, flux=flux, tol=1e-13, max_iter=80)
+    assert f["status"] == O.OK
+    return u0, f["uC"]
+
+
+@pytest.mark.parametrize("scheme,flux", [(O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+                                         (O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION),
+                                         (O.SCHEME_FO_FE, O.FLUX_BURGERS)])
+@pytest.mark.parametrize("L,relax,guess", [(2, O.RELAX_FCF, O.GUESS_EQ17),
+                                           (3, O.RELAX_F, O.GUESS_EQ17),
+                                           (3, O.RELAX_FCF, O.GUESS_INJECT)])
+def test_adjoint_mgrit_fixed_point_is_the_serial_adjoint(scheme, flux, L, relax, guess):
+    # the fixed point of the backward V-cycle is the serial adjoint (itself
+    # pinned by finite differences above), whatever the hierarchy
+    nx, nt, m, T = 32, 64, 4, 0.08
+    u0, uC = _forward(nx, nt, m, L, T, seed=3, scheme=scheme, flux=flux)
+    lamT = np.random.default_rng(2).standard_normal(nx)
+    a = O.adjoint_mgrit(uC, lamT, nt, m, L, T, scheme=scheme, flux=flux, relax=relax,
+                        guess=guess, tol=1e-12, max_iter=60)
+    assert a["status"] == O.OK
+    ref = O.adjoint_serial(u0, lamT, T / nt, nt, scheme=scheme, flux=flux)
+    np.testing.assert_allclose(a["lam0"], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+    # every C-point is the serial adjoint at that time: the chained VJPs of
+    # the m steps before the next C-point, at the serial forward states
+    traj = O.serial(u0, T / nt, nt, scheme=scheme, flux=flux, store_all=True)
+    for i in range(nt // m):
+        lam = a["lamC"][i + 1]
+        for n in range(m * (i + 1) - 1, m * i - 1, -1):
+            lam = O.step_vjp(traj[n], lam, T / nt, scheme=scheme, flux=flux)
+        np.testing.assert_allclose(a["lamC"][i], lam, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_adjoint_mgrit_two_level_F_relaxation_exact_after_nt_over_m_cycles():
+    # forward substitution structure: after k two-level F-cycles the first k
+    # backward C-intervals are exact, so by nt/m cycles the residual is roundoff
+    nx, nt, m, T = 24, 32, 4, 0.06
+    _, uC = _forward(nx, nt, m, 2, T, seed=11)
+    lamT = np.random.default_rng(5).standard_normal(nx)
+    a = O.adjoint_mgrit(uC, lamT, nt, m, 2, T, relax=O.RELAX_F, tol=0.0, max_iter=nt // m)
+    assert a["status"] == O.ENOTCONV
+    assert a["res_hist"][-1] < 1e-13 * a["res_hist"][0]
+
+
+def test_adjoint_mgrit_upwind_advection_mirrors_forward_mgrit():
+    # first-order upwind advection with forward Euler is linear and
+    # shift-invariant: Phi = (1-c) I + c S with S the periodic right shift, so
+    # Phi^T = P Phi P with P the reflection i -> nx-1-i (on every level).  The
+    # adjoint V-cycle on lamT must then be the reflected forward V-cycle on
+    # P lamT, iterate by iterate: same residual history, reflected C-points.
+    nx, nt, m, L, T = 40, 128, 4, 3, 0.4
+    rng = np.random.default_rng(7)
+    lamT = rng.standard_normal(nx)
+    uC = np.zeros((nt // m + 1, nx))       # the states do not enter a linear scheme
+    kw = dict(scheme=O.SCHEME_FO_FE, flux=O.FLUX_ADVECTION, relax=O.RELAX_FCF, tol=1e-13,
+              max_iter=40)
+    a = O.adjoint_mgrit(uC, lamT, nt, m, L, T, **kw)
+    f = O.mgrit(lamT[::-1].copy(), nt, m, L, T, **kw)
+    assert a["status"] == f["status"] == O.OK
+    assert a["iters"] == f["iters"]
+    np.testing.assert_allclose(a["res_hist"], f["res_hist"], rtol=1e-10,
+                               atol=1e-13 * f["res_hist"][0])
+    nc = nt // m
+    for i in range(nc + 1):
+        np.testing.assert_allclose(a["lamC"][nc - i], f["uC"][i][::-1], rtol=0, atol=1e-13)
