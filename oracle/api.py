@@ -14,6 +14,7 @@ FLUX_BURGERS, FLUX_ADVECTION = 0, 1
 NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE = 0, 1
 RELAX_F, RELAX_FCF = 0, 1
 GUESS_EQ17, GUESS_INJECT = 0, 1
+CYCLE_V, CYCLE_F = 0, 1
 OK, EINVAL, EDIVERGED, ENOTCONV = 0, -1, -4, -5
 
 _lib = None
@@ -47,12 +48,12 @@ def _load():
         lib.orc_serial.restype = None
         lib.orc_serial.argtypes = [I, D, D, I, I, I, I, P, P, I]
         lib.orc_mgrit.restype = I
-        lib.orc_mgrit.argtypes = [I, I, I, I, I, I, I, D, D, I, I, D, I,
+        lib.orc_mgrit.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, D, I,
                                   P, P, P, P, P, P, P]
         lib.orc_residual.restype = I
         lib.orc_residual.argtypes = [I, I, I, I, I, I, D, D, P, P]
         lib.orc_vcycles.restype = I
-        lib.orc_vcycles.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, P, P, P]
+        lib.orc_vcycles.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, I, P, P, P]
         lib.orc_weno5_left_grad.restype = None
         lib.orc_weno5_left_grad.argtypes = [P, P]
         lib.orc_step_vjp.restype = None
@@ -60,7 +61,7 @@ def _load():
         lib.orc_adjoint_serial.restype = None
         lib.orc_adjoint_serial.argtypes = [I, D, D, I, I, I, P, P, P]
         lib.orc_adjoint_mgrit.restype = I
-        lib.orc_adjoint_mgrit.argtypes = [I, I, I, I, I, I, D, D, I, I, D, I,
+        lib.orc_adjoint_mgrit.argtypes = [I, I, I, I, I, I, D, D, I, I, I, D, I,
                                           P, P, P, P, P, P]
         lib.orc_num_threads.restype = I
         lib.orc_num_threads.argtypes = []
@@ -117,7 +118,7 @@ def serial(u0, dt, nsteps, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
 
 def mgrit(u0, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
           numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, tol=1e-10,
-          max_iter=64, Lx=1.0, uC_init=None, want_full=False):
+          max_iter=64, Lx=1.0, uC_init=None, want_full=False, cycle=CYCLE_V):
     """Run the oracle MGRIT V-cycle.  Returns a dict with status, iters,
     res_hist, uC ((nt/m+1, nx)), uT and (optionally) the full trajectory."""
     u0 = _f64(u0)
@@ -130,7 +131,7 @@ def mgrit(u0, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
     iters = ctypes.c_int(0)
     init = None if uC_init is None else _f64(uC_init)
     st = _load().orc_mgrit(nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax, guess,
-                           tol, max_iter, _ptr(u0), _ptr(init), _ptr(uC), _ptr(full),
+                           cycle, tol, max_iter, _ptr(u0), _ptr(init), _ptr(uC), _ptr(full),
                            _ptr(uT), ctypes.cast(ctypes.pointer(iters), ctypes.c_void_p),
                            _ptr(hist))
     k = iters.value
@@ -152,14 +153,14 @@ def residual(uC, nt, m, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
 
 
 def vcycles(u0, nt, m, levels, T, ncycles, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
-            numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, Lx=1.0):
-    """Exactly ncycles V-cycles (no stopping test); returns (uC, res_hist)."""
+            numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, Lx=1.0, cycle=CYCLE_V):
+    """Exactly ncycles cycles (no stopping test); returns (uC, res_hist)."""
     u0 = _f64(u0)
     nx = u0.size
     uC = np.zeros((nt // m + 1, nx))
     hist = np.zeros(max(ncycles, 1))
     st = _load().orc_vcycles(nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax, guess,
-                             ncycles, _ptr(u0), _ptr(uC), _ptr(hist))
+                             cycle, ncycles, _ptr(u0), _ptr(uC), _ptr(hist))
     if st != OK:
         raise ValueError("orc_vcycles: invalid arguments")
     return uC, hist[:ncycles]
@@ -191,7 +192,8 @@ def adjoint_serial(u0, lamT, dt, nsteps, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_B
 
 
 def adjoint_mgrit(uC, lamT, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
-                  relax=RELAX_FCF, guess=GUESS_EQ17, tol=1e-10, max_iter=64, Lx=1.0):
+                  relax=RELAX_FCF, guess=GUESS_EQ17, tol=1e-10, max_iter=64, Lx=1.0,
+                  cycle=CYCLE_V):
     """Adjoint MGRIT backward in time from the forward C-point checkpoints uC
     ((nt/m+1, nx)).  Returns a dict with status, iters, res_hist, lam0 and
     lamC (row i = lam at forward point m*i)."""
@@ -201,8 +203,8 @@ def adjoint_mgrit(uC, lamT, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=F
     lamC = np.zeros((nt // m + 1, nx))
     hist = np.zeros(max_iter + 2)
     iters = ctypes.c_int(0)
-    st = _load().orc_adjoint_mgrit(nx, nt, m, levels, scheme, flux, Lx, T, relax, guess, tol,
-                                   max_iter, _ptr(uC), _ptr(lamT), _ptr(lam0), _ptr(lamC),
+    st = _load().orc_adjoint_mgrit(nx, nt, m, levels, scheme, flux, Lx, T, relax, guess, cycle,
+                                   tol, max_iter, _ptr(uC), _ptr(lamT), _ptr(lam0), _ptr(lamC),
                                    ctypes.cast(ctypes.pointer(iters), ctypes.c_void_p),
                                    _ptr(hist))
     k = iters.value

@@ -21,6 +21,7 @@
  *   coarsest sequential solve ..................... Sec. 3.2, Eq. (coarseCorr)
  *   ideal interpolation ........................... Sec. 3.2, Eq. (interpolation)
  *   V-cycle ....................................... Algorithm 1
+ *   F-cycle ....................................... Sec. 3.2 (Fig. MGcycles)
  *
  * Readings of the paper taken where it is silent or inconsistent:
  *   - the WENO tables' row r acts on cells {i-r, i-r+1, i-r+2} (the printed
@@ -60,6 +61,7 @@ enum { ORC_FLUX_BURGERS = 0, ORC_FLUX_ADVECTION = 1 };
 enum { ORC_NUMFLUX_LF_SPLIT = 0, ORC_NUMFLUX_LF_STATE = 1 };
 enum { ORC_RELAX_F = 0, ORC_RELAX_FCF = 1 };
 enum { ORC_GUESS_EQ17 = 0, ORC_GUESS_INJECT = 1 };
+enum { ORC_CYCLE_V = 0, ORC_CYCLE_F = 1 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -3, ORC_EDIVERGED = -4,
        ORC_ENOTCONV = -5 };
 
@@ -445,7 +447,7 @@ int orc_num_threads(void)
 /* ====================================================================== */
 
 typedef struct {
-    int nx, m, L, scheme, flux, numflux, relax, guess;
+    int nx, m, L, scheme, flux, numflux, relax, guess, cycle;
     double dx, dt0;
     int nt[32];            /* steps on level l: nt / m^l */
     double *u[32];         /* (nt_l + 1) * nx */
@@ -617,19 +619,47 @@ static void vcycle_from(orc_mg *M, int l)
     }
 }
 
+/* F-cycle (Sec. 3.2, the cycle sketch of Fig. MGcycles; the standard
+ * multigrid F-cycle): below a level, first an F-cycle, then one V-cycle,
+ * each with the level's relaxation, restriction and interpolation around it. */
+static void fcycle_from(orc_mg *M, int l)
+{
+    if (l < M->L - 1) {
+        relax(M, l);
+        residual_restrict(M, l, 1);
+        fcycle_from(M, l + 1);
+        interpolate(M, l, 1);
+        relax(M, l);
+        residual_restrict(M, l, 1);
+        vcycle_from(M, l + 1);
+        interpolate(M, l, 1);
+    } else {
+        coarse_solve(M, l);
+    }
+}
+
+static void cycle_from(orc_mg *M, int l)
+{
+    if (M->cycle == ORC_CYCLE_F)
+        fcycle_from(M, l);
+    else
+        vcycle_from(M, l);
+}
+
 static void mg_free(orc_mg *M)
 {
     for (int l = 0; l < M->L; ++l) { free(M->u[l]); free(M->g[l]); }
 }
 
 static int mg_init(orc_mg *M, int nx, int nt, int m, int levels, int scheme, int flux,
-                   int numflux, double Lx, double T, int relax_kind, int guess)
+                   int numflux, double Lx, double T, int relax_kind, int guess, int cycle)
 {
     if (nx < 1 || nt < 1 || m < 2 || levels < 2 || levels > 31) return ORC_EINVAL;
+    if (cycle != ORC_CYCLE_V && cycle != ORC_CYCLE_F) return ORC_EINVAL;
     if (scheme == ORC_SCHEME_WENO5_SSPRK3 && nx < 5) return ORC_EINVAL;
     memset(M, 0, sizeof *M);
     M->nx = nx; M->m = m; M->L = levels; M->scheme = scheme; M->flux = flux;
-    M->numflux = numflux; M->relax = relax_kind; M->guess = guess;
+    M->numflux = numflux; M->relax = relax_kind; M->guess = guess; M->cycle = cycle;
     M->dx = Lx / nx; M->dt0 = T / nt;
     long long div = 1;
     for (int l = 0; l < levels; ++l) {
@@ -663,7 +693,7 @@ static int mg_loop(orc_mg *M, double tol, int max_iter, int *iters_out, double *
         if (!isfinite(rk) || rk > 1e8 * r0) { st = ORC_EDIVERGED; break; }
         if (k >= max_iter) { st = ORC_ENOTCONV; break; }
         residual_restrict(M, 0, 1);
-        vcycle_from(M, 1);
+        cycle_from(M, 1);
         interpolate(M, 0, 0);
     }
     if (iters_out) *iters_out = k;
@@ -680,12 +710,13 @@ static int mg_loop(orc_mg *M, double tol, int max_iter, int *iters_out, double *
  * Returns ORC_OK / ORC_EDIVERGED / ORC_ENOTCONV / ORC_EINVAL.
  */
 int orc_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, int numflux,
-              double Lx, double T, int relax_kind, int guess, double tol, int max_iter,
+              double Lx, double T, int relax_kind, int guess, int cycle, double tol, int max_iter,
               const double *u0, const double *uC_init, double *uC_out, double *u_full_out,
               double *uT_out, int *iters_out, double *res_hist)
 {
     orc_mg M;
-    int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess);
+    int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess,
+                     cycle);
     if (st) return st;
     size_t rowb = sizeof(double) * (size_t)nx;
     memcpy(row(M.g[0], nx, 0), u0, rowb);
@@ -712,11 +743,12 @@ int orc_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, int numfl
  * level-0 C-points (after the last cycle's relaxation) go to uC_out if given.
  */
 int orc_vcycles(int nx, int nt, int m, int levels, int scheme, int flux, int numflux,
-                double Lx, double T, int relax_kind, int guess, int ncycles,
+                double Lx, double T, int relax_kind, int guess, int cycle, int ncycles,
                 const double *u0, double *uC_out, double *res_hist)
 {
     orc_mg M;
-    int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess);
+    int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess,
+                     cycle);
     if (st) return st;
     size_t rowb = sizeof(double) * (size_t)nx;
     memcpy(row(M.g[0], nx, 0), u0, rowb);
@@ -725,7 +757,7 @@ int orc_vcycles(int nx, int nt, int m, int levels, int scheme, int flux, int num
         relax(&M, 0);
         double rk = sqrt(residual_restrict(&M, 0, 1));
         if (res_hist) res_hist[k] = rk;
-        vcycle_from(&M, 1);
+        cycle_from(&M, 1);
         interpolate(&M, 0, 0);
     }
     if (uC_out)
@@ -751,13 +783,13 @@ int orc_vcycles(int nx, int nt, int m, int levels, int scheme, int flux, int num
  * lamC_out with row i = lam at forward point m*i, i = 0..nt/m.
  */
 int orc_adjoint_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, double Lx,
-                      double T, int relax_kind, int guess, double tol, int max_iter,
+                      double T, int relax_kind, int guess, int cycle, double tol, int max_iter,
                       const double *uC, const double *lamT, double *lam0_out,
                       double *lamC_out, int *iters_out, double *res_hist)
 {
     orc_mg M;
     int st = mg_init(&M, nx, nt, m, levels, scheme, flux, ORC_NUMFLUX_LF_SPLIT, Lx, T,
-                     relax_kind, guess);
+                     relax_kind, guess, cycle);
     if (st) return st;
     size_t rowb = sizeof(double) * (size_t)nx;
     double *traj = malloc(rowb * (size_t)nt);

@@ -144,3 +144,72 @@ def test_invalid_arguments():
     assert O.mgrit(u0, 16, 2, 1, 0.1)["status"] == O.EINVAL     # one level
     assert O.mgrit(u0, 16, 4, 4, 0.1)["status"] == O.EINVAL     # 16 % 4^3 != 0
     assert O.mgrit(np.zeros(4), 16, 4, 2, 0.1)["status"] == O.EINVAL   # WENO5 needs nx >= 5
+
+
+# ---- F-cycle (Sec. 3.2, Fig. MGcycles) ----------------------------------
+
+@pytest.mark.parametrize("levels", [3, 4])
+@pytest.mark.parametrize("relax", [O.RELAX_F, O.RELAX_FCF])
+def test_f_cycle_keeps_the_serial_fixed_point(levels, relax):
+    # started on the serial trajectory, every FAS coarse correction of the
+    # F-cycle's extra coarse visits is zero: cycles leave the C-points in place
+    nx, nt, m, T = 32, 256, 2, 0.1
+    u0 = inputs.fourier_ic(nx, seed=1)
+    traj = serial_traj(u0, nt, T)
+    r = O.mgrit(u0, nt, m, levels, T, relax=relax, uC_init=traj[::m], tol=0.0, max_iter=2,
+                cycle=O.CYCLE_F)
+    assert r["status"] == O.ENOTCONV
+    assert np.all(r["res_hist"] < 1e-13)
+    np.testing.assert_allclose(r["uC"], traj[::m], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("levels", [3, 4])
+@pytest.mark.parametrize("relax", [O.RELAX_F, O.RELAX_FCF])
+def test_converged_f_cycle_equals_serial(levels, relax):
+    nx, nt, m, T = 64, 256, 2, 0.2
+    u0 = inputs.sine_ic(nx)
+    r = O.mgrit(u0, nt, m, levels, T, relax=relax, tol=1e-10, max_iter=60, cycle=O.CYCLE_F)
+    assert r["status"] == O.OK
+    traj = serial_traj(u0, nt, T)
+    np.testing.assert_allclose(r["uC"], traj[::m], rtol=0, atol=1e-9)
+
+
+def test_two_level_f_cycle_is_the_v_cycle():
+    # with one coarse level both cycles visit it once per cycle
+    nx, nt, m, T = 40, 128, 4, 0.1
+    u0 = inputs.fourier_ic(nx, seed=8)
+    v = O.mgrit(u0, nt, m, 2, T, tol=1e-12, cycle=O.CYCLE_V)
+    f = O.mgrit(u0, nt, m, 2, T, tol=1e-12, cycle=O.CYCLE_F)
+    assert v["iters"] == f["iters"]
+    np.testing.assert_array_equal(v["res_hist"], f["res_hist"])
+    np.testing.assert_array_equal(v["uC"], f["uC"])
+
+
+@pytest.mark.parametrize("scheme", [O.SCHEME_WENO5_SSPRK3, O.SCHEME_FO_FE])
+def test_f_cycle_brute_force_monolithic_residual_tiny(scheme):
+    nx, nt, m, levels, T = 16, 16, 2, 3, 0.05
+    u0 = inputs.fourier_ic(nx, seed=4)
+    r = O.mgrit(u0, nt, m, levels, T, scheme=scheme, tol=1e-12, max_iter=40, want_full=True,
+                cycle=O.CYCLE_F)
+    assert r["status"] == O.OK
+    u = r["u"]
+    worst = max(np.abs(u[n] - O.step(u[n - 1], T / nt, scheme)).max() for n in range(1, nt + 1))
+    assert worst < 1e-11
+
+
+def test_f_cycle_iterates_conserve_mass():
+    nx, nt, m, T = 48, 256, 4, 0.15
+    u0 = inputs.fourier_ic(nx, seed=5)
+    r = O.mgrit(u0, nt, m, 4, T, tol=0.0, max_iter=2, cycle=O.CYCLE_F)
+    assert np.abs(r["uC"].sum(axis=1) - u0.sum()).max() < 1e-11 * nx
+
+
+def test_f_cycle_needs_fewer_cycles_on_a_smooth_case():
+    # the extra coarse visits give the F-cycle a better coarse correction
+    # (3 vs 5 cycles at 3 levels, 4 vs 7 at 4 levels on this case)
+    u0 = inputs.fourier_ic(64, seed=3)
+    for levels in (3, 4):
+        v = O.mgrit(u0, 1024, 4, levels, 0.1, tol=1e-11, cycle=O.CYCLE_V)
+        f = O.mgrit(u0, 1024, 4, levels, 0.1, tol=1e-11, cycle=O.CYCLE_F)
+        assert v["status"] == f["status"] == O.OK
+        assert f["iters"] < v["iters"]
