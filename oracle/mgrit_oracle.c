@@ -113,11 +113,15 @@ static double weno5_left(const double q[5], double p_out[3], double beta_out[3],
         const double *s = &q[2 - r];
         /* Eq. (C): candidate reconstruction on stencil r */
         p[r] = (TAB_C[r][0] * s[0] + TAB_C[r][1] * s[1] + TAB_C[r][2] * s[2]) / 6.0;
-        /* Eq. (B): beta_r = s^T B_r s */
+        /* Eq. (B): beta_r = s^T B_r s.  Every row and column of the printed
+         * B_r sums to zero, so beta_r(s) = beta_r(s - s_1 (1,1,1)); the form
+         * is evaluated on the stencil minus its middle value, which avoids
+         * cancelling O(|q|^2) terms when the data are smooth. */
+        const double t[3] = { s[0] - s[1], 0.0, s[2] - s[1] };
         double qf = 0.0;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
-                qf += s[a] * TAB_B[r][a][b] * s[b];
+                qf += t[a] * TAB_B[r][a][b] * t[b];
         beta[r] = qf / 6.0;
         /* Eq. (omega): alpha_r = d_r / (eps + beta_r)^2 */
         double den = WENO_EPS + beta[r];
@@ -247,15 +251,18 @@ static void weno5_left_grad(const double q[5], double grad[5])
     for (int r = 0; r < 3; ++r) {
         const double *s = &q[2 - r];
         p[r] = (TAB_C[r][0] * s[0] + TAB_C[r][1] * s[1] + TAB_C[r][2] * s[2]) / 6.0;
+        /* beta_r and its gradient on the stencil minus its middle value, as in
+         * weno5_left (both are invariant under adding a constant) */
+        const double t[3] = { s[0] - s[1], 0.0, s[2] - s[1] };
         double qf = 0.0;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
-                qf += s[a] * TAB_B[r][a][b] * s[b];
+                qf += t[a] * TAB_B[r][a][b] * t[b];
         beta[r] = qf / 6.0;
         for (int a = 0; a < 3; ++a) {
             dp[r][2 - r + a] = TAB_C[r][a] / 6.0;
             double g = 0.0;
-            for (int b = 0; b < 3; ++b) g += (TAB_B[r][a][b] + TAB_B[r][b][a]) * s[b];
+            for (int b = 0; b < 3; ++b) g += (TAB_B[r][a][b] + TAB_B[r][b][a]) * t[b];
             db[r][2 - r + a] = g / 6.0;
         }
         double den = WENO_EPS + beta[r];
