@@ -9,12 +9,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mgrit_oracle.c")
 _LIB = os.path.join(_HERE, "liborc_mgrit.so")
 
-SCHEME_WENO5_SSPRK3, SCHEME_FO_FE = 0, 1
+SCHEME_WENO5_SSPRK3, SCHEME_FO_FE, SCHEME_LF_FE = 0, 1, 2
 FLUX_BURGERS, FLUX_ADVECTION = 0, 1
 NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE = 0, 1
 RELAX_F, RELAX_FCF = 0, 1
 GUESS_EQ17, GUESS_INJECT = 0, 1
 CYCLE_V, CYCLE_F = 0, 1
+COARSE_REDISC, COARSE_PSI0, COARSE_PSI1 = 0, 1, 2
 OK, EINVAL, EDIVERGED, ENOTCONV = 0, -1, -4, -5
 
 _lib = None
@@ -48,12 +49,12 @@ def _load():
         lib.orc_serial.restype = None
         lib.orc_serial.argtypes = [I, D, D, I, I, I, I, P, P, I]
         lib.orc_mgrit.restype = I
-        lib.orc_mgrit.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, D, I,
+        lib.orc_mgrit.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, I, D, I,
                                   P, P, P, P, P, P, P]
         lib.orc_residual.restype = I
         lib.orc_residual.argtypes = [I, I, I, I, I, I, D, D, P, P]
         lib.orc_vcycles.restype = I
-        lib.orc_vcycles.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, I, P, P, P]
+        lib.orc_vcycles.argtypes = [I, I, I, I, I, I, I, D, D, I, I, I, I, I, P, P, P]
         lib.orc_weno5_left_grad.restype = None
         lib.orc_weno5_left_grad.argtypes = [P, P]
         lib.orc_step_vjp.restype = None
@@ -63,6 +64,8 @@ def _load():
         lib.orc_adjoint_mgrit.restype = I
         lib.orc_adjoint_mgrit.argtypes = [I, I, I, I, I, I, D, D, I, I, I, D, I,
                                           P, P, P, P, P, P]
+        lib.orc_psi_step.restype = None
+        lib.orc_psi_step.argtypes = [I, D, D, I, I, I, P, P]
         lib.orc_num_threads.restype = I
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -118,7 +121,8 @@ def serial(u0, dt, nsteps, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
 
 def mgrit(u0, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
           numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, tol=1e-10,
-          max_iter=64, Lx=1.0, uC_init=None, want_full=False, cycle=CYCLE_V):
+          max_iter=64, Lx=1.0, uC_init=None, want_full=False, cycle=CYCLE_V,
+          coarse=COARSE_REDISC):
     """Run the oracle MGRIT V-cycle.  Returns a dict with status, iters,
     res_hist, uC ((nt/m+1, nx)), uT and (optionally) the full trajectory."""
     u0 = _f64(u0)
@@ -131,7 +135,7 @@ def mgrit(u0, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
     iters = ctypes.c_int(0)
     init = None if uC_init is None else _f64(uC_init)
     st = _load().orc_mgrit(nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax, guess,
-                           cycle, tol, max_iter, _ptr(u0), _ptr(init), _ptr(uC), _ptr(full),
+                           cycle, coarse, tol, max_iter, _ptr(u0), _ptr(init), _ptr(uC), _ptr(full),
                            _ptr(uT), ctypes.cast(ctypes.pointer(iters), ctypes.c_void_p),
                            _ptr(hist))
     k = iters.value
@@ -153,14 +157,15 @@ def residual(uC, nt, m, T, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
 
 
 def vcycles(u0, nt, m, levels, T, ncycles, scheme=SCHEME_WENO5_SSPRK3, flux=FLUX_BURGERS,
-            numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, Lx=1.0, cycle=CYCLE_V):
+            numflux=NUMFLUX_LF_SPLIT, relax=RELAX_FCF, guess=GUESS_EQ17, Lx=1.0, cycle=CYCLE_V,
+            coarse=COARSE_REDISC):
     """Exactly ncycles cycles (no stopping test); returns (uC, res_hist)."""
     u0 = _f64(u0)
     nx = u0.size
     uC = np.zeros((nt // m + 1, nx))
     hist = np.zeros(max(ncycles, 1))
     st = _load().orc_vcycles(nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax, guess,
-                             cycle, ncycles, _ptr(u0), _ptr(uC), _ptr(hist))
+                             cycle, coarse, ncycles, _ptr(u0), _ptr(uC), _ptr(hist))
     if st != OK:
         raise ValueError("orc_vcycles: invalid arguments")
     return uC, hist[:ncycles]
@@ -209,3 +214,12 @@ def adjoint_mgrit(uC, lamT, nt, m, levels, T, scheme=SCHEME_WENO5_SSPRK3, flux=F
                                    _ptr(hist))
     k = iters.value
     return dict(status=st, iters=k, res_hist=hist[:k + 1].copy(), lam0=lam0, lamC=lamC)
+
+
+def psi_step(u, dt, M, order, flux=FLUX_BURGERS, Lx=1.0):
+    """Matched coarse step for M fine steps of the classical LF + FE scheme:
+    order 0 = Psi0, order 1 = Psi1 (dt is the fine step)."""
+    u = _f64(u)
+    out = np.zeros_like(u)
+    _load().orc_psi_step(u.size, Lx, dt, M, order, flux, _ptr(u), _ptr(out))
+    return out

@@ -22,6 +22,9 @@
  *   ideal interpolation ........................... Sec. 3.2, Eq. (interpolation)
  *   V-cycle ....................................... Algorithm 1
  *   F-cycle ....................................... Sec. 3.2 (Fig. MGcycles)
+ *   classical LF + FE fine scheme ................. Sec. 3.3, Eq. (fineLF)
+ *   matched coarse integrators Psi0, Psi1 ......... Sec. 3.3, Eqs. (coarseLFord0),
+ *                                                   (coarseLFord1), (fineLFxM)
  *
  * Readings of the paper taken where it is silent or inconsistent:
  *   - the WENO tables' row r acts on cells {i-r, i-r+1, i-r+2} (the printed
@@ -56,12 +59,13 @@
 
 /* identifiers passed in from Python; values chosen independently of the
  * CUDA library, which documents the same integers in its own header */
-enum { ORC_SCHEME_WENO5_SSPRK3 = 0, ORC_SCHEME_FO_FE = 1 };
+enum { ORC_SCHEME_WENO5_SSPRK3 = 0, ORC_SCHEME_FO_FE = 1, ORC_SCHEME_LF_FE = 2 };
 enum { ORC_FLUX_BURGERS = 0, ORC_FLUX_ADVECTION = 1 };
 enum { ORC_NUMFLUX_LF_SPLIT = 0, ORC_NUMFLUX_LF_STATE = 1 };
 enum { ORC_RELAX_F = 0, ORC_RELAX_FCF = 1 };
 enum { ORC_GUESS_EQ17 = 0, ORC_GUESS_INJECT = 1 };
 enum { ORC_CYCLE_V = 0, ORC_CYCLE_F = 1 };
+enum { ORC_COARSE_REDISC = 0, ORC_COARSE_PSI0 = 1, ORC_COARSE_PSI1 = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -3, ORC_EDIVERGED = -4,
        ORC_ENOTCONV = -5 };
 
@@ -208,13 +212,49 @@ static void spatial_op(int nx, double dx, int scheme, int flux, int numflux,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Classical Lax-Friedrichs + forward Euler, Sec. 3.3 Eq. (fineLF):       */
+/*   u_i^{n+1} = (E u)_i - dt (D f(u))_i,                                 */
+/*   (E v)_i = (v_{i+1} + v_{i-1}) / 2,  (D v)_i = (v_{i+1} - v_{i-1})/2dx */
+/* ---------------------------------------------------------------------- */
+static void op_E(int nx, const double *v, double *out)
+{
+    for (int i = 0; i < nx; ++i) out[i] = 0.5 * (v[wrap(i + 1, nx)] + v[wrap(i - 1, nx)]);
+}
+
+static void op_D(int nx, double dx, const double *v, double *out)
+{
+    for (int i = 0; i < nx; ++i) out[i] = (v[wrap(i + 1, nx)] - v[wrap(i - 1, nx)]) / (2.0 * dx);
+}
+
+static void op_f(int nx, int flux, const double *v, double *out)
+{
+    for (int i = 0; i < nx; ++i) out[i] = phys_flux(flux, v[i]);
+}
+
+/* v <- E^k v (work: nx) */
+static void op_E_pow(int nx, int k, double *v, double *work)
+{
+    for (int j = 0; j < k; ++j) {
+        op_E(nx, v, work);
+        memcpy(v, work, sizeof(double) * (size_t)nx);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
 /* Time stepper Phi with step dt, Sec. 2.2: SSPRK3 (Eq. SSPRK3) or        */
-/* forward Euler (Eq. SSPRK1).  out may not alias u.                      */
+/* forward Euler (Eq. SSPRK1); or Eq. (fineLF).  out may not alias u.     */
 /* ---------------------------------------------------------------------- */
 static void phi_step(int nx, double dx, double dt, int scheme, int flux, int numflux,
                      const double *u, double *out, double *work /* 6*nx */)
 {
     double *A = work, *u1 = work + nx, *u2 = work + 2 * nx, *w3 = work + 3 * nx;
+    if (scheme == ORC_SCHEME_LF_FE) {
+        op_E(nx, u, u1);
+        op_f(nx, flux, u, u2);
+        op_D(nx, dx, u2, A);
+        for (int i = 0; i < nx; ++i) out[i] = u1[i] - dt * A[i];
+        return;
+    }
     if (scheme == ORC_SCHEME_FO_FE) {
         spatial_op(nx, dx, scheme, flux, numflux, u, A, w3);
         for (int i = 0; i < nx; ++i) out[i] = u[i] + dt * A[i];
@@ -228,6 +268,36 @@ static void phi_step(int nx, double dx, double dt, int scheme, int flux, int num
     spatial_op(nx, dx, scheme, flux, numflux, u2, A, w3);
     for (int i = 0; i < nx; ++i)
         out[i] = 1.0 / 3.0 * u[i] + 2.0 / 3.0 * u2[i] + 2.0 / 3.0 * dt * A[i];
+}
+
+/* ---------------------------------------------------------------------- */
+/* Coarse integrators matched to M steps of Eq. (fineLF), Sec. 3.3        */
+/* (Eqs. coarseLFord0, coarseLFord1, fineLFxM), dt the fine step:         */
+/*   Psi0(u) = E^M u - M dt D f(u)                                        */
+/*   Psi1(u) = E^M u - dt sum_{i=1..M} E^{i-1} D f(E^{M-i} u)             */
+/* work: 4*nx                                                             */
+/* ---------------------------------------------------------------------- */
+static void psi_step(int nx, double dx, double dt, int M, int order, int flux,
+                     const double *u, double *out, double *work)
+{
+    double *a = work, *b = work + nx, *c = work + 2 * nx, *t = work + 3 * nx;
+    /* E^M u */
+    memcpy(out, u, sizeof(double) * (size_t)nx);
+    op_E_pow(nx, M, out, t);
+    if (order == 0) {
+        op_f(nx, flux, u, a);
+        op_D(nx, dx, a, b);
+        for (int i = 0; i < nx; ++i) out[i] -= M * dt * b[i];
+        return;
+    }
+    for (int i = 1; i <= M; ++i) {
+        memcpy(a, u, sizeof(double) * (size_t)nx);
+        op_E_pow(nx, M - i, a, t);          /* E^{M-i} u */
+        op_f(nx, flux, a, b);               /* f(E^{M-i} u) */
+        op_D(nx, dx, b, c);                 /* D f(...) */
+        op_E_pow(nx, i - 1, c, t);          /* E^{i-1} D f(...) */
+        for (int x = 0; x < nx; ++x) out[x] -= dt * c[x];
+    }
 }
 
 /* ====================================================================== */
@@ -420,6 +490,14 @@ void orc_step(int nx, double Lx, double dt, int scheme, int flux, int numflux,
     free(work);
 }
 
+void orc_psi_step(int nx, double Lx, double dt, int M, int order, int flux, const double *u,
+                  double *out)
+{
+    double *work = malloc(sizeof(double) * 4 * (size_t)nx);
+    psi_step(nx, Lx / nx, dt, M, order, flux, u, out, work);
+    free(work);
+}
+
 /* Serial fine time-stepping u^{n+1} = Phi(u^n) (forward substitution of
  * Eq. monolithicSystem).  traj is (nsteps+1)*nx if store_all, else nx. */
 void orc_serial(int nx, double Lx, double dt, int nsteps, int scheme, int flux,
@@ -454,7 +532,7 @@ int orc_num_threads(void)
 /* ====================================================================== */
 
 typedef struct {
-    int nx, m, L, scheme, flux, numflux, relax, guess, cycle;
+    int nx, m, L, scheme, flux, numflux, relax, guess, cycle, coarse;
     double dx, dt0;
     int nt[32];            /* steps on level l: nt / m^l */
     double *u[32];         /* (nt_l + 1) * nx */
@@ -481,6 +559,13 @@ static double level_dt(const orc_mg *M, int l)
 static void propagate(const orc_mg *M, int l, int i, const double *x, double *y, double *work)
 {
     if (!M->adjoint) {
+        if (l > 0 && M->coarse != ORC_COARSE_REDISC) {
+            /* matched coarse integrator: M_l = m^l fine steps of Eq. (fineLF) */
+            int Ml = 1;
+            for (int k = 0; k < l; ++k) Ml *= M->m;
+            psi_step(M->nx, M->dx, M->dt0, Ml, M->coarse == ORC_COARSE_PSI1, M->flux, x, y, work);
+            return;
+        }
         phi_step(M->nx, M->dx, level_dt(M, l), M->scheme, M->flux, M->numflux, x, y, work);
         return;
     }
@@ -659,14 +744,19 @@ static void mg_free(orc_mg *M)
 }
 
 static int mg_init(orc_mg *M, int nx, int nt, int m, int levels, int scheme, int flux,
-                   int numflux, double Lx, double T, int relax_kind, int guess, int cycle)
+                   int numflux, double Lx, double T, int relax_kind, int guess, int cycle,
+                   int coarse)
 {
     if (nx < 1 || nt < 1 || m < 2 || levels < 2 || levels > 31) return ORC_EINVAL;
     if (cycle != ORC_CYCLE_V && cycle != ORC_CYCLE_F) return ORC_EINVAL;
+    if (coarse < ORC_COARSE_REDISC || coarse > ORC_COARSE_PSI1) return ORC_EINVAL;
+    if (coarse != ORC_COARSE_REDISC && scheme != ORC_SCHEME_LF_FE) return ORC_EINVAL;
+    if (scheme == ORC_SCHEME_LF_FE && nx < 3) return ORC_EINVAL;
     if (scheme == ORC_SCHEME_WENO5_SSPRK3 && nx < 5) return ORC_EINVAL;
     memset(M, 0, sizeof *M);
     M->nx = nx; M->m = m; M->L = levels; M->scheme = scheme; M->flux = flux;
     M->numflux = numflux; M->relax = relax_kind; M->guess = guess; M->cycle = cycle;
+    M->coarse = coarse;
     M->dx = Lx / nx; M->dt0 = T / nt;
     long long div = 1;
     for (int l = 0; l < levels; ++l) {
@@ -717,13 +807,14 @@ static int mg_loop(orc_mg *M, double tol, int max_iter, int *iters_out, double *
  * Returns ORC_OK / ORC_EDIVERGED / ORC_ENOTCONV / ORC_EINVAL.
  */
 int orc_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, int numflux,
-              double Lx, double T, int relax_kind, int guess, int cycle, double tol, int max_iter,
+              double Lx, double T, int relax_kind, int guess, int cycle, int coarse,
+              double tol, int max_iter,
               const double *u0, const double *uC_init, double *uC_out, double *u_full_out,
               double *uT_out, int *iters_out, double *res_hist)
 {
     orc_mg M;
     int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess,
-                     cycle);
+                     cycle, coarse);
     if (st) return st;
     size_t rowb = sizeof(double) * (size_t)nx;
     memcpy(row(M.g[0], nx, 0), u0, rowb);
@@ -750,12 +841,13 @@ int orc_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, int numfl
  * level-0 C-points (after the last cycle's relaxation) go to uC_out if given.
  */
 int orc_vcycles(int nx, int nt, int m, int levels, int scheme, int flux, int numflux,
-                double Lx, double T, int relax_kind, int guess, int cycle, int ncycles,
+                double Lx, double T, int relax_kind, int guess, int cycle, int coarse,
+                int ncycles,
                 const double *u0, double *uC_out, double *res_hist)
 {
     orc_mg M;
     int st = mg_init(&M, nx, nt, m, levels, scheme, flux, numflux, Lx, T, relax_kind, guess,
-                     cycle);
+                     cycle, coarse);
     if (st) return st;
     size_t rowb = sizeof(double) * (size_t)nx;
     memcpy(row(M.g[0], nx, 0), u0, rowb);
@@ -795,8 +887,9 @@ int orc_adjoint_mgrit(int nx, int nt, int m, int levels, int scheme, int flux, d
                       double *lamC_out, int *iters_out, double *res_hist)
 {
     orc_mg M;
+    if (scheme == ORC_SCHEME_LF_FE) return ORC_EINVAL;   /* no adjoint of Eq. (fineLF) */
     int st = mg_init(&M, nx, nt, m, levels, scheme, flux, ORC_NUMFLUX_LF_SPLIT, Lx, T,
-                     relax_kind, guess, cycle);
+                     relax_kind, guess, cycle, ORC_COARSE_REDISC);
     if (st) return st;
     size_t rowb = sizeof(double) * (size_t)nx;
     double *traj = malloc(rowb * (size_t)nt);

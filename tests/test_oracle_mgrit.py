@@ -213,3 +213,51 @@ def test_f_cycle_needs_fewer_cycles_on_a_smooth_case():
         f = O.mgrit(u0, 1024, 4, levels, 0.1, tol=1e-11, cycle=O.CYCLE_F)
         assert v["status"] == f["status"] == O.OK
         assert f["iters"] < v["iters"]
+
+
+# ---- matched coarse integrators (Sec. 3.3) -------------------------------
+
+@pytest.mark.parametrize("coarse", [O.COARSE_PSI0, O.COARSE_PSI1])
+def test_matched_coarse_integrators_keep_the_fine_fixed_point(coarse):
+    # the coarse integrator changes convergence, never the answer: converged
+    # MGRIT equals serial stepping of the fine scheme, Eq. (fineLF)
+    nx, nt, m, L, T = 64, 512, 2, 5, 0.475
+    u0 = inputs.sine_ic(nx, offset=0.0)
+    r = O.mgrit(u0, nt, m, L, T, scheme=O.SCHEME_LF_FE, relax=O.RELAX_F, coarse=coarse,
+                tol=1e-11, max_iter=40)
+    assert r["status"] == O.OK
+    traj = serial_traj(u0, nt, T, scheme=O.SCHEME_LF_FE)
+    np.testing.assert_allclose(r["uC"], traj[::m], rtol=0, atol=1e-10)
+
+
+def _errors(coarse, ncycles, nx=64, nt=512, ic="stationary"):
+    # relative space-time L2 error of the level-0 C-points after k cycles
+    # (Sec. 4 setting: 5 levels, m = 2, T = 0.475, F-relaxation, V-cycle)
+    u0 = inputs.sine_ic(nx, offset=0.0) if ic == "stationary" else inputs.sine_ic(nx, 0.5, 0.5)
+    ser = serial_traj(u0, nt, 0.475, scheme=O.SCHEME_LF_FE)[::2]
+    out = []
+    for k in range(1, ncycles + 1):
+        r = O.mgrit(u0, nt, 2, 5, 0.475, scheme=O.SCHEME_LF_FE, relax=O.RELAX_F,
+                    coarse=coarse, tol=0.0, max_iter=k)
+        e = np.linalg.norm(r["uC"] - ser) / np.linalg.norm(ser)
+        out.append(e if np.isfinite(e) else np.inf)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("ic", ["stationary", "moving"])
+def test_paper_claim_matching_restores_convergence(ic):
+    # Sec. 4 (fine-integrator matching): rediscretisation blows up within a few
+    # cycles, zeroth-order matching converges, first-order matching faster
+    red = _errors(O.COARSE_REDISC, 4, ic=ic)
+    p0 = _errors(O.COARSE_PSI0, 4, ic=ic)
+    p1 = _errors(O.COARSE_PSI1, 4, ic=ic)
+    assert red.max() > 1.0
+    assert np.all(np.diff(p0) < 0) and np.all(np.diff(p1) < 0)
+    assert np.all(p1 < p0)
+    assert p1[3] < 1e-6
+
+
+def test_matched_integrators_need_the_lf_fine_scheme():
+    u0 = inputs.sine_ic(32)
+    r = O.mgrit(u0, 64, 2, 3, 0.1, coarse=O.COARSE_PSI1)
+    assert r["status"] == O.EINVAL

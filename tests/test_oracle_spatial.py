@@ -227,3 +227,88 @@ def test_serial_matches_repeated_steps():
     for _ in range(5):
         b = O.step(b, 1e-3)
     np.testing.assert_array_equal(a, b)
+
+
+# ---- classical Lax-Friedrichs + forward Euler and the matched coarse
+# ---- integrators (Sec. 3.3, Eqs. fineLF, coarseLFord0/1, fineLFxM) -------
+
+def _E(v):
+    return 0.5 * (np.roll(v, -1) + np.roll(v, 1))
+
+
+def _D(v, dx):
+    return (np.roll(v, -1) - np.roll(v, 1)) / (2 * dx)
+
+
+def test_lf_fe_advection_at_cfl_one_is_the_exact_shift():
+    # (u_{i+1} + u_{i-1})/2 - (u_{i+1} - u_{i-1})/2 = u_{i-1}; integer data and
+    # a power-of-two nx make every operation exact
+    nx = 64
+    u = np.random.default_rng(0).integers(-1000, 1000, nx).astype(np.float64)
+    got = O.step(u, 1.0 / nx, scheme=O.SCHEME_LF_FE, flux=O.FLUX_ADVECTION)
+    np.testing.assert_array_equal(got, np.roll(u, 1))
+
+
+def test_lf_fe_conserves_and_keeps_constants():
+    nx = 64
+    u = inputs.fourier_ic(nx, seed=3)
+    v = O.step(u, 0.3 / nx, scheme=O.SCHEME_LF_FE)
+    assert abs(v.sum() - u.sum()) < 1e-13 * nx
+    c = np.full(nx, 0.7)
+    np.testing.assert_array_equal(O.step(c, 0.01, scheme=O.SCHEME_LF_FE), c)
+
+
+def test_matched_integrators_of_one_step_are_the_fine_step():
+    nx = 40
+    u = inputs.fourier_ic(nx, seed=4)
+    fine = O.step(u, 0.2 / nx, scheme=O.SCHEME_LF_FE)
+    np.testing.assert_array_equal(O.psi_step(u, 0.2 / nx, 1, 0), fine)
+    np.testing.assert_array_equal(O.psi_step(u, 0.2 / nx, 1, 1), fine)
+
+
+def test_two_step_matching_identities_for_advection():
+    # f = u: Phi = E - dt D with E, D commuting, so
+    #   Phi^2 - Psi1 = dt^2 D^2 u  and  Phi^2 - Psi0 = -2 dt (E - I) D u + dt^2 D^2 u
+    nx, dx = 48, 1.0 / 48
+    u = inputs.fourier_ic(nx, seed=5)
+    dt = 0.3 * dx
+    two = O.step(O.step(u, dt, scheme=O.SCHEME_LF_FE, flux=O.FLUX_ADVECTION), dt,
+                 scheme=O.SCHEME_LF_FE, flux=O.FLUX_ADVECTION)
+    p1 = O.psi_step(u, dt, 2, 1, flux=O.FLUX_ADVECTION)
+    p0 = O.psi_step(u, dt, 2, 0, flux=O.FLUX_ADVECTION)
+    Du = _D(u, dx)
+    np.testing.assert_allclose(two - p1, dt ** 2 * _D(Du, dx), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(two - p0, -2 * dt * (_E(Du) - Du) + dt ** 2 * _D(Du, dx),
+                               rtol=0, atol=1e-13)
+
+
+def test_two_step_first_order_matching_identity_for_burgers():
+    # Phi^2(u) = E^2 u - dt (E D f + D f(E u)) + dt^2 D(E u . D f) - dt^3/2 D((D f)^2)
+    # exactly for f = u^2/2 (Taylor expansion of f around E u terminates), so
+    # Phi^2 - Psi1 is the last two terms
+    nx, dx = 64, 1.0 / 64
+    u = inputs.fourier_ic(nx, seed=6)
+    dt = 0.25 * dx
+    two = O.step(O.step(u, dt, scheme=O.SCHEME_LF_FE), dt, scheme=O.SCHEME_LF_FE)
+    p1 = O.psi_step(u, dt, 2, 1)
+    Df = _D(0.5 * u * u, dx)
+    rest = dt ** 2 * _D(_E(u) * Df, dx) - 0.5 * dt ** 3 * _D(Df * Df, dx)
+    np.testing.assert_allclose(two - p1, rest, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_first_order_matching_error_is_second_order_in_dt(M):
+    # Psi1 matches M fine steps up to O(dt^2) (Eq. fineLFxM): halving dt
+    # divides the mismatch by ~4; Psi0 only matches to O(dt)
+    nx = 64
+    u = inputs.fourier_ic(nx, seed=7)
+
+    def fine(dt):
+        v = u
+        for _ in range(M):
+            v = O.step(v, dt, scheme=O.SCHEME_LF_FE)
+        return v
+    e1 = [np.abs(fine(dt) - O.psi_step(u, dt, M, 1)).max() for dt in (0.02 / nx, 0.01 / nx)]
+    e0 = [np.abs(fine(dt) - O.psi_step(u, dt, M, 0)).max() for dt in (0.02 / nx, 0.01 / nx)]
+    assert 3.5 < e1[0] / e1[1] < 4.5
+    assert 1.7 < e0[0] / e0[1] < 2.3
