@@ -11,7 +11,7 @@ _LIB = os.path.join(_HERE, "liborc_mgrit.so")
 
 SCHEME_WENO5_SSPRK3, SCHEME_FO_FE, SCHEME_LF_FE = 0, 1, 2
 FLUX_BURGERS, FLUX_ADVECTION = 0, 1
-NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE = 0, 1
+NUMFLUX_LF_SPLIT, NUMFLUX_LF_STATE, NUMFLUX_ROE = 0, 1, 2
 RELAX_F, RELAX_FCF = 0, 1
 GUESS_EQ17, GUESS_INJECT = 0, 1
 CYCLE_V, CYCLE_F = 0, 1

@@ -15,6 +15,7 @@
  *   WENO reconstruction, k = 2 tables ............. Sec. 2.1.1, Eqs. (C),(B),(omega),(D)
  *   k = 0 reconstruction .......................... Sec. 2.1.1 (closing remark)
  *   Lax-Friedrichs flux, global alpha ............. Sec. 2.1.2, Eq. (LFflux)
+ *   Roe flux, Harten-Hyman entropy fix ............ Sec. 2.1.2, Eq. (roeflux)
  *   SSPRK3 / forward Euler ........................ Sec. 2.2, Eqs. (SSPRK3),(SSPRK1)
  *   F-/FCF-relaxation ............................. Sec. 3.2, Eq. (relaxation)
  *   injection + FAS restriction, coarse guess ..... Sec. 3.2, Eqs. (restriction::rhs),(restriction::u)
@@ -61,7 +62,7 @@
  * CUDA library, which documents the same integers in its own header */
 enum { ORC_SCHEME_WENO5_SSPRK3 = 0, ORC_SCHEME_FO_FE = 1, ORC_SCHEME_LF_FE = 2 };
 enum { ORC_FLUX_BURGERS = 0, ORC_FLUX_ADVECTION = 1 };
-enum { ORC_NUMFLUX_LF_SPLIT = 0, ORC_NUMFLUX_LF_STATE = 1 };
+enum { ORC_NUMFLUX_LF_SPLIT = 0, ORC_NUMFLUX_LF_STATE = 1, ORC_NUMFLUX_ROE = 2 };
 enum { ORC_RELAX_F = 0, ORC_RELAX_FCF = 1 };
 enum { ORC_GUESS_EQ17 = 0, ORC_GUESS_INJECT = 1 };
 enum { ORC_CYCLE_V = 0, ORC_CYCLE_F = 1 };
@@ -191,6 +192,25 @@ static void spatial_op(int nx, double dx, int scheme, int flux, int numflux,
         }
         for (int i = 0; i < nx; ++i)
             F[i] = recon_minus(k, t1, nx, i) + recon_plus(k, t2, nx, i);
+    } else if (numflux == ORC_NUMFLUX_ROE) {
+        /* Eq. (roeflux) for a scalar law on reconstructed states: Roe speed
+         * lam = (f(u+) - f(u-)) / (u+ - u-), i.e. the Roe average (u+ + u-)/2
+         * for Burgers and 1 for advection; eigenvalues at the states
+         * lam-/+ = f'(u-/+); Harten-Hyman entropy fix
+         *   delta = max(0, lam - lam-, lam+ - lam),
+         *   q = (lam^2/delta + delta)/2 if |lam| < delta, else |lam|;
+         *   F = (f(u-) + f(u+))/2 - q (u+ - u-)/2. */
+        for (int i = 0; i < nx; ++i) {
+            double um = recon_minus(k, u, nx, i), up = recon_plus(k, u, nx, i);
+            double lam = flux == ORC_FLUX_BURGERS ? 0.5 * (up + um) : 1.0;
+            double lm = flux == ORC_FLUX_BURGERS ? um : 1.0;
+            double lp = flux == ORC_FLUX_BURGERS ? up : 1.0;
+            double delta = 0.0;
+            if (lam - lm > delta) delta = lam - lm;
+            if (lp - lam > delta) delta = lp - lam;
+            double q = fabs(lam) < delta ? 0.5 * (lam * lam / delta + delta) : fabs(lam);
+            F[i] = 0.5 * (phys_flux(flux, um) + phys_flux(flux, up)) - 0.5 * q * (up - um);
+        }
     } else {
         /* Eq. (LFflux) on reconstructed states, alpha over all u^{+/-} */
         for (int i = 0; i < nx; ++i) {

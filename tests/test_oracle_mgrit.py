@@ -261,3 +261,13 @@ def test_matched_integrators_need_the_lf_fine_scheme():
     u0 = inputs.sine_ic(32)
     r = O.mgrit(u0, 64, 2, 3, 0.1, coarse=O.COARSE_PSI1)
     assert r["status"] == O.EINVAL
+
+
+@pytest.mark.parametrize("scheme", [O.SCHEME_WENO5_SSPRK3, O.SCHEME_FO_FE])
+def test_roe_flux_mgrit_converges_to_serial(scheme):
+    nx, nt, m, T = 64, 256, 4, 0.2
+    u0 = inputs.sine_ic(nx, offset=0.0)        # transonic: the entropy fix is exercised
+    r = O.mgrit(u0, nt, m, 3, T, scheme=scheme, numflux=O.NUMFLUX_ROE, tol=1e-11, max_iter=40)
+    assert r["status"] == O.OK
+    traj = serial_traj(u0, nt, T, scheme=scheme, numflux=O.NUMFLUX_ROE)
+    np.testing.assert_allclose(r["uC"], traj[::m], rtol=0, atol=1e-10)

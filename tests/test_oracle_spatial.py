@@ -312,3 +312,48 @@ def test_first_order_matching_error_is_second_order_in_dt(M):
     e0 = [np.abs(fine(dt) - O.psi_step(u, dt, M, 0)).max() for dt in (0.02 / nx, 0.01 / nx)]
     assert 3.5 < e1[0] / e1[1] < 4.5
     assert 1.7 < e0[0] / e0[1] < 2.3
+
+
+# ---- Roe flux with the Harten-Hyman entropy fix (Sec. 2.1.2, Eq. roeflux) ---
+
+def test_roe_is_upwind_for_advection():
+    # f = u: Roe speed 1, no fix, F = u^-: the same flux as the LF splitting
+    nx = 64
+    u = inputs.fourier_ic(nx, seed=2)
+    for scheme in (O.SCHEME_WENO5_SSPRK3, O.SCHEME_FO_FE):
+        a = O.spatial_op(u, scheme, O.FLUX_ADVECTION, O.NUMFLUX_ROE)
+        b = O.spatial_op(u, scheme, O.FLUX_ADVECTION, O.NUMFLUX_LF_SPLIT)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+def test_first_order_roe_burgers_is_the_upwind_godunov_flux_away_from_sonic_points():
+    # same-sign neighbours: F_{i+1/2} = f(upwind value) exactly, so on positive
+    # data A_i = -(f(u_i) - f(u_{i-1}))/dx
+    nx = 50
+    u = 1.0 + 0.5 * np.random.default_rng(3).random(nx)
+    A = O.spatial_op(u, O.SCHEME_FO_FE, O.FLUX_BURGERS, O.NUMFLUX_ROE)
+    f = 0.5 * u * u
+    np.testing.assert_allclose(A, -(f - np.roll(f, 1)) * nx, rtol=1e-13, atol=0)
+
+
+def test_entropy_fix_gives_the_godunov_flux_in_a_transonic_rarefaction():
+    # u = -a | +a (periodic, so +a | -a at the wrap): the rarefaction
+    # interface carries Godunov's f(0) = 0 (without the fix Roe would give
+    # a^2/2, an expansion shock); the stationary shock at the wrap carries
+    # f(a) = a^2/2, as do all interfaces inside the constant states
+    nx, a = 16, 0.8
+    u = np.where(np.arange(nx) < nx // 2, -a, a)
+    A = O.spatial_op(u, O.SCHEME_FO_FE, O.FLUX_BURGERS, O.NUMFLUX_ROE)
+    F = np.full(nx, a * a / 2)        # F[i] = F_{i+1/2}
+    F[nx // 2 - 1] = 0.0              # the -a | +a interface
+    np.testing.assert_allclose(A, -(F - np.roll(F, 1)) * nx, rtol=0, atol=1e-13)
+
+
+def test_roe_conserves_and_keeps_constants():
+    nx = 64
+    u = inputs.fourier_ic(nx, seed=9)
+    A = O.spatial_op(u, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, O.NUMFLUX_ROE)
+    assert abs(A.sum()) < 1e-12 * nx * nx
+    c = np.full(nx, -0.3)
+    np.testing.assert_array_equal(O.spatial_op(c, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS,
+                                               O.NUMFLUX_ROE), np.zeros(nx))
