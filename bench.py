@@ -47,6 +47,10 @@ SAMPLE = dict(nx=4096, nt=4096, m=4, levels=6, T=0.25, seed=0)   # CPU baseline 
 # + 9 (|u|, max, f = u^2/2, f^+/-) = 158; 3 stages + 12 for the RK
 # combinations = 486 (Burgers).
 FLOPS_PER_CELL_UPDATE = 486
+# adjoint gradient workload: pre-shock and post-shock final times with the
+# levels the coarse CFL allows (level-2 CFL 0.51 at T=0.12, level-1 0.32 at T=0.3)
+ADJOINT_WORKLOAD = dict(nx=2048, nt=8192, m=4, seed=1, target_seed=1001, breaking_time=0.201,
+                        cases=((0.12, 3), (0.3, 2)))
 
 # FP64 peak of the SIMT pipe, from the unit counts and clocks: 152 SMs x
 # 2.07 GHz x 4 FP64 FLOP/clk/SM (the nominal 1.25 TFLOP/s FP64 rate).
@@ -76,6 +80,9 @@ def parse():
     p.add_argument("--impl", default="mgrit", choices=["mgrit", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch line")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient line")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the paper's coarse-integrator / relaxation / cycle comparisons")
     return p.parse_args()
 
 
@@ -208,6 +215,109 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- GPU ---
+
+def adjoint_gradient(mgrit, inputs, dev, stream):
+    """dJ/du0 of J = 1/2 ||u(T) - u_target||^2 (Burgers, nx=2048, nt=8192,
+    m=4, FP64; u0 seed 1, breaking time 0.20; u_target = forward solution from
+    seed 1001) at the pre-shock T=0.12 and the post-shock T=0.3: forward
+    MGRIT to tol, adjoint MGRIT from its C-point checkpoints, against the
+    serial adjoint (C-point checkpointing, one CTA) and serial stepping."""
+    import torch
+    W = ADJOINT_WORKLOAD
+    u0 = torch.as_tensor(inputs.fourier_ic(W["nx"], seed=W["seed"]), device=dev)
+    ut0 = torch.as_tensor(inputs.fourier_ic(W["nx"], seed=W["target_seed"]), device=dev)
+    out = {"workload": "J = 1/2 ||u(T) - u_target||^2, Burgers WENO5-JS/LF-split/SSPRK3 FP64, "
+                       "nx=2048, nt=8192, m=4, FCF, tol 1e-10; u0 Fourier seed 1 (breaks at "
+                       "t=0.20), u_target from seed 1001", "runs": []}
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    for T, L in W["cases"]:
+        s = mgrit.Solver(W["nx"], W["nt"], W["m"], L, T=T, max_iter=120)
+        target = s.serial_step(ut0, W["nt"])
+        s.solve(u0)                                   # warm-up: allocation and graph capture
+        (st, uT, uC, fst), fwd_ms = timed(lambda: s.solve(u0))
+        lamT = (uT - target).contiguous()
+        s.adjoint(uC, lamT)                           # warm-up: adjoint workspaces and graphs
+        (ast, g, _, ast_stats), adj_ms = timed(lambda: s.adjoint(uC, lamT))
+        uT_ser, ser_ms = timed(lambda: s.serial_step(u0, W["nt"]))
+        lam_ser = (uT_ser - target).contiguous()
+        g_ser, aser_ms = timed(lambda: s.adjoint_serial(u0, lam_ser))
+        rel = float((g - g_ser).abs().max() / g_ser.abs().max())
+        out["runs"].append({
+            "T": T, "levels": L, "shock": T > W["breaking_time"],
+            "forward": {"status": mgrit.STATUS_NAMES[st], "cycles": fst.iters, "ms": fwd_ms},
+            "adjoint_mgrit": {"status": mgrit.STATUS_NAMES[ast], "cycles": ast_stats.iters,
+                              "ms": adj_ms,
+                              "vjp_cell_updates_per_s": ast_stats.cell_updates / (adj_ms / 1e3)},
+            "serial": {"forward_ms": ser_ms, "adjoint_ms": aser_ms},
+            "gradient_ms": fwd_ms + adj_ms, "serial_gradient_ms": ser_ms + aser_ms,
+            "rel_max_diff_vs_serial_adjoint": rel,
+            "J": 0.5 * float((lamT ** 2).sum())})
+        s.close()
+    return out
+
+
+def paper_variants(mgrit, inputs, dev):
+    """The paper's Sec. 4 comparisons on the GPU, on its setting: Burgers with
+    the classical Lax-Friedrichs + FE fine scheme (Eq. fineLF), nx=128,
+    nt=1024, T=0.475, m=2, 5 levels (coarsest CFL 0.95), F-relaxation,
+    V-cycle; stationary (sin 2 pi x) and moving ((1 + sin 2 pi x)/2) shocks.
+    (1) relative space-time L2 error of the level-0 C-points against serial
+    stepping after each of the first 8 cycles, for rediscretised, Psi0 and
+    Psi1 coarse integrators; (2) cycles to ||r|| < 1e-10 with Psi1 for F/FCF
+    relaxation x Eq. (restriction::u)/injection x V/F-cycle."""
+    import torch
+    nx, nt, m, L, T = 128, 1024, 2, 5, 0.475
+    nC = nt // m
+    out = {"setting": "Burgers, classical LF + FE, nx=128, nt=1024, T=0.475, m=2, 5 levels",
+           "error_per_cycle": {}, "cycles_to_tol_psi1": {}}
+    names = {mgrit.COARSE_REDISC: "rediscretised", mgrit.COARSE_PSI0: "psi0",
+             mgrit.COARSE_PSI1: "psi1"}
+    for ic, (off, amp) in (("stationary", (0.0, 1.0)), ("moving", (0.5, 0.5))):
+        u0 = torch.as_tensor(inputs.sine_ic(nx, offset=off, amp=amp), device=dev)
+        s = mgrit.Solver(nx, nt, m, L, mgrit.LF_FE, mgrit.BURGERS, T=T)
+        ser = torch.empty((nC + 1, nx), dtype=torch.float64, device=dev)
+        ser[0] = u0
+        for i in range(nC):                         # serial C-points, m steps at a time
+            ser[i + 1] = s.serial_step(ser[i].contiguous(), m)
+        norm = float(ser.norm())
+        s.close()
+        res = {}
+        for coarse, name in names.items():
+            s = mgrit.Solver(nx, nt, m, L, mgrit.LF_FE, mgrit.BURGERS, T=T, relax=mgrit.RELAX_F,
+                             coarse=coarse)
+            errs = []
+            for k in range(1, 9):
+                s.run_cycles(u0, k)
+                e = float((s.cpoints() - ser).norm()) / norm
+                errs.append(e if e == e and e != float("inf") else None)
+            res[name] = errs
+            s.close()
+        out["error_per_cycle"][ic] = res
+        for relax in (mgrit.RELAX_F, mgrit.RELAX_FCF):
+            for guess in (mgrit.GUESS_EQ17, mgrit.GUESS_INJECT):
+                for cycle in (mgrit.CYCLE_V, mgrit.CYCLE_F):
+                    s = mgrit.Solver(nx, nt, m, L, mgrit.LF_FE, mgrit.BURGERS, T=T, relax=relax,
+                                     guess=guess, cycle=cycle, coarse=mgrit.COARSE_PSI1,
+                                     max_iter=60)
+                    st, _, _, stats = s.solve(u0, want_uC=False)
+                    key = "%s/%s/%s" % ("FCF" if relax else "F", "inject" if guess else "eq17",
+                                        "F-cycle" if cycle else "V-cycle")
+                    out["cycles_to_tol_psi1"].setdefault(ic, {})[key] = {
+                        "status": mgrit.STATUS_NAMES[st], "cycles": stats.iters,
+                        "ms": stats.t_total_ms}
+                    s.close()
+    return out
+
 
 def run_mgrit(args):
     import torch
@@ -423,6 +533,9 @@ def run_mgrit(args):
                    "one_context_at_a_time_ms_per_cycle": mss / args.steps,
                    "speedup_vs_one_at_a_time": mss / msb, "autotune_seconds": tune_s}
 
+    adjoint = None if args.no_adjoint else adjoint_gradient(mgrit, inputs, dev, stream)
+    variants = None if args.no_variants else paper_variants(mgrit, inputs, dev)
+
     if rank != 0:
         if ws > 1:
             tdist.destroy_process_group()
@@ -467,6 +580,8 @@ def run_mgrit(args):
         "time_to_tol_cfl_capped": ttt,
         "fp32_sweeps": fp32,
         "batched": batched,
+        "adjoint": adjoint,
+        "paper_variants": variants,
     }
     print(json.dumps(line))
     if ws > 1:

@@ -46,26 +46,42 @@ enum {
     MGRIT_ETIMEOUT = -6    /* reserved: a bounded device wait gave up */
 };
 
-/* spatial reconstruction + time integrator (Sec. 2.1.1, Sec. 2.2) */
-enum { MGRIT_WENO5_SSPRK3 = 0, MGRIT_FO_FE = 1 };
+/* spatial reconstruction + time integrator (Sec. 2.1.1, Sec. 2.2), or the
+ * classical Lax-Friedrichs + forward Euler scheme of Sec. 3.3 Eq. (fineLF),
+ * u_i <- (u_{i+1} + u_{i-1})/2 - dt (f(u_{i+1}) - f(u_{i-1}))/(2 dx)
+ * (FP64, single-CTA sequential solves; numflux does not apply) */
+enum { MGRIT_WENO5_SSPRK3 = 0, MGRIT_FO_FE = 1, MGRIT_LF_FE = 2 };
 /* physical flux f (Sec. 2): Burgers u^2/2, or linear advection with speed 1 */
 enum { MGRIT_BURGERS = 0, MGRIT_ADVECTION = 1 };
 /* numerical flux (Sec. 2.1.2): global Lax-Friedrichs splitting
  * f^{+/-} = (f(u) +/- alpha u)/2 reconstructed left/right-biased, or the
  * state form of Eq. (LFflux) with the dissipative sign; alpha is the
  * global maximum of |f'| over the stage input (split) or over all
- * reconstructed states (state form), recomputed at every RK stage */
-enum { MGRIT_LF_SPLIT = 0, MGRIT_LF_STATE = 1 };
+ * reconstructed states (state form), recomputed at every RK stage; or
+ * Roe's flux on the reconstructed states with the Harten-Hyman entropy fix
+ * (Eq. roeflux; Roe speed (u^+ + u^-)/2 for Burgers, 1 for advection):
+ * F = (f(u^-) + f(u^+))/2 - q (u^+ - u^-)/2 with q = |lam|, or
+ * (lam^2/delta + delta)/2 when |lam| < delta = max(0, lam - f'(u^-), f'(u^+) - lam) */
+enum { MGRIT_LF_SPLIT = 0, MGRIT_LF_STATE = 1, MGRIT_ROE = 2 };
 enum { MGRIT_RELAX_F = 0, MGRIT_RELAX_FCF = 1 };         /* Sec. 3.2 */
 enum { MGRIT_GUESS_EQ17 = 0, MGRIT_GUESS_INJECT = 1 };   /* Eq. restriction::u */
+enum { MGRIT_CYCLE_V = 0, MGRIT_CYCLE_F = 1 };           /* Algorithm 1; Sec. 3.2 */
+/* coarse integrators (Sec. 3.3): rediscretisation with dt m^l, or, for
+ * MGRIT_LF_FE, the integrators matched to M = m^l fine steps (dt the fine step):
+ *   PSI0  E^M u - M dt D f(u)                          (Eq. coarseLFord0)
+ *   PSI1  E^M u - dt sum_{i=1..M} E^{i-1} D f(E^{M-i} u)  (Eqs. coarseLFord1, fineLFxM)
+ * with (E v)_i = (v_{i+1} + v_{i-1})/2 and (D v)_i = (v_{i+1} - v_{i-1})/(2 dx) */
+enum { MGRIT_COARSE_REDISC = 0, MGRIT_COARSE_PSI0 = 1, MGRIT_COARSE_PSI1 = 2 };
 
 typedef struct {
     double T;        /* final time (default 1) */
     double L;        /* domain length (default 1) */
     int relax;       /* MGRIT_RELAX_F / MGRIT_RELAX_FCF (default FCF) */
-    int cycle;       /* 0 = V-cycle (Algorithm 1); the only value accepted */
+    int cycle;       /* MGRIT_CYCLE_V (Algorithm 1, default) or MGRIT_CYCLE_F (the
+                        F-cycle of Sec. 3.2: below each level an F-cycle, then
+                        one V-cycle; batches accept V only) */
     int guess;       /* MGRIT_GUESS_EQ17 (default) / MGRIT_GUESS_INJECT */
-    int numflux;     /* MGRIT_LF_SPLIT (default) / MGRIT_LF_STATE */
+    int numflux;     /* MGRIT_LF_SPLIT (default) / MGRIT_LF_STATE / MGRIT_ROE */
     double tol;      /* stop when the level-0 residual 2-norm < tol (default 1e-10) */
     int max_iter;    /* cycles before MGRIT_ENOTCONV (default 64, at most 254) */
     int precision;   /* 64: every sweep in FP64 (default when nx fits an FP64 slab).
@@ -74,11 +90,14 @@ typedef struct {
                         the coarsest sequential solve stay FP64.  The FP64
                         residual of an FP32 iteration levels off near FP32
                         rounding, so a solve also stops (MGRIT_OK, stats.stagnated
-                        = 1) once two cycles reduce it by less than 10 %. */
+                        = 1) once two cycles reduce it by less than 10 %.
+                        MGRIT_LF_FE accepts 64 only. */
+    int coarse;      /* MGRIT_COARSE_REDISC (default), or PSI0 / PSI1 with the
+                        MGRIT_LF_FE scheme (MGRIT_EINVAL otherwise) */
 } mgrit_params;
 
 typedef struct {
-    int iters;            /* completed V-cycles when the solve stopped */
+    int iters;            /* completed cycles when the solve stopped */
     int status;           /* same code as the return value */
     double res_hist[256]; /* res_hist[k] = residual 2-norm after the level-0
                              relaxation of cycle k, k = 0..iters */
@@ -94,7 +113,7 @@ void mgrit_default_params(mgrit_params *p);
  * Create a solver for nx cells, nt fine steps, coarsening factor m and
  * `levels` time levels (level l has nt/m^l steps).  Requires m >= 2,
  * levels >= 2, nt divisible by m^(levels-1), nx >= 5 (WENO5) or nx >= 3
- * (first order), and nx within the single-CTA slab limit of the build
+ * (first order, classical Lax-Friedrichs), and nx within the single-CTA slab limit of the build
  * (MGRIT_EINVAL otherwise).  Device memory is allocated on the current
  * device at the first solve.  Sec. 3.1 (C/F splitting, time chunks of m
  * steps); Eq. (monolithicSystem) for nt and the time grid.
@@ -202,8 +221,63 @@ int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numfl
  * first call that allocates (0 before).  -1 for an unknown `what`. */
 int mgrit_query(const mgrit_ctx *ctx, int what);
 
-/* Cells x Phi applications of one V-cycle (for throughput figures). */
+/* Cells x Phi applications of one cycle (V or F, for throughput figures). */
 double mgrit_cycle_cell_updates(const mgrit_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Discrete adjoint (the paper has no adjoint: these entry points
+ * differentiate the discrete scheme above, for gradients of an objective
+ * J(u^nt) with respect to u^0).  The transpose of the derivative of one step
+ * Phi (Eq. SSPRK3 or SSPRK1, through Eq. spaceDisc, the WENO weights of
+ * Sec. 2.1.1 and the global Lax-Friedrichs splitting of Sec. 2.1.2, with
+ * alpha = max|f'| differentiated at its first maximising cell) is applied
+ * stage by stage with the forward stage states recomputed.  Split numerical
+ * flux only (MGRIT_LF_SPLIT; MGRIT_EINVAL otherwise); FP64 in every
+ * precision mode; nx <= 4096 (the adjoint slab's shared memory), else
+ * MGRIT_EINVAL.  Workspaces (the regenerated fine trajectory, nt x nx, and
+ * the adjoint levels) are allocated on the first call.
+ * ------------------------------------------------------------------------ */
+
+/* out_dev = Phi'(u_dev)^T lam_dev for one fine step (dt = T/nt).  Each
+ * argument holds nx values; any of them may alias.  Asynchronous. */
+int mgrit_step_vjp(mgrit_ctx *ctx, const double *u_dev, const double *lam_dev, double *out_dev,
+                   void *stream);
+
+/* Serial adjoint with C-point checkpointing: lam0_dev = dJ/du^0 given
+ * lamT_dev = dJ/du^nt, through nt fine steps from u0_dev.  One CTA steps
+ * forward keeping u^{mj}, j < nt/m, then for each chunk from the last it
+ * recomputes the chunk's m states from its checkpoint and applies their m
+ * transposed steps backward.  Asynchronous.  Baseline for mgrit_adjoint. */
+int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const double *lamT_dev,
+                         double *lam0_dev, void *stream);
+
+/*
+ * Adjoint MGRIT: lam^n = Phi'(u^n)^T lam^{n+1}, lam^nt = lamT_dev, solved
+ * backward in time by the V-cycle of Algorithm 1 (same levels, m, relax,
+ * guess, tol, max_iter as the context).  In reversed time k = nt - n the
+ * system has the block-bidiagonal form of Eq. (monolithicSystem), so the
+ * V-cycle applies unchanged with the propagator of level l = the transposed
+ * linearisation of Phi_l (step dt m^l) at the forward state of the coarse
+ * point: the fine states on level 0 and the injected forward C-states on
+ * the coarse levels.
+ *   uC_dev    forward C-point checkpoints ((nt/m + 1) x nx), e.g. the uC
+ *             output of mgrit_solve; the fine states between them are
+ *             regenerated by one parallel launch (u^{mj+r} = Phi^r(uC_j))
+ *   lamT_dev  dJ/du^nt (nx)
+ *   lam0_dev  output dJ/du^0 (nx), may be NULL
+ *   lamC_dev  output (nt/m + 1) x nx, row i = lam at forward point m i,
+ *             may be NULL
+ * The residual is the level-0 adjoint residual after each relaxation, with
+ * the stopping, divergence and iteration rules of mgrit_solve.  Returns
+ * MGRIT_OK, MGRIT_EDIVERGED or MGRIT_ENOTCONV (outputs written in all
+ * three cases) or an error.  Synchronises `stream` once per cycle.
+ */
+int mgrit_adjoint(mgrit_ctx *ctx, const double *uC_dev, const double *lamT_dev, double *lam0_dev,
+                  double *lamC_dev, void *stream, mgrit_stats *stats);
+
+/* Adjoint launch shape: what = 0 cells per thread, 1 threads per CTA
+ * (0 when the context's nx or numerical flux has no adjoint); -1 otherwise. */
+int mgrit_adjoint_query(const mgrit_ctx *ctx, int what);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent problems advanced together (the paper treats

@@ -3,6 +3,7 @@ import os
 import shutil
 import subprocess
 import sys
+import time
 from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
@@ -53,14 +54,19 @@ def build(force=False, verbose=False, extra=(), debug=False):
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
             jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
 
+    times = {}
+
     def run(cmd):
+        t0 = time.time()
         r = subprocess.run(cmd, capture_output=True, text=True)
+        times[os.path.basename(cmd[-3]) if cmd[-4] == "-c" else "link"] = time.time() - t0
         if verbose or r.returncode:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         if r.returncode:
             raise RuntimeError("nvcc failed for " + cmd[-3])
         return r.stdout + r.stderr
 
+    t_start = time.time()
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             outs = list(ex.map(run, jobs))
@@ -70,6 +76,11 @@ def build(force=False, verbose=False, extra=(), debug=False):
         tmp = lib + ".tmp.%d" % os.getpid()
         run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
         os.replace(tmp, lib)
+    if times:
+        slow = sorted(times.items(), key=lambda kv: -kv[1])[:4]
+        sys.stderr.write("[build] %s: %d jobs in %.0f s; slowest %s\n" % (
+            os.path.basename(lib), len(times), time.time() - t_start,
+            ", ".join("%s %.0f s" % kv for kv in slow)))
     return "".join(outs)
 
 

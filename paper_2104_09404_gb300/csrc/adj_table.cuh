@@ -1,0 +1,38 @@
+// Table of adjoint kernel instances (FP64), indexed by [scheme][flux][cells-per-thread].
+#pragma once
+#include "adjoint.cuh"
+
+namespace mgrit {
+
+constexpr int NCPT_ADJ = 4;   // 1, 2, 4, 8 cells per thread: nx <= 4096 at 512 threads
+
+struct AdjTable {
+    const void *k[2][2][NCPT_ADJ];
+};
+
+template <int S, int F>
+void fill_adj_sf(AdjTable &t)
+{
+    t.k[S][F][0] = (const void *)&k_adjoint<S, F, 1>;
+    t.k[S][F][1] = (const void *)&k_adjoint<S, F, 2>;
+    t.k[S][F][2] = (const void *)&k_adjoint<S, F, 4>;
+    t.k[S][F][3] = (const void *)&k_adjoint<S, F, 8>;
+}
+
+// one translation unit per (scheme, flux) group, compiled in parallel
+void fill_adj_weno_burgers(AdjTable &t);
+void fill_adj_weno_advection(AdjTable &t);
+void fill_adj_fo(AdjTable &t);
+
+// dst row (nrows-1-r) = src row r, r = 0..nrows-1 (dst must not alias src)
+cudaError_t launch_reverse_rows(const double *src, double *dst, long long nrows, int nx,
+                                cudaStream_t s);
+
+inline void fill_adj_all(AdjTable &t)
+{
+    fill_adj_weno_burgers(t);
+    fill_adj_weno_advection(t);
+    fill_adj_fo(t);
+}
+
+}  // namespace mgrit

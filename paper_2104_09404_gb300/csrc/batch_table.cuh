@@ -29,8 +29,11 @@ void fill_batch_cluster(const void *(&t)[2][2])
     t[F][1] = (const void *)&k_seq_cluster_batch<double, SCH_WENO5_SSPRK3, F, 2>;
 }
 
-void fill_batch_f32(BatchTable &t);
-void fill_batch_f64(BatchTable &t);
+// one translation unit per (precision, flux), compiled in parallel
+void fill_batch_f32_burgers(BatchTable &t);
+void fill_batch_f32_advection(BatchTable &t);
+void fill_batch_f64_burgers(BatchTable &t);
+void fill_batch_f64_advection(BatchTable &t);
 
 // batched restriction / norm / conversion launchers (batch_ops.cu)
 cudaError_t launch_restrict_batch(const RestrictBatchArgs *args, const BatchItem *map, int nblocks,

@@ -23,65 +23,15 @@
 #include <cstring>
 #include <new>
 
-#include "../../include/mgrit.h"
+#include "ctx.cuh"
 #include "kernel_table.cuh"
 #include "restrict.cuh"
 
 using namespace mgrit;
 
-namespace {
-
-constexpr int MAXLEV = 32;
-
-struct Launch {
-    const void *slab;   // k_slab instance for (precision, scheme, flux, cells per thread); null: unsupported
-    int threads;
-    int cpt;
-    size_t smem;
-};
-
-// sequential stepping on a thread-block cluster (coarsest solve, serial stepper)
-struct ClusterLaunch {
-    const void *fn;     // k_seq_cluster instance; null: single-CTA k_slab
-    int K;              // CTAs in the cluster
-    int cpt;            // cells per thread (1 or 2)
-    int threads;
-    size_t smem;
-};
-
-}  // namespace
-
-struct mgrit_ctx {
-    int nx, nt, m, L, scheme, flux;
-    mgrit_params p;
-    int nt_l[MAXLEV], nC_l[MAXLEV];
-    double dt_l[MAXLEV];
-    Launch ln64, ln32;
-    ClusterLaunch lc64, lc32;
-    int f32;             // precision the workspaces were allocated for (1: FP32 sweeps)
-    bool alloc;
-    bool prepared;       // workspaces, graphs and an initial iterate exist
-    bool have_state;     // a level-0 relaxation has produced newC[0]
-    int device;
-    void *u[MAXLEV];
-    double *g[MAXLEV];
-    void *newC[MAXLEV], *phirow[MAXLEV], *cstep[MAXLEV];
-    float *u32c;         // FP32 mirror of the coarsest rows (FP32-sweep mode)
-    float *ser32;        // one FP32 row for the FP32 serial stepper
-    double *resid_rows;  // mgrit_residual scratch ((nt/m+1) rows, FP64)
-    double *partials;
-    int nparts;
-    double *d_norm;
-    double *h_norm;
-    cudaStream_t cap;
-    cudaGraphExec_t gA, gB;
-    cudaEvent_t ev0, ev1;
-    char err[256];
-};
-
 static char g_create_err[256] = "";
 
-static int fail(mgrit_ctx *c, int code, const char *fmt, ...)
+int mgrit_fail(mgrit_ctx *c, int code, const char *fmt, ...)
 {
     char *buf = c ? c->err : g_create_err;
     va_list ap;
@@ -90,14 +40,6 @@ static int fail(mgrit_ctx *c, int code, const char *fmt, ...)
     va_end(ap);
     return code;
 }
-
-#define CK(call)                                                                       \
-    do {                                                                               \
-        cudaError_t e_ = (call);                                                       \
-        if (e_ != cudaSuccess)                                                         \
-            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MGRIT_ENOMEM : MGRIT_ECUDA, \
-                        "%s: %s", #call, cudaGetErrorString(e_));                      \
-    } while (0)
 
 static const KernelTable &table()
 {
@@ -125,7 +67,7 @@ static bool choose_launch(int nx, int scheme, int flux, int f32, Launch *ln)
             ln->threads = ((need + 31) / 32) * 32;
             ln->smem = smem;
             ln->slab = f32 ? table().slab32[scheme][flux][ci] : table().slab64[scheme][flux][ci];
-            return true;
+            return ln->slab != nullptr;
         }
     }
     return false;
@@ -148,28 +90,36 @@ extern "C" void mgrit_default_params(mgrit_params *p)
     p->tol = 1e-10;
     p->max_iter = 64;
     p->precision = 64;
+    p->coarse = MGRIT_COARSE_REDISC;
 }
 
 static int check_params(mgrit_ctx *ctx, const mgrit_params *p)
 {
     if (!(p->T > 0) || !(p->L > 0) || !std::isfinite(p->T) || !std::isfinite(p->L))
-        return fail(ctx, MGRIT_EINVAL, "T and L must be positive and finite");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "T and L must be positive and finite");
     if (p->relax != MGRIT_RELAX_F && p->relax != MGRIT_RELAX_FCF)
-        return fail(ctx, MGRIT_EINVAL, "relax must be F (0) or FCF (1)");
-    if (p->cycle != 0) return fail(ctx, MGRIT_EINVAL, "only the V-cycle (0) is built");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "relax must be F (0) or FCF (1)");
+    if (p->cycle != MGRIT_CYCLE_V && p->cycle != MGRIT_CYCLE_F)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "cycle must be V (0) or F (1)");
     if (p->guess != MGRIT_GUESS_EQ17 && p->guess != MGRIT_GUESS_INJECT)
-        return fail(ctx, MGRIT_EINVAL, "guess must be 0 or 1");
-    if (p->numflux != MGRIT_LF_SPLIT && p->numflux != MGRIT_LF_STATE)
-        return fail(ctx, MGRIT_EINVAL, "numflux must be 0 or 1");
-    if (!(p->tol >= 0)) return fail(ctx, MGRIT_EINVAL, "tol must be >= 0");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "guess must be 0 or 1");
+    if (p->numflux != MGRIT_LF_SPLIT && p->numflux != MGRIT_LF_STATE && p->numflux != MGRIT_ROE)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "numflux must be 0, 1 or 2");
+    if (!(p->tol >= 0)) return mgrit_fail(ctx, MGRIT_EINVAL, "tol must be >= 0");
     if (p->max_iter < 0 || p->max_iter > 254)
-        return fail(ctx, MGRIT_EINVAL, "max_iter must be in [0, 254]");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "max_iter must be in [0, 254]");
     if (p->precision != 64 && p->precision != 32)
-        return fail(ctx, MGRIT_EINVAL, "precision must be 64 or 32");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "precision must be 64 or 32");
+    if (p->coarse < MGRIT_COARSE_REDISC || p->coarse > MGRIT_COARSE_PSI1)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "coarse must be 0, 1 or 2");
+    if (ctx && p->coarse != MGRIT_COARSE_REDISC && ctx->scheme != MGRIT_LF_FE)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "matched coarse integrators need the MGRIT_LF_FE scheme");
+    if (ctx && ctx->scheme == MGRIT_LF_FE && p->precision != 64)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "the MGRIT_LF_FE scheme runs in FP64 only");
     if (p->precision == 64 && !ctx->ln64.slab)
-        return fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 single-CTA slab limit", ctx->nx);
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 single-CTA slab limit", ctx->nx);
     if (p->precision == 32 && !ctx->ln32.slab)
-        return fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP32 single-CTA slab limit", ctx->nx);
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP32 single-CTA slab limit", ctx->nx);
     return MGRIT_OK;
 }
 
@@ -186,28 +136,28 @@ extern "C" int mgrit_create(mgrit_ctx **out, int nx, int nt, int m, int levels, 
                             int flux)
 {
     mgrit_ctx *ctx = nullptr;
-    if (!out) return fail(ctx, MGRIT_EINVAL, "out is NULL");
+    if (!out) return mgrit_fail(ctx, MGRIT_EINVAL, "out is NULL");
     *out = nullptr;
-    if (scheme != MGRIT_WENO5_SSPRK3 && scheme != MGRIT_FO_FE)
-        return fail(ctx, MGRIT_EINVAL, "unknown scheme %d", scheme);
+    if (scheme != MGRIT_WENO5_SSPRK3 && scheme != MGRIT_FO_FE && scheme != MGRIT_LF_FE)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "unknown scheme %d", scheme);
     if (flux != MGRIT_BURGERS && flux != MGRIT_ADVECTION)
-        return fail(ctx, MGRIT_EINVAL, "unknown flux %d", flux);
-    if (m < 2) return fail(ctx, MGRIT_EINVAL, "m must be >= 2");
-    if (levels < 2 || levels >= MAXLEV) return fail(ctx, MGRIT_EINVAL, "levels must be in [2, 31]");
-    if (nt < 1) return fail(ctx, MGRIT_EINVAL, "nt must be >= 1");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "unknown flux %d", flux);
+    if (m < 2) return mgrit_fail(ctx, MGRIT_EINVAL, "m must be >= 2");
+    if (levels < 2 || levels >= MAXLEV) return mgrit_fail(ctx, MGRIT_EINVAL, "levels must be in [2, 31]");
+    if (nt < 1) return mgrit_fail(ctx, MGRIT_EINVAL, "nt must be >= 1");
     if (nx < (scheme == MGRIT_WENO5_SSPRK3 ? 5 : 3))
-        return fail(ctx, MGRIT_EINVAL, "nx too small for the scheme");
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx too small for the scheme");
     long long div = 1;
     for (int l = 0; l < levels - 1; ++l) div *= m;
-    if (div > nt || nt % div) return fail(ctx, MGRIT_EINVAL, "nt must be divisible by m^(levels-1)");
+    if (div > nt || nt % div) return mgrit_fail(ctx, MGRIT_EINVAL, "nt must be divisible by m^(levels-1)");
     Launch ln64, ln32;
     const bool ok64 = choose_launch(nx, scheme, flux, 0, &ln64);
     const bool ok32 = choose_launch(nx, scheme, flux, 1, &ln32);
     if (!ok64 && !ok32)
-        return fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the single-CTA slab limit", nx);
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the single-CTA slab limit", nx);
 
     ctx = new (std::nothrow) mgrit_ctx;
-    if (!ctx) return fail(nullptr, MGRIT_ENOMEM, "host allocation failed");
+    if (!ctx) return mgrit_fail(nullptr, MGRIT_ENOMEM, "host allocation failed");
     memset(ctx, 0, sizeof *ctx);
     ctx->nx = nx;
     ctx->nt = nt;
@@ -232,6 +182,7 @@ extern "C" int mgrit_create(mgrit_ctx **out, int nx, int nt, int m, int levels, 
 
 static void free_workspaces(mgrit_ctx *ctx)
 {
+    mgrit_adj_free(ctx);
     if (ctx->gA) cudaGraphExecDestroy(ctx->gA);
     if (ctx->gB) cudaGraphExecDestroy(ctx->gB);
     ctx->gA = ctx->gB = nullptr;
@@ -264,7 +215,7 @@ static void free_workspaces(mgrit_ctx *ctx)
 
 extern "C" int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p)
 {
-    if (!ctx || !p) return fail(ctx, MGRIT_EINVAL, "NULL argument");
+    if (!ctx || !p) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
     int st = check_params(ctx, p);
     if (st) return st;
     const bool same_graph = ctx->p.T == p->T && ctx->p.L == p->L && ctx->p.relax == p->relax &&
@@ -282,7 +233,7 @@ extern "C" int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p)
     return MGRIT_OK;
 }
 
-static int dalloc(mgrit_ctx *ctx, void **ptr, size_t rows, size_t elem)
+int mgrit_dalloc(mgrit_ctx *ctx, void **ptr, size_t rows, size_t elem)
 {
     CK(cudaMalloc(ptr, elem * rows * (size_t)ctx->nx));
     return MGRIT_OK;
@@ -297,6 +248,7 @@ static bool level_f32(const mgrit_ctx *ctx, int l) { return ctx->f32 && l < ctx-
 static void choose_cluster(mgrit_ctx *ctx, int f32, ClusterLaunch *lc)
 {
     lc->fn = nullptr;
+    if (ctx->scheme == MGRIT_LF_FE) return;   // single-CTA kernel only
     const int nx = ctx->nx;
     int K = 1;
     while (K < CLUSTER_MAX && nx / (2 * K) >= 256) K *= 2;
@@ -358,7 +310,7 @@ static cudaError_t launch_seq(const ClusterLaunch &lc, const Launch &ln, cudaStr
     return cudaLaunchKernelExC(&cfg, lc.fn, args);
 }
 
-static int ensure_alloc(mgrit_ctx *ctx)
+int mgrit_ensure_alloc(mgrit_ctx *ctx)
 {
     if (ctx->alloc) return MGRIT_OK;
     CK(cudaGetDevice(&ctx->device));
@@ -367,18 +319,18 @@ static int ensure_alloc(mgrit_ctx *ctx)
     const size_t es = ctx->f32 ? sizeof(float) : sizeof(double);
     int st;
     for (int l = 0; l < L - 1; ++l) {
-        if ((st = dalloc(ctx, &ctx->newC[l], ctx->nC_l[l] + 1, es))) return st;
-        if ((st = dalloc(ctx, &ctx->phirow[l], ctx->nC_l[l] + 1, es))) return st;
-        if ((st = dalloc(ctx, &ctx->cstep[l], ctx->nC_l[l], es))) return st;
+        if ((st = mgrit_dalloc(ctx, &ctx->newC[l], ctx->nC_l[l] + 1, es))) return st;
+        if ((st = mgrit_dalloc(ctx, &ctx->phirow[l], ctx->nC_l[l] + 1, es))) return st;
+        if ((st = mgrit_dalloc(ctx, &ctx->cstep[l], ctx->nC_l[l], es))) return st;
     }
     for (int l = 1; l < L; ++l) {
         const size_t el = level_f32(ctx, l) ? sizeof(float) : sizeof(double);
-        if ((st = dalloc(ctx, &ctx->u[l], ctx->nt_l[l] + 1, el))) return st;
-        if ((st = dalloc(ctx, (void **)&ctx->g[l], ctx->nt_l[l] + 1, sizeof(double)))) return st;
+        if ((st = mgrit_dalloc(ctx, &ctx->u[l], ctx->nt_l[l] + 1, el))) return st;
+        if ((st = mgrit_dalloc(ctx, (void **)&ctx->g[l], ctx->nt_l[l] + 1, sizeof(double)))) return st;
     }
     if (ctx->f32) {
-        if ((st = dalloc(ctx, (void **)&ctx->u32c, ctx->nt_l[L - 1] + 1, sizeof(float)))) return st;
-        if ((st = dalloc(ctx, (void **)&ctx->ser32, 1, sizeof(float)))) return st;
+        if ((st = mgrit_dalloc(ctx, (void **)&ctx->u32c, ctx->nt_l[L - 1] + 1, sizeof(float)))) return st;
+        if ((st = mgrit_dalloc(ctx, (void **)&ctx->ser32, 1, sizeof(float)))) return st;
     }
     ctx->nparts = restrict_blocks(ctx->nC_l[0], ctx->nx);
     CK(cudaMalloc((void **)&ctx->partials, sizeof(double) * ctx->nparts));
@@ -396,7 +348,7 @@ static int ensure_alloc(mgrit_ctx *ctx)
     choose_cluster(ctx, 0, &ctx->lc64);
     if (ctx->f32) choose_cluster(ctx, 1, &ctx->lc32);
     if (!ctx->ln64.slab && !ctx->lc64.fn)
-        return fail(ctx, MGRIT_EINVAL, "no FP64 slab or cluster fits nx = %d for the coarsest solve",
+        return mgrit_fail(ctx, MGRIT_EINVAL, "no FP64 slab or cluster fits nx = %d for the coarsest solve",
                     ctx->nx);
     ctx->alloc = true;
     return MGRIT_OK;
@@ -418,6 +370,15 @@ static SlabArgs<R> base_args(const mgrit_ctx *ctx, int mode, int l)
     a.dxinv = (R)(ctx->nx / ctx->p.L);
     a.dt = (R)ctx->dt_l[l];
     a.dtc = (R)(l + 1 < ctx->L ? ctx->dt_l[l + 1] : 0.0);
+    if (ctx->p.coarse != MGRIT_COARSE_REDISC) {
+        // matched integrators on the coarse levels: level k integrates m^k fine steps
+        int M = 1;
+        for (int k = 0; k < l; ++k) M *= ctx->m;
+        a.psiM = l == 0 ? 0 : M;
+        a.psiMc = M * ctx->m;
+        a.psiOrder = ctx->p.coarse == MGRIT_COARSE_PSI1 ? 1 : 0;
+        a.psiDt = (R)ctx->dt_l[0];
+    }
     return a;
 }
 
@@ -545,17 +506,45 @@ static cudaError_t enqueue_part_a(mgrit_ctx *ctx, cudaStream_t s)
     return launch_norm(ctx->partials, ctx->nparts, ctx->d_norm, s);
 }
 
+// Launch order below level 0: the V-cycle of Algorithm 1 (relax, restrict,
+// recurse, interpolate) or the F-cycle (below each level an F-cycle, then
+// one V-cycle), for any set of level operations
+struct CycleOps {
+    cudaError_t (*relax)(mgrit_ctx *, int, cudaStream_t);
+    cudaError_t (*restrict_)(mgrit_ctx *, int, cudaStream_t);
+    cudaError_t (*coarse)(mgrit_ctx *, cudaStream_t);
+    cudaError_t (*interp)(mgrit_ctx *, int, cudaStream_t);
+};
+
+static cudaError_t emit_cycle(mgrit_ctx *ctx, const CycleOps &o, int l, bool fcycle, cudaStream_t s)
+{
+    if (l == ctx->L - 1) return o.coarse(ctx, s);
+    cudaError_t e;
+    if ((e = o.relax(ctx, l, s))) return e;
+    if ((e = o.restrict_(ctx, l, s))) return e;
+    if ((e = emit_cycle(ctx, o, l + 1, fcycle, s))) return e;
+    if ((e = o.interp(ctx, l, s))) return e;
+    if (!fcycle) return cudaSuccess;
+    if ((e = o.relax(ctx, l, s))) return e;
+    if ((e = o.restrict_(ctx, l, s))) return e;
+    if ((e = emit_cycle(ctx, o, l + 1, false, s))) return e;
+    return o.interp(ctx, l, s);
+}
+
+cudaError_t mgrit_emit_below_level0(mgrit_ctx *ctx, cudaError_t (*relax)(mgrit_ctx *, int, cudaStream_t),
+                                    cudaError_t (*restrict_)(mgrit_ctx *, int, cudaStream_t),
+                                    cudaError_t (*coarse)(mgrit_ctx *, cudaStream_t),
+                                    cudaError_t (*interp)(mgrit_ctx *, int, cudaStream_t),
+                                    cudaStream_t s)
+{
+    const CycleOps o{relax, restrict_, coarse, interp};
+    return emit_cycle(ctx, o, 1, ctx->p.cycle == MGRIT_CYCLE_F, s);
+}
+
 static cudaError_t enqueue_part_b(mgrit_ctx *ctx, cudaStream_t s)
 {
-    cudaError_t e;
-    for (int l = 1; l < ctx->L - 1; ++l) {
-        if ((e = enqueue_relax(ctx, l, s))) return e;
-        if ((e = enqueue_restrict(ctx, l, s))) return e;
-    }
-    if ((e = enqueue_coarse(ctx, s))) return e;
-    for (int l = ctx->L - 2; l >= 1; --l)
-        if ((e = enqueue_interp(ctx, l, s))) return e;
-    return cudaSuccess;
+    return mgrit_emit_below_level0(ctx, enqueue_relax, enqueue_restrict, enqueue_coarse,
+                                   enqueue_interp, s);
 }
 
 static int capture(mgrit_ctx *ctx, cudaError_t (*fn)(mgrit_ctx *, cudaStream_t),
@@ -567,12 +556,12 @@ static int capture(mgrit_ctx *ctx, cudaError_t (*fn)(mgrit_ctx *, cudaStream_t),
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
-        return fail(ctx, MGRIT_ECUDA, "graph capture: %s",
+        return mgrit_fail(ctx, MGRIT_ECUDA, "graph capture: %s",
                     cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
     e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(ctx, MGRIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return mgrit_fail(ctx, MGRIT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return MGRIT_OK;
 }
 
@@ -598,26 +587,32 @@ static int init_iterate(mgrit_ctx *ctx, const double *u0, cudaStream_t s)
     return MGRIT_OK;
 }
 
+// Phi applications below level l of one cycle (V or F), see emit_cycle
+static double steps_below(const mgrit_ctx *ctx, int l, bool fcycle)
+{
+    if (l == ctx->L - 1) return ctx->nt_l[l];       // coarsest sequential solve
+    const double m = ctx->m, nc = ctx->nC_l[l];
+    // relaxation (F: m per chunk, FCF: 2m) + the coarse step for the FAS term
+    const double relax = (ctx->p.relax == MGRIT_RELAX_FCF ? 2.0 : 1.0) * nc * m + nc;
+    const double interp = nc * (m - 1);             // interpolation F-relaxation
+    double steps = relax + steps_below(ctx, l + 1, fcycle) + interp;
+    if (fcycle) steps += relax + steps_below(ctx, l + 1, false) + interp;
+    return steps;
+}
+
 extern "C" double mgrit_cycle_cell_updates(const mgrit_ctx *ctx)
 {
     if (!ctx) return 0.0;
-    const double m = ctx->m;
-    double steps = 0.0;
-    for (int l = 0; l < ctx->L - 1; ++l) {
-        const double nc = ctx->nC_l[l];
-        const double relax = ctx->p.relax == MGRIT_RELAX_FCF ? nc * m + nc * m : nc * m;
-        steps += relax + nc;                        // + the coarse step for the FAS term
-        if (l >= 1) steps += nc * (m - 1);          // interpolation F-relaxation
-    }
-    steps += ctx->nt_l[ctx->L - 1];                 // coarsest sequential solve
-    return steps * ctx->nx;
+    const double m = ctx->m, nc = ctx->nC_l[0];
+    const double relax0 = (ctx->p.relax == MGRIT_RELAX_FCF ? 2.0 : 1.0) * nc * m + nc;
+    return (relax0 + steps_below(ctx, 1, ctx->p.cycle == MGRIT_CYCLE_F)) * ctx->nx;
 }
 
 static int prepare(mgrit_ctx *ctx, const double *u0_dev, cudaStream_t s)
 {
-    if (!u0_dev) return fail(ctx, MGRIT_EINVAL, "u0_dev is NULL");
+    if (!u0_dev) return mgrit_fail(ctx, MGRIT_EINVAL, "u0_dev is NULL");
     int st;
-    if ((st = ensure_alloc(ctx))) return st;
+    if ((st = mgrit_ensure_alloc(ctx))) return st;
     if ((st = ensure_graphs(ctx))) return st;
     if ((st = init_iterate(ctx, u0_dev, s))) return st;
     ctx->prepared = true;
@@ -691,15 +686,15 @@ extern "C" int mgrit_solve(mgrit_ctx *ctx, const double *u0_dev, double *uC_out_
         stats->cell_updates = updates;
         stats->stagnated = stagnated;
     }
-    if (status == MGRIT_EDIVERGED) fail(ctx, status, "diverged at cycle %d", k);
-    if (status == MGRIT_ENOTCONV) fail(ctx, status, "not converged after %d cycles", k);
+    if (status == MGRIT_EDIVERGED) mgrit_fail(ctx, status, "diverged at cycle %d", k);
+    if (status == MGRIT_ENOTCONV) mgrit_fail(ctx, status, "not converged after %d cycles", k);
     return status;
 }
 
 extern "C" int mgrit_run_cycles(mgrit_ctx *ctx, const double *u0_dev, int ncycles, void *stream)
 {
     if (!ctx) return MGRIT_EINVAL;
-    if (ncycles < 0) return fail(ctx, MGRIT_EINVAL, "ncycles must be >= 0");
+    if (ncycles < 0) return mgrit_fail(ctx, MGRIT_EINVAL, "ncycles must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     int st = prepare(ctx, u0_dev, s);
     if (st) return st;
@@ -713,8 +708,8 @@ extern "C" int mgrit_run_cycles(mgrit_ctx *ctx, const double *u0_dev, int ncycle
 
 extern "C" int mgrit_copy_cpoints(mgrit_ctx *ctx, double *uC_out_dev, void *stream)
 {
-    if (!ctx || !uC_out_dev) return fail(ctx, MGRIT_EINVAL, "NULL argument");
-    if (!ctx->have_state) return fail(ctx, MGRIT_EINVAL, "no solve has run on this context");
+    if (!ctx || !uC_out_dev) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
+    if (!ctx->have_state) return mgrit_fail(ctx, MGRIT_EINVAL, "no solve has run on this context");
     return copy_out(ctx, uC_out_dev, 0, ctx->nC_l[0] + 1, (cudaStream_t)stream);
 }
 
@@ -722,9 +717,9 @@ extern "C" int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *u
                                  void *stream)
 {
     if (!ctx) return MGRIT_EINVAL;
-    if (!u0_dev || !uT_dev || nsteps < 0) return fail(ctx, MGRIT_EINVAL, "bad arguments");
+    if (!u0_dev || !uT_dev || nsteps < 0) return mgrit_fail(ctx, MGRIT_EINVAL, "bad arguments");
     int st;
-    if ((st = ensure_alloc(ctx))) return st;
+    if ((st = mgrit_ensure_alloc(ctx))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (!ctx->f32) {
         SlabArgs<double> a = base_args<double>(ctx, MODE_SEQ, 0);
@@ -748,12 +743,12 @@ extern "C" int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *u
 extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void *stream)
 {
     if (!ctx) return MGRIT_EINVAL;
-    if (!uC_dev || !norm_out) return fail(ctx, MGRIT_EINVAL, "NULL argument");
-    if (!ctx->ln64.slab) return fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 slab limit", ctx->nx);
+    if (!uC_dev || !norm_out) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
+    if (!ctx->ln64.slab) return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 slab limit", ctx->nx);
     int st;
-    if ((st = ensure_alloc(ctx))) return st;
+    if ((st = mgrit_ensure_alloc(ctx))) return st;
     if (!ctx->resid_rows &&
-        (st = dalloc(ctx, (void **)&ctx->resid_rows, ctx->nC_l[0] + 1, sizeof(double))))
+        (st = mgrit_dalloc(ctx, (void **)&ctx->resid_rows, ctx->nC_l[0] + 1, sizeof(double))))
         return st;
     cudaStream_t s = (cudaStream_t)stream;
     // always the FP64 operator: the residual of the FP64 discrete system
@@ -783,29 +778,29 @@ extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm
 extern "C" int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *stream)
 {
     if (!ctx) return MGRIT_EINVAL;
-    if (!ctx->prepared) return fail(ctx, MGRIT_EINVAL, "no solve has run on this context");
-    if (reps < 0) return fail(ctx, MGRIT_EINVAL, "reps must be >= 0");
+    if (!ctx->prepared) return mgrit_fail(ctx, MGRIT_EINVAL, "no solve has run on this context");
+    if (reps < 0) return mgrit_fail(ctx, MGRIT_EINVAL, "reps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     const int L = ctx->L;
     for (int r = 0; r < reps; ++r) {
         switch (which) {
         case 0:
-            if (level < 0 || level > L - 2) return fail(ctx, MGRIT_EINVAL, "bad level");
+            if (level < 0 || level > L - 2) return mgrit_fail(ctx, MGRIT_EINVAL, "bad level");
             CK(enqueue_relax(ctx, level, s));
             break;
         case 1:
-            if (level < 0 || level > L - 2) return fail(ctx, MGRIT_EINVAL, "bad level");
+            if (level < 0 || level > L - 2) return mgrit_fail(ctx, MGRIT_EINVAL, "bad level");
             CK(enqueue_restrict(ctx, level, s));
             break;
         case 2:
             CK(enqueue_coarse(ctx, s));
             break;
         case 3:
-            if (level < 1 || level > L - 2) return fail(ctx, MGRIT_EINVAL, "bad level");
+            if (level < 1 || level > L - 2) return mgrit_fail(ctx, MGRIT_EINVAL, "bad level");
             CK(enqueue_interp(ctx, level, s));
             break;
         default:
-            return fail(ctx, MGRIT_EINVAL, "unknown kernel id %d", which);
+            return mgrit_fail(ctx, MGRIT_EINVAL, "unknown kernel id %d", which);
         }
     }
     return MGRIT_OK;
@@ -874,8 +869,10 @@ const BatchTable &btable()
     static BatchTable t = [] {
         BatchTable k;
         memset(&k, 0, sizeof k);
-        fill_batch_f32(k);
-        fill_batch_f64(k);
+        fill_batch_f32_burgers(k);
+        fill_batch_f32_advection(k);
+        fill_batch_f64_burgers(k);
+        fill_batch_f64_advection(k);
         return k;
     }();
     return t;
@@ -1218,6 +1215,7 @@ extern "C" int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst,
     *out = nullptr;
     mgrit_params p;
     if (params) p = *params; else mgrit_default_params(&p);
+    if (p.cycle != MGRIT_CYCLE_V) return bfail(nullptr, MGRIT_EINVAL, "batches run the V-cycle only");
     b = new (std::nothrow) mgrit_batch();
     if (!b) return bfail(nullptr, MGRIT_ENOMEM, "host allocation failed");
     b->n = n;
@@ -1258,7 +1256,7 @@ extern "C" int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst,
         b->cpt.push_back(ln.cpt);
         b->cpt64.push_back(c->ln64.cpt);
         b->maxL = std::max(b->maxL, d.levels);
-        if ((st = ensure_alloc(c))) {
+        if ((st = mgrit_ensure_alloc(c))) {
             bfail(b, st, "instance %d: %s", i, c->err);
             break;
         }

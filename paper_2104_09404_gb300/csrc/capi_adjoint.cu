@@ -1,0 +1,390 @@
+// Adjoint entry points of the C ABI (declared in include/mgrit.h):
+// mgrit_step_vjp, mgrit_adjoint_serial and mgrit_adjoint.
+//
+// Adjoint MGRIT data in HBM, all FP64, mirroring the forward solver's layout
+// with the time axis reversed (row k of a level = reversed point k, i.e.
+// forward point N_l - k):
+//   traj        forward fine states u^0..u^{N-1}, regenerated from the
+//               forward C-point checkpoints by one launch (chunk j from uC_j)
+//   level 0     C-points live in u[1]; newC[0], phirow[0], cstep[0]
+//   0 < l < L-1 u[l], g[l] ((N_l+1) rows), newC/phirow/cstep[l]
+//   l = L-1     u[L-1], g[L-1]
+//   scratch     one row per relaxation CTA (the stage state u1 of a VJP)
+//   cps         nt/m forward checkpoints of the serial adjoint
+// One cycle = graph A (level-0 relaxation, residual + restriction, norm) and
+// graph B (coarser levels, coarsest solve, interpolation), as forward.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "adj_table.cuh"
+#include "ctx.cuh"
+#include "restrict.cuh"
+
+using namespace mgrit;
+
+namespace mgrit {
+
+struct AdjWork {
+    const void *fn;      // k_adjoint instance for (scheme, flux, cells per thread)
+    int threads, cpt;
+    size_t smem;
+    double *traj;
+    double *u[MAXLEV], *g[MAXLEV];
+    double *newC[MAXLEV], *phirow[MAXLEV], *cstep[MAXLEV];
+    double *scratch;
+    double *cps;
+    double *partials;
+    int nparts;
+    double *d_norm;
+    cudaGraphExec_t gA, gB;
+};
+
+}  // namespace mgrit
+
+static const AdjTable &adj_table()
+{
+    static AdjTable t = [] {
+        AdjTable k;
+        memset(&k, 0, sizeof k);
+        fill_adj_all(k);
+        return k;
+    }();
+    return t;
+}
+
+void mgrit_adj_free(mgrit_ctx *ctx)
+{
+    AdjWork *w = ctx->adj;
+    if (!w) return;
+    if (w->gA) cudaGraphExecDestroy(w->gA);
+    if (w->gB) cudaGraphExecDestroy(w->gB);
+    for (int l = 0; l < MAXLEV; ++l) {
+        cudaFree(w->u[l]);
+        cudaFree(w->g[l]);
+        cudaFree(w->newC[l]);
+        cudaFree(w->phirow[l]);
+        cudaFree(w->cstep[l]);
+    }
+    cudaFree(w->traj);
+    cudaFree(w->scratch);
+    cudaFree(w->cps);
+    cudaFree(w->partials);
+    cudaFree(w->d_norm);
+    delete w;
+    ctx->adj = nullptr;
+}
+
+// smallest cells-per-thread giving at most 512 threads per CTA, if the
+// adjoint slab's shared memory fits
+static bool adj_choose(const mgrit_ctx *ctx, AdjWork *w)
+{
+    if (ctx->scheme != MGRIT_WENO5_SSPRK3 && ctx->scheme != MGRIT_FO_FE) return false;
+    const size_t smem = adj_smem_bytes<double>(ctx->nx);
+    if (smem > 227 * 1024) return false;
+    static const int cpts[NCPT_ADJ] = {1, 2, 4, 8};
+    for (int ci = 0; ci < NCPT_ADJ; ++ci) {
+        const int need = (ctx->nx + cpts[ci] - 1) / cpts[ci];
+        if (need <= 512) {
+            w->cpt = cpts[ci];
+            w->threads = ((need + 31) / 32) * 32;
+            w->smem = smem;
+            w->fn = adj_table().k[ctx->scheme][ctx->flux][ci];
+            return w->fn != nullptr;
+        }
+    }
+    return false;
+}
+
+static int adj_check(mgrit_ctx *ctx)
+{
+    if (ctx->scheme == MGRIT_LF_FE)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "the adjoint covers the WENO5 and first-order schemes");
+    if (ctx->p.numflux != MGRIT_LF_SPLIT)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "the adjoint differentiates the split numerical flux only");
+    AdjWork probe;
+    memset(&probe, 0, sizeof probe);
+    if (!adj_choose(ctx, &probe))
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the adjoint slab limit (4096)", ctx->nx);
+    return MGRIT_OK;
+}
+
+static int adj_alloc(mgrit_ctx *ctx, AdjWork *w)
+{
+    int st;
+    const int L = ctx->L;
+    const size_t es = sizeof(double);
+    if ((st = mgrit_dalloc(ctx, (void **)&w->traj, ctx->nt, es))) return st;
+    for (int l = 1; l < L; ++l) {
+        if ((st = mgrit_dalloc(ctx, (void **)&w->u[l], ctx->nt_l[l] + 1, es))) return st;
+        if ((st = mgrit_dalloc(ctx, (void **)&w->g[l], ctx->nt_l[l] + 1, es))) return st;
+    }
+    for (int l = 0; l < L - 1; ++l) {
+        if ((st = mgrit_dalloc(ctx, (void **)&w->newC[l], ctx->nC_l[l] + 1, es))) return st;
+        if ((st = mgrit_dalloc(ctx, (void **)&w->phirow[l], ctx->nC_l[l] + 1, es))) return st;
+        if ((st = mgrit_dalloc(ctx, (void **)&w->cstep[l], ctx->nC_l[l], es))) return st;
+    }
+    const int srows = ctx->nC_l[0] + 1 > 1 + ctx->m ? ctx->nC_l[0] + 1 : 1 + ctx->m;
+    if ((st = mgrit_dalloc(ctx, (void **)&w->scratch, srows, es))) return st;
+    if ((st = mgrit_dalloc(ctx, (void **)&w->cps, ctx->nC_l[0], es))) return st;
+    w->nparts = restrict_blocks(ctx->nC_l[0], ctx->nx);
+    CK(cudaMalloc((void **)&w->partials, sizeof(double) * w->nparts));
+    CK(cudaMalloc((void **)&w->d_norm, sizeof(double)));
+    CK(cudaFuncSetAttribute(w->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem));
+    return MGRIT_OK;
+}
+
+// adjoint workspaces on first use; a failed allocation leaves none behind
+static int adj_ensure(mgrit_ctx *ctx)
+{
+    int st;
+    if ((st = adj_check(ctx))) return st;
+    if ((st = mgrit_ensure_alloc(ctx))) return st;
+    if (ctx->adj) return MGRIT_OK;
+    AdjWork *w = new (std::nothrow) AdjWork;
+    if (!w) return mgrit_fail(ctx, MGRIT_ENOMEM, "host allocation failed");
+    memset(w, 0, sizeof *w);
+    ctx->adj = w;
+    adj_choose(ctx, w);
+    if ((st = adj_alloc(ctx, w))) mgrit_adj_free(ctx);
+    return st;
+}
+
+static AdjArgs adj_base(const mgrit_ctx *ctx, int mode, int l)
+{
+    const AdjWork *w = ctx->adj;
+    AdjArgs a;
+    memset(&a, 0, sizeof a);
+    a.mode = mode;
+    a.nx = ctx->nx;
+    a.m = ctx->m;
+    a.nC = ctx->nC_l[l];
+    a.fcf = ctx->p.relax == MGRIT_RELAX_FCF;
+    a.dxinv = ctx->nx / ctx->p.L;
+    a.dt = ctx->dt_l[l];
+    a.dtc = l + 1 < ctx->L ? ctx->dt_l[l + 1] : 0.0;
+    a.N = ctx->nt;
+    long long s = 1;
+    for (int k = 0; k < l; ++k) s *= ctx->m;
+    a.s = s;
+    a.sc = s * ctx->m;
+    a.traj = w->traj;
+    a.nrows_traj = ctx->nt;
+    a.scratch = w->scratch;
+    return a;
+}
+
+static cudaError_t adj_launch(const mgrit_ctx *ctx, int grid, cudaStream_t s, AdjArgs *a)
+{
+    const AdjWork *w = ctx->adj;
+    void *args[] = {a};
+    return cudaLaunchKernel(w->fn, dim3(grid), dim3(w->threads), args, w->smem, s);
+}
+
+static cudaError_t adj_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
+{
+    AdjWork *w = ctx->adj;
+    AdjArgs a = adj_base(ctx, ADJ_RELAX, l);
+    a.uC = l == 0 ? w->u[1] : w->u[l];
+    a.strideC = (long long)(l == 0 ? 1 : ctx->m) * ctx->nx;
+    a.g = l == 0 ? nullptr : w->g[l];
+    a.newC = w->newC[l];
+    a.phirow = w->phirow[l];
+    a.cstep = w->cstep[l];
+    a.nrows_uC = a.nrows_newC = a.nrows_phirow = a.nC + 1;
+    a.nrows_cstep = a.nC;
+    a.nrows_g = ctx->nt_l[l] + 1;
+    return adj_launch(ctx, a.nC + 1, s, &a);
+}
+
+static cudaError_t adj_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
+{
+    AdjWork *w = ctx->adj;
+    RestrictArgs r;
+    memset(&r, 0, sizeof r);
+    r.newC = w->newC[l];
+    r.phirow = w->phirow[l];
+    r.cstep = w->cstep[l];
+    r.g = l == 0 ? nullptr : w->g[l];
+    r.gn = w->g[l + 1];
+    r.un = w->u[l + 1];
+    r.partials = l == 0 ? w->partials : nullptr;
+    r.nrows_g = ctx->nt_l[l] + 1;
+    r.nx = ctx->nx;
+    r.m = ctx->m;
+    r.nC = ctx->nC_l[l];
+    r.guess = ctx->p.guess;
+    return launch_restrict(r, l == 0 ? w->nparts : restrict_blocks(r.nC, r.nx), s);
+}
+
+static cudaError_t adj_coarse(mgrit_ctx *ctx, cudaStream_t s)
+{
+    AdjWork *w = ctx->adj;
+    const int l = ctx->L - 1;
+    AdjArgs a = adj_base(ctx, ADJ_SEQ, l);
+    a.src = w->g[l];
+    a.g = w->g[l];
+    a.rows = w->u[l];
+    a.nsteps = ctx->nt_l[l];
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    return adj_launch(ctx, 1, s, &a);
+}
+
+static cudaError_t adj_interp(mgrit_ctx *ctx, int l, cudaStream_t s)
+{
+    AdjWork *w = ctx->adj;
+    AdjArgs a = adj_base(ctx, ADJ_INTERP, l);
+    a.uC = w->u[l + 1];
+    a.g = w->g[l];
+    a.rows = w->u[l];
+    a.nrows_uC = a.nC + 1;
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    return adj_launch(ctx, a.nC, s, &a);
+}
+
+static cudaError_t adj_part_a(mgrit_ctx *ctx, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = adj_relax(ctx, 0, s))) return e;
+    if ((e = adj_restrict(ctx, 0, s))) return e;
+    return launch_norm(ctx->adj->partials, ctx->adj->nparts, ctx->adj->d_norm, s);
+}
+
+static cudaError_t adj_part_b(mgrit_ctx *ctx, cudaStream_t s)
+{
+    return mgrit_emit_below_level0(ctx, adj_relax, adj_restrict, adj_coarse, adj_interp, s);
+}
+
+static int adj_capture(mgrit_ctx *ctx, cudaError_t (*fn)(mgrit_ctx *, cudaStream_t),
+                       cudaGraphExec_t *out)
+{
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = fn(ctx, ctx->cap);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return mgrit_fail(ctx, MGRIT_ECUDA, "adjoint graph capture: %s",
+                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return mgrit_fail(ctx, MGRIT_ECUDA, "adjoint graph instantiate: %s", cudaGetErrorString(e));
+    return MGRIT_OK;
+}
+
+extern "C" int mgrit_step_vjp(mgrit_ctx *ctx, const double *u_dev, const double *lam_dev,
+                              double *out_dev, void *stream)
+{
+    if (!ctx) return MGRIT_EINVAL;
+    if (!u_dev || !lam_dev || !out_dev) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
+    int st;
+    if ((st = adj_ensure(ctx))) return st;
+    AdjArgs a = adj_base(ctx, ADJ_VJP, 0);
+    a.src = u_dev;
+    a.uC = lam_dev;
+    a.out = out_dev;
+    CK(adj_launch(ctx, 1, (cudaStream_t)stream, &a));
+    return MGRIT_OK;
+}
+
+extern "C" int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const double *lamT_dev,
+                                    double *lam0_dev, void *stream)
+{
+    if (!ctx) return MGRIT_EINVAL;
+    if (!u0_dev || !lamT_dev || !lam0_dev) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
+    int st;
+    if ((st = adj_ensure(ctx))) return st;
+    AdjWork *w = ctx->adj;
+    AdjArgs a = adj_base(ctx, ADJ_SERIAL, 0);
+    a.src = u0_dev;
+    a.uC = lamT_dev;
+    a.out = lam0_dev;
+    a.rows = w->cps;
+    a.nrows_rows = ctx->nC_l[0];
+    CK(adj_launch(ctx, 1, (cudaStream_t)stream, &a));
+    return MGRIT_OK;
+}
+
+extern "C" int mgrit_adjoint(mgrit_ctx *ctx, const double *uC_dev, const double *lamT_dev,
+                             double *lam0_dev, double *lamC_dev, void *stream, mgrit_stats *stats)
+{
+    if (!ctx) return MGRIT_EINVAL;
+    if (!uC_dev || !lamT_dev) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
+    int st;
+    if ((st = adj_ensure(ctx))) return st;
+    AdjWork *w = ctx->adj;
+    if (!w->gA && (st = adj_capture(ctx, adj_part_a, &w->gA))) return st;
+    if (!w->gB && (st = adj_capture(ctx, adj_part_b, &w->gB))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nx = ctx->nx, nC = ctx->nC_l[0];
+    if (stats) memset(stats, 0, sizeof *stats);
+    CK(cudaEventRecord(ctx->ev0, s));
+    // forward fine states from the C-point checkpoints
+    AdjArgs t = adj_base(ctx, ADJ_TRAJ, 0);
+    t.uC = uC_dev;
+    t.rows = w->traj;
+    t.nrows_uC = nC + 1;
+    CK(adj_launch(ctx, nC, s, &t));
+    // initial iterate: every level-0 C-point = lamT; row 0 of every u_l, g_l = lamT
+    CK(launch_broadcast_row(lamT_dev, w->u[1], 0, nx, (long long)nC + 1, s));
+    for (int l = 1; l < ctx->L; ++l) {
+        CK(cudaMemcpyAsync(w->g[l], lamT_dev, sizeof(double) * nx, cudaMemcpyDeviceToDevice, s));
+        if (l > 1)
+            CK(cudaMemcpyAsync(w->u[l], lamT_dev, sizeof(double) * nx, cudaMemcpyDeviceToDevice, s));
+    }
+    const double cyc = mgrit_cycle_cell_updates(ctx);
+    const double relax0 = (double)nx * nC *
+                          ((ctx->p.relax == MGRIT_RELAX_FCF ? 2.0 : 1.0) * ctx->m + 1.0);
+    double updates = (double)nx * nC * (ctx->m - 1);   // trajectory regeneration
+    double r0 = 0.0;
+    int k = 0, status = MGRIT_OK;
+    for (;; ++k) {
+        CK(cudaGraphLaunch(w->gA, s));
+        updates += relax0;
+        CK(cudaMemcpyAsync(ctx->h_norm, w->d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double rk = *ctx->h_norm;
+        if (stats && k < 256) stats->res_hist[k] = rk;
+        if (k == 0) r0 = rk;
+        if (rk < ctx->p.tol) { status = MGRIT_OK; break; }
+        if (!std::isfinite(rk) || rk > 1e8 * r0) { status = MGRIT_EDIVERGED; break; }
+        if (k >= ctx->p.max_iter) { status = MGRIT_ENOTCONV; break; }
+        CK(cudaGraphLaunch(w->gB, s));
+        updates += cyc - relax0;
+    }
+    CK(cudaEventRecord(ctx->ev1, s));
+    // reversed point nt (= forward point 0) is the last level-0 C-point
+    if (lam0_dev)
+        CK(cudaMemcpyAsync(lam0_dev, w->newC[0] + (size_t)nC * nx, sizeof(double) * nx,
+                           cudaMemcpyDeviceToDevice, s));
+    if (lamC_dev) CK(launch_reverse_rows(w->newC[0], lamC_dev, (long long)nC + 1, nx, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        stats->iters = k;
+        stats->status = status;
+        stats->t_total_ms = ms;
+        stats->cell_updates = updates;
+    }
+    if (status == MGRIT_EDIVERGED) mgrit_fail(ctx, status, "adjoint diverged at cycle %d", k);
+    if (status == MGRIT_ENOTCONV) mgrit_fail(ctx, status, "adjoint not converged after %d cycles", k);
+    return status;
+}
+
+extern "C" int mgrit_adjoint_query(const mgrit_ctx *ctx, int what)
+{
+    if (!ctx) return -1;
+    AdjWork w;
+    memset(&w, 0, sizeof w);
+    const bool ok = ctx->p.numflux == MGRIT_LF_SPLIT && adj_choose(ctx, &w);
+    switch (what) {
+    case 0: return ok ? w.cpt : 0;
+    case 1: return ok ? w.threads : 0;
+    default: return -1;
+    }
+}

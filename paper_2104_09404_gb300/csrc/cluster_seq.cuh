@@ -7,7 +7,7 @@
 //   1. each CTA reduces max|f'| over its cells and publishes the partial in
 //      its shared memory; cluster barrier; every CTA reads the K partials
 //      through distributed shared memory (DSMEM) -> the global LF alpha;
-//   2. each CTA writes f^+/- (split form) or the stage state (state form) of
+//   2. each CTA writes f^+/- (split form) or the stage state (state form, Roe) of
 //      its cells; cluster barrier; three ghost cells on each side are read
 //      from the neighbouring CTAs' shared memory (periodic: rank 0's left
 //      neighbour is rank K-1);
@@ -154,6 +154,25 @@ struct ClusterSlab {
             }
             if (threadIdx.x == blockDim.x - 1)   // left boundary interface
                 qf[0] = rec_minus(fp, GHOST - 1) + rec_plus(fm, GHOST - 1);
+        } else if (numflux == NF_ROE) {
+            // local per interface: one cluster barrier per stage, as for advection
+            R *wa = arr(buf, 0);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < n) MGRIT_SH(wa, i + GHOST, lim()) = w[c];
+            }
+            cl.sync();
+            ghosts(buf, 1);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < n)
+                    MGRIT_SH(qf, i + 1, nmax + 2) =
+                        roe_flux<FLUX>(rec_minus(wa, i + GHOST), rec_plus(wa, i + GHOST));
+            }
+            if (threadIdx.x == blockDim.x - 1)
+                qf[0] = roe_flux<FLUX>(rec_minus(wa, GHOST - 1), rec_plus(wa, GHOST - 1));
         } else {
             R *wa = arr(buf, 0);
 #pragma unroll

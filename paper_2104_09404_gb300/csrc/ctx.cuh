@@ -1,0 +1,86 @@
+// Private host-side definitions shared by the C-ABI translation units
+// (capi.cu: forward solver and batches; capi_adjoint.cu: the adjoint).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "../../include/mgrit.h"
+
+namespace mgrit {
+
+constexpr int MAXLEV = 32;
+
+struct Launch {
+    const void *slab;   // k_slab instance for (precision, scheme, flux, cells per thread); null: unsupported
+    int threads;
+    int cpt;
+    size_t smem;
+};
+
+// sequential stepping on a thread-block cluster (coarsest solve, serial stepper)
+struct ClusterLaunch {
+    const void *fn;     // k_seq_cluster instance; null: single-CTA k_slab
+    int K;              // CTAs in the cluster
+    int cpt;            // cells per thread (1 or 2)
+    int threads;
+    size_t smem;
+};
+
+struct AdjWork;   // adjoint workspaces (capi_adjoint.cu), allocated on first use
+
+}  // namespace mgrit
+
+struct mgrit_ctx {
+    int nx, nt, m, L, scheme, flux;
+    mgrit_params p;
+    int nt_l[mgrit::MAXLEV], nC_l[mgrit::MAXLEV];
+    double dt_l[mgrit::MAXLEV];
+    mgrit::Launch ln64, ln32;
+    mgrit::ClusterLaunch lc64, lc32;
+    int f32;             // precision the workspaces were allocated for (1: FP32 sweeps)
+    bool alloc;
+    bool prepared;       // workspaces, graphs and an initial iterate exist
+    bool have_state;     // a level-0 relaxation has produced newC[0]
+    int device;
+    void *u[mgrit::MAXLEV];
+    double *g[mgrit::MAXLEV];
+    void *newC[mgrit::MAXLEV], *phirow[mgrit::MAXLEV], *cstep[mgrit::MAXLEV];
+    float *u32c;         // FP32 mirror of the coarsest rows (FP32-sweep mode)
+    float *ser32;        // one FP32 row for the FP32 serial stepper
+    double *resid_rows;  // mgrit_residual scratch ((nt/m+1) rows, FP64)
+    double *partials;
+    int nparts;
+    double *d_norm;
+    double *h_norm;
+    cudaStream_t cap;
+    cudaGraphExec_t gA, gB;
+    cudaEvent_t ev0, ev1;
+    mgrit::AdjWork *adj;
+    char err[256];
+};
+
+// record a one-line error (ctx may be null: the creation error) and return code
+int mgrit_fail(mgrit_ctx *c, int code, const char *fmt, ...);
+// device rows x nx elements of `elem` bytes
+int mgrit_dalloc(mgrit_ctx *ctx, void **ptr, size_t rows, size_t elem);
+// level workspaces, events and the capture stream of the forward solver
+int mgrit_ensure_alloc(mgrit_ctx *ctx);
+// release the adjoint workspaces (no-op if none)
+void mgrit_adj_free(mgrit_ctx *ctx);
+// enqueue the part of one cycle below level 0 (V- or F-cycle by ctx->p.cycle)
+// from the given level operations
+cudaError_t mgrit_emit_below_level0(mgrit_ctx *ctx, cudaError_t (*relax)(mgrit_ctx *, int, cudaStream_t),
+                                    cudaError_t (*restrict_)(mgrit_ctx *, int, cudaStream_t),
+                                    cudaError_t (*coarse)(mgrit_ctx *, cudaStream_t),
+                                    cudaError_t (*interp)(mgrit_ctx *, int, cudaStream_t),
+                                    cudaStream_t s);
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return mgrit_fail(ctx, e_ == cudaErrorMemoryAllocation ? MGRIT_ENOMEM : MGRIT_ECUDA, \
+                              "%s: %s", #call, cudaGetErrorString(e_));                \
+    } while (0)

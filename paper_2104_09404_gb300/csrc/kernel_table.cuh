@@ -9,15 +9,19 @@ constexpr int CPT_VALUES[NCPT] = {1, 2, 4, 8, 16, 32};
 constexpr int NCPT64 = 5;          // FP64 slabs stop at 16 cells per thread (nx <= 8192)
 constexpr int MAX_THREADS = 512;   // matches __launch_bounds__ of k_slab
 
+constexpr int NSCHEME = 3;         // WENO5 + SSPRK3, first order + FE, classical LF + FE
+
+// scheme 2 (classical Lax-Friedrichs + forward Euler) exists in FP64 slabs
+// only; the cluster kernels cover schemes 0 and 1
 struct KernelTable {
-    const void *slab64[2][2][NCPT];
-    const void *slab32[2][2][NCPT];
+    const void *slab64[NSCHEME][2][NCPT];
+    const void *slab32[NSCHEME][2][NCPT];
     const void *seqc64[2][2][2];   // k_seq_cluster, cells per thread 1 or 2
     const void *seqc32[2][2][2];
 };
 
 template <typename R, int S, int F>
-void fill_sf(const void *(&t)[2][2][NCPT])
+void fill_sf(const void *(&t)[NSCHEME][2][NCPT])
 {
     t[S][F][0] = (const void *)&k_slab<R, S, F, 1>;
     t[S][F][1] = (const void *)&k_slab<R, S, F, 2>;
@@ -27,7 +31,7 @@ void fill_sf(const void *(&t)[2][2][NCPT])
 }
 
 template <int S, int F>
-void fill_sf32(const void *(&t)[2][2][NCPT])
+void fill_sf32(const void *(&t)[NSCHEME][2][NCPT])
 {
     fill_sf<float, S, F>(t);
     t[S][F][5] = (const void *)&k_slab<float, S, F, 32>;
@@ -40,21 +44,28 @@ void fill_cluster(const void *(&t)[2][2][2])
     t[S][F][1] = (const void *)&k_seq_cluster<R, S, F, 2>;
 }
 
-// one translation unit per (precision, scheme, flux), compiled in parallel
+// one translation unit per (precision, scheme, flux) and kind (slab or
+// cluster kernels), compiled in parallel
 void fill_f64_weno_burgers(KernelTable &t);
 void fill_f64_weno_advection(KernelTable &t);
+void fill_f64_weno_cluster(KernelTable &t);
 void fill_f64_fo(KernelTable &t);
+void fill_f64_lf(KernelTable &t);
 void fill_f32_weno_burgers(KernelTable &t);
 void fill_f32_weno_advection(KernelTable &t);
+void fill_f32_weno_cluster(KernelTable &t);
 void fill_f32_fo(KernelTable &t);
 
 inline void fill_all(KernelTable &t)
 {
     fill_f64_weno_burgers(t);
     fill_f64_weno_advection(t);
+    fill_f64_weno_cluster(t);
     fill_f64_fo(t);
+    fill_f64_lf(t);
     fill_f32_weno_burgers(t);
     fill_f32_weno_advection(t);
+    fill_f32_weno_cluster(t);
     fill_f32_fo(t);
 }
 

@@ -47,6 +47,11 @@ struct SlabArgs {
     R *out;
     // row extents of the arrays above (checked by MGRIT_DEBUG builds)
     long long nrows_uC, nrows_newC, nrows_phirow, nrows_cstep, nrows_g, nrows_rows;
+    // SCH_LF_FE only: matched integrator of this level (psiM) and of the next
+    // coarser one (psiMc) for psiM/psiMc fine steps of size psiDt; 0 = the
+    // fine scheme with the level's step (rediscretisation)
+    int psiM, psiMc, psiOrder;
+    R psiDt;
 };
 
 template <typename R, int SCHEME, int FLUX, int CPT>
@@ -73,7 +78,9 @@ __device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const
     if (a.cstep) {
         // coarse step of the FAS term; u is then re-read from the row this
         // thread just stored (its own cells), which saves CPT registers
+        if (SCHEME == SCH_LF_FE) S.psiM = a.psiMc;
         S.step(u, a.dtc);
+        if (SCHEME == SCH_LF_FE) S.psiM = a.psiM;
         S.store(u, rowp(a.cstep, j, nx, a.nrows_cstep));
         S.load(u, rowp(a.newC, j, nx, a.nrows_newC));
     }
@@ -125,6 +132,11 @@ __global__ void __launch_bounds__(512) k_slab(SlabArgs<R> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
+    if (SCHEME == SCH_LF_FE) {
+        S.psiM = a.psiM;
+        S.psiOrder = a.psiOrder;
+        S.psiDt = a.psiDt;
+    }
     if (a.mode == MODE_RELAX)
         relax_chunk(S, a, (int)blockIdx.x);
     else if (a.mode == MODE_INTERP)

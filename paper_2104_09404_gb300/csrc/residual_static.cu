@@ -73,7 +73,8 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     if (!uC_dev || !norm_dev) return MGRIT_EINVAL;
     if (scheme != MGRIT_WENO5_SSPRK3 && scheme != MGRIT_FO_FE) return MGRIT_EINVAL;
     if (flux != MGRIT_BURGERS && flux != MGRIT_ADVECTION) return MGRIT_EINVAL;
-    if (numflux != MGRIT_LF_SPLIT && numflux != MGRIT_LF_STATE) return MGRIT_EINVAL;
+    if (numflux != MGRIT_LF_SPLIT && numflux != MGRIT_LF_STATE && numflux != MGRIT_ROE)
+        return MGRIT_EINVAL;
     if (m < 2 || nt < m || nt % m) return MGRIT_EINVAL;
     if (nx < (scheme == MGRIT_WENO5_SSPRK3 ? 5 : 3)) return MGRIT_EINVAL;
     if (!(T > 0) || !(L > 0) || !std::isfinite(T) || !std::isfinite(L)) return MGRIT_EINVAL;

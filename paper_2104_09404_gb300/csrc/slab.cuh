@@ -20,9 +20,9 @@
 
 namespace mgrit {
 
-enum { SCH_WENO5_SSPRK3 = 0, SCH_FO_FE = 1 };
+enum { SCH_WENO5_SSPRK3 = 0, SCH_FO_FE = 1, SCH_LF_FE = 2 };
 enum { FLX_BURGERS = 0, FLX_ADVECTION = 1 };
-enum { NF_SPLIT = 0, NF_STATE = 1 };
+enum { NF_SPLIT = 0, NF_STATE = 1, NF_ROE = 2 };
 
 constexpr int GHOST = 3;
 constexpr int NWARP_MAX = 32;
@@ -86,6 +86,25 @@ __device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
     return (P0 * t0 + P1 * t1 + P2 * t2) / (R(6) * (t0 + t1 + t2));
 }
 
+// Roe flux of a scalar law from the reconstructed states a = u^-, b = u^+
+// (Sec. 2.1.2, Eq. roeflux): Roe speed lam = (u^+ + u^-)/2 for Burgers, 1 for
+// advection; eigenvalues at the states lam^-/+ = f'(u^-/+); Harten-Hyman fix
+//   delta = max(0, lam - lam^-, lam^+ - lam),
+//   q = (lam^2/delta + delta)/2 if |lam| < delta, else |lam|;
+//   F = (f(u^-) + f(u^+))/2 - q (u^+ - u^-)/2.
+template <int FLUX, typename R>
+__device__ __forceinline__ R roe_flux(R a, R b)
+{
+    const R lam = FLUX == FLX_BURGERS ? R(0.5) * (b + a) : R(1);
+    const R lm = FLUX == FLX_BURGERS ? a : R(1);
+    const R lp = FLUX == FLX_BURGERS ? b : R(1);
+    R delta = R(0);
+    if (lam - lm > delta) delta = lam - lm;
+    if (lp - lam > delta) delta = lp - lam;
+    const R q = fabs(lam) < delta ? R(0.5) * (lam * lam / delta + delta) : fabs(lam);
+    return R(0.5) * (phys_flux<FLUX>(a) + phys_flux<FLUX>(b)) - R(0.5) * q * (b - a);
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_max(R v)
 {
@@ -116,9 +135,15 @@ struct Slab {
     int nx;
     int numflux;
     R dxinv;
+    // SCH_LF_FE only: the integrator of the current level.  psiM = 0: the fine
+    // scheme Eq. (fineLF) with the step passed to step(); psiM = M >= 1: the
+    // matched integrator for M fine steps of size psiDt, zeroth order
+    // (psiOrder 0, Eq. coarseLFord0) or first order (1, Eq. coarseLFord1)
+    int psiM, psiOrder;
+    R psiDt;
 
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
-        : nx(nx_), numflux(numflux_), dxinv(dxinv_)
+        : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))
     {
         qa = reinterpret_cast<R *>(smem);
         qb = qa + (nx + 2 * GHOST);
@@ -191,6 +216,20 @@ struct Slab {
                 const int i = cell(c);
                 if (i < nx) put_flux(i, rec_minus(qa, i + GHOST) + rec_plus(qb, i + GHOST));
             }
+        } else if (numflux == NF_ROE) {
+            // local per interface: no global speed, no reduction
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) put(qa, i, w[c]);
+            }
+            __syncthreads();
+#pragma unroll(RECON_UNROLL)
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx)
+                    put_flux(i, roe_flux<FLUX>(rec_minus(qa, i + GHOST), rec_plus(qa, i + GHOST)));
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
@@ -235,9 +274,66 @@ struct Slab {
         return -(MGRIT_SH(qf, i + 1, nx + 1) - MGRIT_SH(qf, i, nx + 1)) * dxinv;
     }
 
-    // u <- Phi(u) with step dt: SSPRK3 (Eq. SSPRK3) or forward Euler (Eq. SSPRK1)
+    // Eq. (fineLF): u <- E u - dt D f(u), (E v)_i = (v_{i+1} + v_{i-1})/2,
+    // (D v)_i = (v_{i+1} - v_{i-1})/(2 dx); or, with psiM = M >= 1, the
+    // matched integrators of Sec. 3.3 for M fine steps of size psiDt:
+    //   zeroth order  E^M u - M psiDt D f(u)
+    //   first order   E^M u - psiDt sum_{i=1..M} E^{i-1} D f(E^{M-i} u),
+    // the sum formed by Horner's rule: acc_M = D f(u), then for k = 1..M-1
+    // acc <- D f(E^k u) + E acc, so acc ends as the sum.
+    __device__ __forceinline__ void lf_step(R (&u)[CPT], R dt)
+    {
+        const R hd = R(0.5) * dxinv;
+        R v[CPT], acc[CPT];
+        const bool first = psiM >= 1 && psiOrder == 1;
+        const int M = psiM >= 1 ? psiM : 1;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            v[c] = u[c];
+            acc[c] = R(0);
+        }
+        for (int k = 0; k < M; ++k) {
+            __syncthreads();   // earlier readers of qa/qb/qf are done
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) {
+                    put(qa, i, v[c]);
+                    if (k == 0 || first) put(qb, i, phys_flux<FLUX>(v[c]));
+                    if (first && k > 0) put(qf, i, acc[c]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx) {
+                    const int s = i + GHOST;
+                    const R Df = (MGRIT_SH(qb, s + 1, lim()) - MGRIT_SH(qb, s - 1, lim())) * hd;
+                    if (first)
+                        acc[c] = k == 0 ? Df
+                                        : Df + R(0.5) * (MGRIT_SH(qf, s + 1, lim()) + MGRIT_SH(qf, s - 1, lim()));
+                    else if (k == 0)
+                        acc[c] = Df;   // D f(u)
+                    v[c] = R(0.5) * (MGRIT_SH(qa, s + 1, lim()) + MGRIT_SH(qa, s - 1, lim()));
+                }
+            }
+        }
+        // v = E^M u; acc = D f(u) (fine, zeroth order) or the first-order sum
+        const R h = psiM >= 1 ? (first ? psiDt : R(M) * psiDt) : dt;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (cell(c) < nx) u[c] = v[c] - h * acc[c];
+    }
+
+    // u <- Phi(u) with step dt: SSPRK3 (Eq. SSPRK3), forward Euler (Eq. SSPRK1)
+    // or Eq. (fineLF) and its matched integrators (lf_step)
     __device__ __forceinline__ void step(R (&u)[CPT], R dt)
     {
+        if (SCHEME == SCH_LF_FE) {
+            lf_step(u, dt);
+            return;
+        }
         if (SCHEME == SCH_FO_FE) {
             fluxes(u);
 #pragma unroll

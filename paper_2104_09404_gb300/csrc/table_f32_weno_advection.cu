@@ -4,6 +4,5 @@ namespace mgrit {
 void fill_f32_weno_advection(KernelTable &t)
 {
     fill_sf32<SCH_WENO5_SSPRK3, FLX_ADVECTION>(t.slab32);
-    fill_cluster<float, SCH_WENO5_SSPRK3, FLX_ADVECTION>(t.seqc32);
 }
 }  // namespace mgrit

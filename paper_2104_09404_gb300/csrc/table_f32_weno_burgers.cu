@@ -4,6 +4,5 @@ namespace mgrit {
 void fill_f32_weno_burgers(KernelTable &t)
 {
     fill_sf32<SCH_WENO5_SSPRK3, FLX_BURGERS>(t.slab32);
-    fill_cluster<float, SCH_WENO5_SSPRK3, FLX_BURGERS>(t.seqc32);
 }
 }  // namespace mgrit

@@ -4,6 +4,5 @@ namespace mgrit {
 void fill_f64_weno_advection(KernelTable &t)
 {
     fill_sf<double, SCH_WENO5_SSPRK3, FLX_ADVECTION>(t.slab64);
-    fill_cluster<double, SCH_WENO5_SSPRK3, FLX_ADVECTION>(t.seqc64);
 }
 }  // namespace mgrit

@@ -4,6 +4,5 @@ namespace mgrit {
 void fill_f64_weno_burgers(KernelTable &t)
 {
     fill_sf<double, SCH_WENO5_SSPRK3, FLX_BURGERS>(t.slab64);
-    fill_cluster<double, SCH_WENO5_SSPRK3, FLX_BURGERS>(t.seqc64);
 }
 }  // namespace mgrit

@@ -15,11 +15,13 @@ LIB_PATH = os.path.join(PKG, "libmgrit_debug.so" if os.environ.get("MGRIT_DEBUG"
                         else "libmgrit.so")
 
 OK, EINVAL, ECUDA, ENOMEM, EDIVERGED, ENOTCONV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-WENO5_SSPRK3, FO_FE = 0, 1
+WENO5_SSPRK3, FO_FE, LF_FE = 0, 1, 2
 BURGERS, ADVECTION = 0, 1
-LF_SPLIT, LF_STATE = 0, 1
+LF_SPLIT, LF_STATE, ROE = 0, 1, 2
 RELAX_F, RELAX_FCF = 0, 1
 GUESS_EQ17, GUESS_INJECT = 0, 1
+CYCLE_V, CYCLE_F = 0, 1
+COARSE_REDISC, COARSE_PSI0, COARSE_PSI1 = 0, 1, 2
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM",
                 EDIVERGED: "EDIVERGED", ENOTCONV: "ENOTCONV", ETIMEOUT: "ETIMEOUT"}
 
@@ -27,7 +29,8 @@ STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM",
 class mgrit_params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_double), ("L", ctypes.c_double), ("relax", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("guess", ctypes.c_int), ("numflux", ctypes.c_int),
-                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("coarse", ctypes.c_int)]
 
 
 class mgrit_stats(ctypes.Structure):
@@ -60,6 +63,10 @@ _SIGS = {
     "mgrit_residual_static": (_I, [_I, _I, _I, _I, _I, _I, _D, _D, _P, _P, _P]),
     "mgrit_cycle_cell_updates": (_D, [_P]),
     "mgrit_query": (_I, [_P, _I]),
+    "mgrit_step_vjp": (_I, [_P, _P, _P, _P, _P]),
+    "mgrit_adjoint_serial": (_I, [_P, _P, _P, _P, _P]),
+    "mgrit_adjoint": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(mgrit_stats)]),
+    "mgrit_adjoint_query": (_I, [_P, _I]),
     "mgrit_last_error": (ctypes.c_char_p, [_P]),
     "mgrit_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(mgrit_instance), _I,
                                 ctypes.POINTER(mgrit_params)]),
@@ -189,6 +196,43 @@ class Solver:
         sequential stepper (0 before the first allocating call)."""
         return load().mgrit_query(self._h, what)
 
+    # ---- discrete adjoint ----------------------------------------------
+
+    def step_vjp(self, u, lam, out=None, stream=None):
+        """Phi'(u)^T lam for one fine step."""
+        import torch
+        if out is None:
+            out = torch.empty_like(lam)
+        self._check(load().mgrit_step_vjp(self._h, _ptr(u), _ptr(lam), _ptr(out),
+                                          _stream_handle(stream)))
+        return out
+
+    def adjoint_serial(self, u0, lamT, out=None, stream=None):
+        """dJ/du0 from dJ/du(T) = lamT through nt serial steps (C-point checkpoints)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(lamT)
+        self._check(load().mgrit_adjoint_serial(self._h, _ptr(u0), _ptr(lamT), _ptr(out),
+                                                _stream_handle(stream)))
+        return out
+
+    def adjoint(self, uC, lamT, want_lamC=False, stream=None):
+        """Adjoint MGRIT from the forward C-point checkpoints uC ((nt/m+1, nx)).
+        Returns (status, lam0, lamC or None, stats)."""
+        import torch
+        lam0 = torch.empty_like(lamT)
+        lamC = torch.empty((self.nt // self.m + 1, self.nx), dtype=torch.float64,
+                           device=lamT.device) if want_lamC else None
+        stats = mgrit_stats()
+        st = load().mgrit_adjoint(self._h, _ptr(uC), _ptr(lamT), _ptr(lam0), _ptr(lamC),
+                                  _stream_handle(stream), ctypes.byref(stats))
+        self._check(st, (OK, EDIVERGED, ENOTCONV))
+        return st, lam0, lamC, stats
+
+    def adjoint_query(self, what):
+        """0: cells per thread, 1: threads per CTA of the adjoint kernels (0: unsupported)."""
+        return load().mgrit_adjoint_query(self._h, what)
+
     def close(self):
         if getattr(self, "_h", None):
             load().mgrit_destroy(self._h)
@@ -277,3 +321,43 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class MGRITSolve(torch.autograd.Function):
+        """u(T) = MGRIT solve from u0 (to the solver's tolerance); its backward
+        pass is dJ/du0 = adjoint MGRIT from the forward C-point checkpoints,
+        given dJ/du(T)."""
+
+        @staticmethod
+        def forward(ctx, u0, solver):
+            st, uT, uC, _ = solver.solve(u0.detach().contiguous())
+            if st != OK:
+                raise MGRITError(st, "forward MGRIT did not converge")
+            ctx.solver = solver
+            ctx.save_for_backward(uC)
+            return uT
+
+        @staticmethod
+        def backward(ctx, gT):
+            (uC,) = ctx.saved_tensors
+            st, lam0, _, _ = ctx.solver.adjoint(uC, gT.detach().to(torch.float64).contiguous())
+            if st != OK:
+                raise MGRITError(st, "adjoint MGRIT did not converge")
+            return lam0, None
+
+    return MGRITSolve
+
+
+_MGRITSolve = None
+
+
+def mgrit_solve(u0, solver):
+    """Differentiable u(T) = Phi^nt(u0) through an MGRIT Solver (FP64 CUDA
+    tensors, split numerical flux): autograd's backward runs adjoint MGRIT."""
+    global _MGRITSolve
+    if _MGRITSolve is None:
+        _MGRITSolve = _autograd_function()
+    return _MGRITSolve.apply(u0, solver)

@@ -7,6 +7,13 @@ small = nx 4096, nt 2048, m 4, 4 levels, T 0.125 (same kernel shape, 513
 CTAs).  The context is prepared with zero cycles (workspaces allocated,
 level-0 C-points = u0), then the chosen kernel is launched `reps` times; it
 is the first launch of that kernel in the process.
+
+    python -m paper_2104_09404_gb300.profile --adjoint
+
+runs the adjoint gradient workload instead (nx 2048, nt 8192, m 4, 3 levels,
+T 0.12, u0 Fourier seed 1, target seed 1001): a forward solve, then one
+adjoint cycle (k_adjoint launches: the forward-trajectory regeneration, then
+the level-0 adjoint relaxation).
 """
 import argparse
 import sys
@@ -25,9 +32,21 @@ def main(argv=None):
     p.add_argument("--kernel", default="relax", choices=sorted(KERNELS))
     p.add_argument("--level", type=int, default=0)
     p.add_argument("--reps", type=int, default=1)
+    p.add_argument("--adjoint", action="store_true")
     a = p.parse_args(argv)
     import torch
     from . import inputs, mgrit
+    if a.adjoint:
+        nx, nt = 2048, 8192
+        s = mgrit.Solver(nx, nt, 4, 3, T=0.12)
+        u0 = torch.as_tensor(inputs.fourier_ic(nx, seed=1), device="cuda")
+        target = s.serial_step(torch.as_tensor(inputs.fourier_ic(nx, seed=1001), device="cuda"), nt)
+        st, uT, uC, _ = s.solve(u0)
+        s.set_params(max_iter=0)
+        s.adjoint(uC, (uT - target).contiguous())
+        torch.cuda.synchronize()
+        print("adjoint workload: trajectory + one adjoint cycle")
+        return 0
     c = CASES[a.case]
     s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"])
     u0 = torch.as_tensor(inputs.fourier_ic(c["nx"], seed=0), device="cuda")

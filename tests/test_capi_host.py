@@ -49,7 +49,7 @@ def test_default_params(lib):
     p = M.mgrit_params()
     lib.mgrit_default_params(ctypes.byref(p))
     assert (p.T, p.L, p.relax, p.cycle, p.guess, p.numflux) == (1.0, 1.0, 1, 0, 0, 0)
-    assert p.tol == 1e-10 and p.max_iter == 64 and p.precision == 64
+    assert p.tol == 1e-10 and p.max_iter == 64 and p.precision == 64 and p.coarse == 0
 
 
 @pytest.mark.parametrize("args,frag", [
@@ -80,7 +80,8 @@ def test_create_set_params_destroy_without_gpu(lib):
     lib.mgrit_default_params(ctypes.byref(p))
     p.T = 0.5
     assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK
-    for field, bad in (("relax", 3), ("cycle", 1), ("guess", 2), ("numflux", 5),
+    for field, bad in (("relax", 3), ("cycle", 2), ("guess", 2), ("numflux", 5), ("coarse", 3),
+                       ("coarse", 1),
                        ("tol", -1.0), ("max_iter", 1000), ("precision", 16), ("T", 0.0)):
         q = M.mgrit_params.from_buffer_copy(p)
         setattr(q, field, bad)
@@ -89,6 +90,11 @@ def test_create_set_params_destroy_without_gpu(lib):
     assert lib.mgrit_query(h, 2) == 0 and lib.mgrit_query(h, 9) == -1    # nothing allocated yet
     # 3 levels, m = 4: (2*4 + 1) * 16 + (2*4 + 1 + 3) * 4 + 4 steps per cycle at FCF
     assert lib.mgrit_cycle_cell_updates(h) == 100 * ((2 * 4 + 1) * 16 + (2 * 4 + 1 + 3) * 4 + 4)
+    # F-cycle: level 1 is visited twice (relaxation, coarsest solve, interpolation each time)
+    q = M.mgrit_params.from_buffer_copy(p)
+    q.cycle = M.CYCLE_F
+    assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.OK
+    assert lib.mgrit_cycle_cell_updates(h) == 100 * ((2 * 4 + 1) * 16 + 2 * ((2 * 4 + 1 + 3) * 4 + 4))
     lib.mgrit_destroy(h)
     lib.mgrit_destroy(None)
 
@@ -103,3 +109,46 @@ def test_null_arguments_are_rejected(lib):
     assert lib.mgrit_solve(h, None, None, None, None, None) == M.EINVAL
     assert lib.mgrit_copy_cpoints(h, None, None) == M.EINVAL
     lib.mgrit_destroy(h)
+
+
+def test_adjoint_shape_and_host_checks_without_gpu(lib):
+    from paper_2104_09404_gb300 import mgrit as M
+    h = ctypes.c_void_p()
+    assert lib.mgrit_create(ctypes.byref(h), 2048, 64, 4, 2, 0, 0) == M.OK
+    assert lib.mgrit_adjoint_query(h, 0) == 4 and lib.mgrit_adjoint_query(h, 1) == 512
+    assert lib.mgrit_adjoint_query(h, 7) == -1
+    lib.mgrit_destroy(h)
+    # nx above the adjoint slab limit: EINVAL before any device work
+    assert lib.mgrit_create(ctypes.byref(h), 8192, 64, 4, 2, 0, 0) == M.OK
+    assert lib.mgrit_adjoint_query(h, 0) == 0
+    one = ctypes.c_void_p(16)   # never dereferenced: the size check comes first
+    st = lib.mgrit_adjoint(h, one, one, None, None, None, None)
+    assert st == M.EINVAL and "adjoint slab limit" in lib.mgrit_last_error(h).decode()
+    lib.mgrit_destroy(h)
+    # the state-reconstruction flux has no adjoint
+    assert lib.mgrit_create(ctypes.byref(h), 256, 64, 4, 2, 0, 0) == M.OK
+    p = M.mgrit_params()
+    lib.mgrit_default_params(ctypes.byref(p))
+    p.numflux = 1
+    assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK
+    assert lib.mgrit_adjoint_query(h, 0) == 0
+    st = lib.mgrit_step_vjp(h, one, one, one, None)
+    assert st == M.EINVAL and "split" in lib.mgrit_last_error(h).decode()
+    lib.mgrit_destroy(h)
+
+
+def test_lf_scheme_host_checks_without_gpu(lib):
+    from paper_2104_09404_gb300 import mgrit as M
+    h = ctypes.c_void_p()
+    assert lib.mgrit_create(ctypes.byref(h), 128, 1024, 2, 5, M.LF_FE, M.BURGERS) == M.OK
+    p = M.mgrit_params()
+    lib.mgrit_default_params(ctypes.byref(p))
+    for coarse in (M.COARSE_REDISC, M.COARSE_PSI0, M.COARSE_PSI1):
+        p.coarse = coarse
+        assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK
+    p.precision = 32
+    assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.EINVAL
+    assert "FP64 only" in lib.mgrit_last_error(h).decode()
+    assert lib.mgrit_adjoint_query(h, 0) == 0
+    lib.mgrit_destroy(h)
+    assert lib.mgrit_create(ctypes.byref(h), 2, 64, 2, 2, M.LF_FE, M.BURGERS) == M.EINVAL

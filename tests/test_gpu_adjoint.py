@@ -1,0 +1,246 @@
+"""Discrete adjoint on the GPU (through the C ABI) against the FP64 oracle.
+
+Bar: one transposed step and the serial adjoint within 1e-11 relative
+max-norm of the oracle; adjoint MGRIT with the oracle's iteration count,
+residual history to rounding and 1e-11 relative max-norm on lam^0 and every
+C-point; at the full adjoint workload (nx = 2048, nt = 8192) the gradient
+against central finite differences of the objective (h = 1e-6, 32 random
+directions, relative 1e-6 plus the quotient's measured rounding noise, and
+1e-6 in the median; h = 1e-6 before the shock, 1e-7 after it, where the
+global max in alpha makes J piecewise differentiable on the 1e-6 scale) and
+against the GPU serial adjoint.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2104_09404_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_09404_gb300 import build as B, mgrit
+    B.build()
+    mgrit.load()
+    return mgrit
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def relerr(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def solver(M, nx, nt, m, L, T, scheme=O.SCHEME_WENO5_SSPRK3, flux=O.FLUX_BURGERS, **kw):
+    return M.Solver(nx, nt, m, L, scheme=scheme, flux=flux, T=T, **kw)
+
+
+# ------------------------------------------------------------ one step -----
+
+VJP_CASES = [
+    # nx, scheme, flux (ragged sizes cover idle threads; 4096 is 8 cells per thread)
+    (5, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (64, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (777, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION),
+    (1000, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (2048, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (3001, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (4096, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (3, O.SCHEME_FO_FE, O.FLUX_BURGERS),
+    (300, O.SCHEME_FO_FE, O.FLUX_BURGERS),
+    (257, O.SCHEME_FO_FE, O.FLUX_ADVECTION),
+]
+
+
+@pytest.mark.parametrize("nx,scheme,flux", VJP_CASES)
+def test_step_vjp_parity(M, nx, scheme, flux):
+    u = inputs.fourier_ic(nx, seed=nx)
+    lam = np.random.default_rng(nx).standard_normal(nx)
+    dt = 0.4 / nx / max(np.abs(u).max(), 1.0)
+    S = solver(M, nx, 16, 4, 2, 16 * dt, scheme, flux)
+    got = S.step_vjp(dev(u), dev(lam)).cpu().numpy()
+    ref = O.step_vjp(u, lam, dt, scheme=scheme, flux=flux)
+    assert relerr(got, ref) <= RTOL
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_step_vjp_alpha_tie_takes_the_first_maximiser(M, sign):
+    # |u| attains its maximum in two cells: alpha is differentiated at the
+    # lower index on both sides (and with the sign of u there)
+    nx = 600
+    u = 0.3 * inputs.fourier_ic(nx, seed=4)
+    u[77] = sign * 1.25
+    u[421] = -sign * 1.25
+    lam = np.random.default_rng(1).standard_normal(nx)
+    dt = 0.3 / nx
+    S = solver(M, nx, 16, 4, 2, 16 * dt)
+    got = S.step_vjp(dev(u), dev(lam)).cpu().numpy()
+    ref = O.step_vjp(u, lam, dt)
+    assert relerr(got, ref) <= RTOL
+
+
+def test_step_vjp_in_place(M):
+    nx = 512
+    u = inputs.fourier_ic(nx, seed=2)
+    lam = np.random.default_rng(2).standard_normal(nx)
+    dt = 0.2 / nx
+    S = solver(M, nx, 16, 4, 2, 16 * dt)
+    t = dev(lam)
+    S.step_vjp(dev(u), t, out=t)
+    assert relerr(t.cpu().numpy(), O.step_vjp(u, lam, dt)) <= RTOL
+
+
+# ------------------------------------------------------------ serial -------
+
+SERIAL_CASES = [
+    # nx, nt, m, T, scheme, flux
+    (128, 64, 4, 0.05, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (1000, 32, 8, 0.01, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (333, 48, 4, 0.05, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION),
+    (200, 100, 4, 0.1, O.SCHEME_FO_FE, O.FLUX_BURGERS),
+]
+
+
+@pytest.mark.parametrize("nx,nt,m,T,scheme,flux", SERIAL_CASES)
+def test_adjoint_serial_parity(M, nx, nt, m, T, scheme, flux):
+    u0 = inputs.fourier_ic(nx, seed=11)
+    lamT = np.random.default_rng(12).standard_normal(nx)
+    S = solver(M, nx, nt, m, 2, T, scheme, flux)
+    got = S.adjoint_serial(dev(u0), dev(lamT)).cpu().numpy()
+    ref = O.adjoint_serial(u0, lamT, T / nt, nt, scheme=scheme, flux=flux)
+    assert relerr(got, ref) <= RTOL
+
+
+# ------------------------------------------------------------ MGRIT --------
+
+MGRIT_CASES = [
+    # name, nx, nt, m, L, T, params
+    ("weno-2lev-fcf", 64, 256, 4, 2, 0.1, dict()),
+    ("weno-3lev-f-inject", 128, 256, 4, 3, 0.04, dict(relax=0, guess=1)),
+    ("weno-ragged-m8", 1000, 128, 8, 2, 0.005, dict()),
+    ("weno-4lev", 256, 1024, 4, 4, 0.02, dict()),
+    ("advection", 96, 128, 4, 3, 0.1, dict()),
+    ("fo-burgers", 100, 512, 4, 3, 0.2, dict()),
+    ("weno-2048", 2048, 256, 4, 3, 0.004, dict()),
+]
+
+
+@pytest.mark.parametrize("name,nx,nt,m,L,T,kw", MGRIT_CASES, ids=[c[0] for c in MGRIT_CASES])
+def test_adjoint_mgrit_parity(M, name, nx, nt, m, L, T, kw):
+    scheme = O.SCHEME_FO_FE if name.startswith("fo") else O.SCHEME_WENO5_SSPRK3
+    flux = O.FLUX_ADVECTION if name == "advection" else O.FLUX_BURGERS
+    u0 = inputs.fourier_ic(nx, seed=21)
+    fwd = O.mgrit(u0, nt, m, L, T, scheme=scheme, flux=flux, tol=1e-12, max_iter=80,
+                  relax=kw.get("relax", O.RELAX_FCF), guess=kw.get("guess", O.GUESS_EQ17))
+    assert fwd["status"] == O.OK
+    uC = fwd["uC"]
+    lamT = np.random.default_rng(22).standard_normal(nx)
+    ref = O.adjoint_mgrit(uC, lamT, nt, m, L, T, scheme=scheme, flux=flux,
+                          relax=kw.get("relax", O.RELAX_FCF), guess=kw.get("guess", O.GUESS_EQ17),
+                          tol=1e-10, max_iter=60)
+    assert ref["status"] == O.OK
+    S = solver(M, nx, nt, m, L, T, scheme, flux, tol=1e-10, max_iter=60, **kw)
+    st, lam0, lamC, stats = S.adjoint(dev(uC), dev(lamT), want_lamC=True)
+    assert st == M.OK
+    assert stats.iters == ref["iters"]
+    hist = np.array(stats.res_hist[:stats.iters + 1])
+    np.testing.assert_allclose(hist, ref["res_hist"], rtol=1e-9, atol=1e-12 * ref["res_hist"][0])
+    assert relerr(lam0.cpu().numpy(), ref["lam0"]) <= RTOL
+    assert relerr(lamC.cpu().numpy(), ref["lamC"]) <= RTOL
+
+
+def test_adjoint_mgrit_is_deterministic(M):
+    nx, nt, m, L, T = 512, 256, 4, 3, 0.02
+    u0 = dev(inputs.fourier_ic(nx, seed=3))
+    S = solver(M, nx, nt, m, L, T)
+    st, _, uC, _ = S.solve(u0)
+    lamT = dev(np.random.default_rng(3).standard_normal(nx))
+    a = S.adjoint(uC, lamT, want_lamC=True)
+    b = S.adjoint(uC, lamT, want_lamC=True)
+    assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+    assert list(a[3].res_hist[:a[3].iters + 1]) == list(b[3].res_hist[:b[3].iters + 1])
+
+
+def test_autograd_function_gives_the_serial_adjoint_gradient(M):
+    # J = 1/2 ||u(T) - target||^2 through the differentiable MGRIT solve;
+    # its gradient equals the oracle's serial adjoint to the solver tolerance
+    nx, nt, m, L, T = 128, 256, 4, 3, 0.08
+    u0 = inputs.fourier_ic(nx, seed=31)
+    target = O.serial(inputs.fourier_ic(nx, seed=1031), T / nt, nt)
+    S = solver(M, nx, nt, m, L, T, tol=1e-12)
+    x = dev(u0).requires_grad_(True)
+    uT = M.mgrit_solve(x, S)
+    J = 0.5 * ((uT - dev(target)) ** 2).sum()
+    J.backward()
+    uT_ref = O.serial(u0, T / nt, nt)
+    ref = O.adjoint_serial(u0, uT_ref - target, T / nt, nt)
+    assert relerr(x.grad.cpu().numpy(), ref) <= 1e-9
+
+
+def test_adjoint_rejects_the_state_flux(M):
+    S = solver(M, 64, 64, 4, 2, 0.05, numflux=1)
+    with pytest.raises(M.MGRITError) as e:
+        S.adjoint(dev(np.zeros((17, 64))), dev(np.zeros(64)))
+    assert "split" in str(e.value)
+
+
+# -------------------------------------------- full adjoint workload --------
+
+@pytest.mark.parametrize("T,L,h", [(0.12, 3, 1e-6), (0.3, 2, 1e-7)])
+def test_full_size_gradient_against_finite_differences(M, T, L, h):
+    # nx = 2048, nt = 8192, m = 4, J = 1/2 ||u(T) - u_target||^2 with
+    # u_target the forward solution from a perturbed seed; u0 of seed 1 breaks
+    # at t = 0.20, so T = 0.12 is pre-shock and T = 0.3 post-shock (levels
+    # limited by the coarse CFL: 0.51 on level 2 at T = 0.12, 0.32 on level 1
+    # at T = 0.3).  The MGRIT gradient must match the GPU serial adjoint, and
+    # that the central differences of J evaluated by GPU serial stepping
+    # (32 directions, relative 1e-6).
+    # After the shock |u| is nearly flat just upstream of it, so the cell
+    # that attains alpha = max|f'| switches under perturbations of ~1e-6: J
+    # is only piecewise differentiable on that scale and central differences
+    # with h = 1e-6 straddle the kinks (7e-6 relative here; on the CPU oracle
+    # at this size the gap is 1e-5, 2e-6, 7e-8 at h = 1e-5, 1e-6, 1e-7, not the
+    # h^2 of a truncation error).  Post-shock the step is therefore 1e-7.
+    # There the rounding of J (~600, evaluated through 8192 steps whose
+    # rounding differs between the +h and -h runs, ~2e-13) contributes ~1e-6
+    # absolute to the quotient; it is measured per direction as
+    # |FD(2h) - FD(h)| (truncation and kinks are negligible at these h) and
+    # allowed twice over on top of the 1e-6 relative bar; the median
+    # relative error over the directions must meet 1e-6 outright.
+    nx, nt, m = 2048, 8192, 4
+    u0 = dev(inputs.fourier_ic(nx, seed=1))
+    S = solver(M, nx, nt, m, L, T, tol=1e-11, max_iter=80)
+    target = S.serial_step(dev(inputs.fourier_ic(nx, seed=1001)), nt)
+
+    def J(x):
+        return 0.5 * float(((S.serial_step(x, nt) - target) ** 2).sum())
+
+    st, uT, uC, _ = S.solve(u0)
+    assert st == M.OK
+    lamT = (uT - target).contiguous()
+    st, g, _, stats = S.adjoint(uC, lamT)
+    assert st == M.OK
+    g_serial = S.adjoint_serial(u0, (S.serial_step(u0, nt) - target).contiguous())
+    assert relerr(g.cpu().numpy(), g_serial.cpu().numpy()) <= 1e-7
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    gn = float(g_serial.norm())
+    rel = []
+    for _ in range(32):
+        v = torch.randn(nx, dtype=torch.float64, device="cuda", generator=gen)
+        fd = (J(u0 + h * v) - J(u0 - h * v)) / (2 * h)
+        fd2 = (J(u0 + 2 * h * v) - J(u0 - 2 * h * v)) / (4 * h)
+        gv = float(g_serial @ v)
+        scale = max(abs(fd), 1e-3 * gn * float(v.norm()))
+        assert abs(gv - fd) <= 1e-6 * scale + 2 * abs(fd2 - fd), (gv, fd, fd2)
+        rel.append(abs(gv - fd) / scale)
+    assert np.median(rel) <= 1e-6, sorted(rel)

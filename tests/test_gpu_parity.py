@@ -74,6 +74,24 @@ def test_serial_stepping_parity(M, nx, scheme, flux, numflux, nsteps, cfl):
     assert relerr(out.cpu().numpy(), ref) <= RTOL
 
 
+@pytest.mark.parametrize("nx,scheme,flux,nsteps", [
+    (300, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, 120),   # single CTA
+    (2048, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, 64),   # 8-CTA cluster
+    (4096, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS, 32),   # 16-CTA cluster
+    (777, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION, 60),
+    (257, O.SCHEME_FO_FE, O.FLUX_BURGERS, 200),
+])
+def test_roe_flux_serial_parity(M, nx, scheme, flux, nsteps):
+    # sin(2 pi x) changes sign: transonic interfaces exercise the entropy fix
+    u0 = inputs.sine_ic(nx, offset=0.0)
+    T = time_for_cfl(u0, nx, nsteps, flux, 0.5)
+    s = M.Solver(nx, nsteps, 2, 2, scheme, flux, T=T, numflux=O.NUMFLUX_ROE)
+    out = s.serial_step(dev(u0), nsteps)
+    torch.cuda.synchronize()
+    ref = O.serial(u0, T / nsteps, nsteps, scheme, flux, O.NUMFLUX_ROE)
+    assert relerr(out.cpu().numpy(), ref) <= RTOL
+
+
 @pytest.mark.parametrize("nx,K", [(256, 1), (512, 2), (1000, 2), (2048, 8), (4096, 16), (8192, 16)])
 def test_sequential_stepper_cluster_shape(M, nx, K):
     # the serial stepper and the coarsest solve spread one slab over a
@@ -116,20 +134,52 @@ MGRIT_CASES = [
     ("fourier-256", 256, 1024, 4, 3, 0.05, {}, 7),
     ("m8-coarsest-1-step", 32, 64, 8, 3, 0.05, {}, 8),
     ("nx5", 5, 32, 2, 3, 0.02, {}, 9),
+    ("f-cycle-L3", 64, 1024, 4, 3, 0.1, dict(cycle=O.CYCLE_F), 3),
+    ("f-cycle-L4-F-relax", 64, 1024, 4, 4, 0.1, dict(cycle=O.CYCLE_F, relax=O.RELAX_F), 3),
+    ("f-cycle-L5-fo", 96, 1024, 4, 5, 0.1, dict(cycle=O.CYCLE_F, scheme=O.SCHEME_FO_FE), 10),
+    # classical Lax-Friedrichs + FE (Eq. fineLF) with rediscretised or matched
+    # coarse integrators (Sec. 3.3) on the paper's stationary / moving shocks
+    ("lf-redisc-L5-diverges", 64, 512, 2, 5, 0.475,
+     dict(scheme=O.SCHEME_LF_FE, relax=O.RELAX_F), "stationary"),
+    ("lf-psi0-L5", 64, 512, 2, 5, 0.475,
+     dict(scheme=O.SCHEME_LF_FE, relax=O.RELAX_F, coarse=O.COARSE_PSI0), "stationary"),
+    ("lf-psi1-L5", 128, 1024, 2, 5, 0.475,
+     dict(scheme=O.SCHEME_LF_FE, relax=O.RELAX_F, coarse=O.COARSE_PSI1), "stationary"),
+    ("lf-psi1-L4-fcf-fcycle", 64, 512, 2, 4, 0.475,
+     dict(scheme=O.SCHEME_LF_FE, coarse=O.COARSE_PSI1, cycle=O.CYCLE_F), "moving"),
+    ("lf-psi1-advection", 64, 256, 4, 3, 0.2,
+     dict(scheme=O.SCHEME_LF_FE, flux=O.FLUX_ADVECTION, coarse=O.COARSE_PSI1), 3),
+    ("lf-psi0-m4-ragged", 100, 512, 4, 3, 0.3,
+     dict(scheme=O.SCHEME_LF_FE, coarse=O.COARSE_PSI0), "moving"),
+    # Roe flux with the Harten-Hyman entropy fix (Eq. roeflux)
+    ("roe-weno-L3", 64, 256, 4, 3, 0.2, dict(numflux=O.NUMFLUX_ROE), "stationary"),
+    ("roe-fo-L2", 96, 256, 4, 2, 0.2, dict(scheme=O.SCHEME_FO_FE, numflux=O.NUMFLUX_ROE),
+     "stationary"),
+    ("roe-weno-fcycle-512", 512, 2048, 4, 4, 0.1,
+     dict(numflux=O.NUMFLUX_ROE, cycle=O.CYCLE_F), 12),
 ]
 
 
 def run_pair(M, nx, nt, m, L, T, kw, seed, max_iter=40, tol=1e-10):
-    u0 = inputs.sine_ic(nx) if seed is None else inputs.fourier_ic(nx, seed=seed)
+    if seed is None:
+        u0 = inputs.sine_ic(nx)
+    elif seed == "stationary":             # sin(2 pi x): a shock that stays at x = 1/2
+        u0 = inputs.sine_ic(nx, offset=0.0)
+    elif seed == "moving":                 # (1 + sin(2 pi x)) / 2: a moving shock
+        u0 = inputs.sine_ic(nx, offset=0.5, amp=0.5)
+    else:
+        u0 = inputs.fourier_ic(nx, seed=seed)
     scheme = kw.get("scheme", O.SCHEME_WENO5_SSPRK3)
     flux = kw.get("flux", O.FLUX_BURGERS)
     params = dict(T=T, tol=tol, max_iter=max_iter, numflux=kw.get("numflux", 0),
-                  relax=kw.get("relax", O.RELAX_FCF), guess=kw.get("guess", O.GUESS_EQ17))
+                  relax=kw.get("relax", O.RELAX_FCF), guess=kw.get("guess", O.GUESS_EQ17),
+                  cycle=kw.get("cycle", O.CYCLE_V), coarse=kw.get("coarse", O.COARSE_REDISC))
     s = M.Solver(nx, nt, m, L, scheme, flux, **params)
     st, uT, uC, stats = s.solve(dev(u0))
     torch.cuda.synchronize()
     ref = O.mgrit(u0, nt, m, L, T, scheme=scheme, flux=flux, numflux=params["numflux"],
-                  relax=params["relax"], guess=params["guess"], tol=tol, max_iter=max_iter)
+                  relax=params["relax"], guess=params["guess"], tol=tol, max_iter=max_iter,
+                  cycle=params["cycle"], coarse=params["coarse"])
     return st, uT.cpu().numpy(), uC.cpu().numpy(), stats, ref, s, u0
 
 
