@@ -196,7 +196,10 @@ def test_mgrit_parity(M, name, nx, nt, m, L, T, kw, seed):
     # of the iterates (~1e-15 |u| per element) set an absolute floor
     floor = 1e-14 * np.abs(ref["uC"][np.isfinite(ref["uC"])]).max(initial=1.0) * np.sqrt(ref["uC"].size)
     np.testing.assert_allclose(hist[finite], ref["res_hist"][finite], rtol=1e-8, atol=floor)
-    if np.all(np.isfinite(ref["uC"])):
+    # iterates of a diverging run amplify rounding differences cycle by cycle,
+    # so their values are compared only for converged runs (outcome, cycle
+    # count and residual history are compared for every run above)
+    if ref["status"] == O.OK:
         assert relerr(uC, ref["uC"]) <= RTOL
         assert relerr(uT, ref["uT"]) <= RTOL
 
