@@ -61,7 +61,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per level-0 relaxation launch from an ncu
 # capture, keyed by a hash of the kernel sources it was taken on; reported
 # only while the kernel is unchanged.
-TRAFFIC = {"8b9f38a8fee32ad0": 144402688 + 345180160}   # profiles/relax_l0_c2_fp64.md
+TRAFFIC = {"297c4e1680f32eb2": 147084544 + 345705216}   # profiles/relax_l0_c2_fp64.md
 
 
 def kernel_hash():

@@ -247,7 +247,9 @@ int mgrit_step_vjp(mgrit_ctx *ctx, const double *u_dev, const double *lam_dev, d
  * lamT_dev = dJ/du^nt, through nt fine steps from u0_dev.  One CTA steps
  * forward keeping u^{mj}, j < nt/m, then for each chunk from the last it
  * recomputes the chunk's m states from its checkpoint and applies their m
- * transposed steps backward.  Asynchronous.  Baseline for mgrit_adjoint. */
+ * transposed steps backward; for nx >= 512 on a thread-block cluster of up to
+ * 16 CTAs (mgrit_adjoint_query(ctx, 2)).  Asynchronous.  Baseline for
+ * mgrit_adjoint. */
 int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const double *lamT_dev,
                          double *lam0_dev, void *stream);
 
@@ -276,7 +278,10 @@ int mgrit_adjoint(mgrit_ctx *ctx, const double *uC_dev, const double *lamT_dev, 
                   double *lamC_dev, void *stream, mgrit_stats *stats);
 
 /* Adjoint launch shape: what = 0 cells per thread, 1 threads per CTA
- * (0 when the context's nx or numerical flux has no adjoint); -1 otherwise. */
+ * (0 when the context's nx or numerical flux has no adjoint); 2 CTAs per
+ * thread-block cluster of the sequential adjoint chains (the coarsest
+ * adjoint solve and mgrit_adjoint_serial; 1 = a single CTA), known after the
+ * first adjoint call (0 before); -1 otherwise. */
 int mgrit_adjoint_query(const mgrit_ctx *ctx, int what);
 
 /* ------------------------------------------------------------------------

@@ -1,6 +1,6 @@
 // Table of adjoint kernel instances (FP64), indexed by [scheme][flux][cells-per-thread].
 #pragma once
-#include "adjoint.cuh"
+#include "cluster_adjoint.cuh"
 
 namespace mgrit {
 
@@ -8,6 +8,7 @@ constexpr int NCPT_ADJ = 4;   // 1, 2, 4, 8 cells per thread: nx <= 4096 at 512 
 
 struct AdjTable {
     const void *k[2][2][NCPT_ADJ];
+    const void *kc[2][2][2];   // k_adjoint_cluster, cells per thread 1 or 2
 };
 
 template <int S, int F>
@@ -17,6 +18,8 @@ void fill_adj_sf(AdjTable &t)
     t.k[S][F][1] = (const void *)&k_adjoint<S, F, 2>;
     t.k[S][F][2] = (const void *)&k_adjoint<S, F, 4>;
     t.k[S][F][3] = (const void *)&k_adjoint<S, F, 8>;
+    t.kc[S][F][0] = (const void *)&k_adjoint_cluster<S, F, 1>;
+    t.kc[S][F][1] = (const void *)&k_adjoint_cluster<S, F, 2>;
 }
 
 // one translation unit per (scheme, flux) group, compiled in parallel

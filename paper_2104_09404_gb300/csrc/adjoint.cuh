@@ -35,27 +35,33 @@ namespace mgrit {
 //   dW = sum_r w_r dp_r + sum_r (p_r - W) dalpha_r / sum alpha,
 //   dalpha_r = -2 alpha_r / s_r dbeta_r,
 //   beta_r = 13/12 x_r^2 + 1/4 y_r^2  ->  dbeta_r = 13/6 x_r dx_r + 1/2 y_r dy_r.
+// Two divisions: 1/s_r = (product of the other two s) / (s_0 s_1 s_2), and
+// 1 / sum alpha (each s_r >= eps = 1e-6, so the product stays normal).
 template <typename R>
 __device__ __forceinline__ void weno5_left_grad(R a, R b, R c, R d, R e, R (&g)[5])
 {
     const R eps = R(1e-6);
-    const R p0 = (R(2) * a - R(7) * b + R(11) * c) / R(6);   // stencil {i-2, i-1, i}, d = 1/10
-    const R p1 = (-b + R(5) * c + R(2) * d) / R(6);         // stencil {i-1, i, i+1}, d = 6/10
-    const R p2 = (R(2) * c + R(5) * d - e) / R(6);          // stencil {i, i+1, i+2}, d = 3/10
+    const R sixth = R(1.0 / 6.0);
+    const R p0 = (R(2) * a - R(7) * b + R(11) * c) * sixth;   // stencil {i-2, i-1, i}, d = 1/10
+    const R p1 = (-b + R(5) * c + R(2) * d) * sixth;         // stencil {i-1, i, i+1}, d = 6/10
+    const R p2 = (R(2) * c + R(5) * d - e) * sixth;          // stencil {i, i+1, i+2}, d = 3/10
     const R x0 = a - R(2) * b + c, y0 = a - R(4) * b + R(3) * c;
     const R x1 = b - R(2) * c + d, y1 = b - d;
     const R x2 = c - R(2) * d + e, y2 = R(3) * c - R(4) * d + e;
     const R s0 = eps + R(13.0 / 12.0) * x0 * x0 + R(0.25) * y0 * y0;
     const R s1 = eps + R(13.0 / 12.0) * x1 * x1 + R(0.25) * y1 * y1;
     const R s2 = eps + R(13.0 / 12.0) * x2 * x2 + R(0.25) * y2 * y2;
-    const R a0 = R(0.1) / (s0 * s0), a1 = R(0.6) / (s1 * s1), a2 = R(0.3) / (s2 * s2);
+    const R s12 = s1 * s2;
+    const R iD = R(1) / (s0 * s12);
+    const R r0 = s12 * iD, r1 = s0 * s2 * iD, r2 = s0 * s1 * iD;   // 1 / s_r
+    const R a0 = R(0.1) * r0 * r0, a1 = R(0.6) * r1 * r1, a2 = R(0.3) * r2 * r2;
     const R inv = R(1) / (a0 + a1 + a2);
     const R w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
     const R W = w0 * p0 + w1 * p1 + w2 * p2;
-    // (p_r - W) (dalpha_r / dbeta_r) / sum alpha
-    const R k0 = (p0 - W) * (R(-2) * a0 / s0) * inv;
-    const R k1 = (p1 - W) * (R(-2) * a1 / s1) * inv;
-    const R k2 = (p2 - W) * (R(-2) * a2 / s2) * inv;
+    // (p_r - W) (dalpha_r / dbeta_r) / sum alpha = (p_r - W) (-2 w_r / s_r)
+    const R k0 = (p0 - W) * (R(-2) * w0 * r0);
+    const R k1 = (p1 - W) * (R(-2) * w1 * r1);
+    const R k2 = (p2 - W) * (R(-2) * w2 * r2);
     // dbeta_r/dq = 13/6 x_r dx_r/dq + 1/2 y_r dy_r/dq with
     //   x0: (1,-2,1,0,0)  y0: (1,-4,3,0,0)
     //   x1: (0,1,-2,1,0)  y1: (0,1,0,-1,0)

@@ -31,6 +31,11 @@ struct AdjWork {
     const void *fn;      // k_adjoint instance for (scheme, flux, cells per thread)
     int threads, cpt;
     size_t smem;
+    // sequential chains (coarsest adjoint solve, serial adjoint) on a cluster:
+    // k_adjoint_cluster instance, null if nx < 512 or no cluster fits
+    const void *cfn;
+    int cK, cthreads;
+    size_t csmem, cfwd;
     double *traj;
     double *u[MAXLEV], *g[MAXLEV];
     double *newC[MAXLEV], *phirow[MAXLEV], *cstep[MAXLEV];
@@ -136,6 +141,52 @@ static int adj_alloc(mgrit_ctx *ctx, AdjWork *w)
     return MGRIT_OK;
 }
 
+// Cluster for the sequential adjoint chains: as the forward stepper, the
+// largest power of two K <= 16 leaving at least 256 cells per CTA, reduced
+// until one cluster of that shape can be co-scheduled; nx < 512 keeps one CTA.
+static void adj_choose_cluster(const mgrit_ctx *ctx, AdjWork *w)
+{
+    w->cfn = nullptr;
+    const int nx = ctx->nx;
+    int K = 1;
+    while (K < CLUSTER_MAX && nx / (2 * K) >= 256) K *= 2;
+    for (; K >= 2; K /= 2) {
+        const int nmax = (nx + K - 1) / K;
+        const int cpt = nmax <= 512 ? 1 : 2;
+        if (nmax > 1024) break;
+        const void *fn = adj_table().kc[ctx->scheme][ctx->flux][cpt - 1];
+        const size_t fwd = cluster_smem_bytes<double>(nx, K);
+        const size_t smem = fwd + cluster_adj_extra_bytes<double>(nx, K);
+        const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+            continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(K);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = K;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        w->cfn = fn;
+        w->cK = K;
+        w->cthreads = threads;
+        w->csmem = smem;
+        w->cfwd = fwd;
+        return;
+    }
+    cudaGetLastError();   // clear a refused attribute or occupancy query
+}
+
 // adjoint workspaces on first use; a failed allocation leaves none behind
 static int adj_ensure(mgrit_ctx *ctx)
 {
@@ -148,8 +199,12 @@ static int adj_ensure(mgrit_ctx *ctx)
     memset(w, 0, sizeof *w);
     ctx->adj = w;
     adj_choose(ctx, w);
-    if ((st = adj_alloc(ctx, w))) mgrit_adj_free(ctx);
-    return st;
+    if ((st = adj_alloc(ctx, w))) {
+        mgrit_adj_free(ctx);
+        return st;
+    }
+    adj_choose_cluster(ctx, w);
+    return MGRIT_OK;
 }
 
 static AdjArgs adj_base(const mgrit_ctx *ctx, int mode, int l)
@@ -181,6 +236,28 @@ static cudaError_t adj_launch(const mgrit_ctx *ctx, int grid, cudaStream_t s, Ad
     const AdjWork *w = ctx->adj;
     void *args[] = {a};
     return cudaLaunchKernel(w->fn, dim3(grid), dim3(w->threads), args, w->smem, s);
+}
+
+// a sequential chain (ADJ_SEQ, ADJ_SERIAL): one cluster if chosen, else one CTA
+static cudaError_t adj_launch_seq(const mgrit_ctx *ctx, cudaStream_t s, AdjArgs *a)
+{
+    const AdjWork *w = ctx->adj;
+    if (!w->cfn) return adj_launch(ctx, 1, s, a);
+    unsigned long long fwd = w->cfwd;
+    void *args[] = {a, &fwd};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(w->cK);
+    cfg.blockDim = dim3(w->cthreads);
+    cfg.dynamicSmemBytes = w->csmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = w->cK;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, w->cfn, args);
 }
 
 static cudaError_t adj_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
@@ -229,7 +306,7 @@ static cudaError_t adj_coarse(mgrit_ctx *ctx, cudaStream_t s)
     a.rows = w->u[l];
     a.nsteps = ctx->nt_l[l];
     a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
-    return adj_launch(ctx, 1, s, &a);
+    return adj_launch_seq(ctx, s, &a);
 }
 
 static cudaError_t adj_interp(mgrit_ctx *ctx, int l, cudaStream_t s)
@@ -305,7 +382,7 @@ extern "C" int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const 
     a.out = lam0_dev;
     a.rows = w->cps;
     a.nrows_rows = ctx->nC_l[0];
-    CK(adj_launch(ctx, 1, (cudaStream_t)stream, &a));
+    CK(adj_launch_seq(ctx, (cudaStream_t)stream, &a));
     return MGRIT_OK;
 }
 
@@ -385,6 +462,7 @@ extern "C" int mgrit_adjoint_query(const mgrit_ctx *ctx, int what)
     switch (what) {
     case 0: return ok ? w.cpt : 0;
     case 1: return ok ? w.threads : 0;
+    case 2: return ctx->adj ? (ctx->adj->cfn ? ctx->adj->cK : 1) : 0;
     default: return -1;
     }
 }

@@ -230,7 +230,8 @@ class Solver:
         return st, lam0, lamC, stats
 
     def adjoint_query(self, what):
-        """0: cells per thread, 1: threads per CTA of the adjoint kernels (0: unsupported)."""
+        """0: cells per thread, 1: threads per CTA of the adjoint kernels (0: unsupported);
+        2: CTAs per cluster of the sequential adjoint chains (after the first adjoint call)."""
         return load().mgrit_adjoint_query(self._h, what)
 
     def close(self):

@@ -103,11 +103,17 @@ def test_step_vjp_in_place(M):
 # ------------------------------------------------------------ serial -------
 
 SERIAL_CASES = [
-    # nx, nt, m, T, scheme, flux
+    # nx, nt, m, T, scheme, flux (nx >= 512 runs on a thread-block cluster:
+    # 1000 -> 2 CTAs of 500 cells, 2048 -> 8, 4096 -> 16)
     (128, 64, 4, 0.05, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
     (1000, 32, 8, 0.01, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
     (333, 48, 4, 0.05, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION),
     (200, 100, 4, 0.1, O.SCHEME_FO_FE, O.FLUX_BURGERS),
+    (2048, 64, 4, 0.01, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (4096, 32, 4, 0.004, O.SCHEME_WENO5_SSPRK3, O.FLUX_BURGERS),
+    (1500, 48, 4, 0.02, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION),
+    (600, 64, 4, 0.05, O.SCHEME_FO_FE, O.FLUX_ADVECTION),
+    (777, 64, 4, 0.05, O.SCHEME_FO_FE, O.FLUX_BURGERS),
 ]
 
 
@@ -119,6 +125,17 @@ def test_adjoint_serial_parity(M, nx, nt, m, T, scheme, flux):
     got = S.adjoint_serial(dev(u0), dev(lamT)).cpu().numpy()
     ref = O.adjoint_serial(u0, lamT, T / nt, nt, scheme=scheme, flux=flux)
     assert relerr(got, ref) <= RTOL
+
+
+@pytest.mark.parametrize("nx,K", [(256, 1), (1000, 2), (2048, 8), (4096, 16)])
+def test_sequential_adjoint_cluster_shape(M, nx, K):
+    # the serial adjoint and the coarsest adjoint solve spread one slab over a
+    # cluster of K CTAs (at least 256 cells each), as the forward stepper does
+    S = solver(M, nx, 16, 4, 2, 0.001)
+    u0 = dev(inputs.fourier_ic(nx, seed=1))
+    S.adjoint_serial(u0, u0.clone())
+    torch.cuda.synchronize()
+    assert S.adjoint_query(2) == K
 
 
 # ------------------------------------------------------------ MGRIT --------
