@@ -33,6 +33,8 @@ def main(argv=None):
     p.add_argument("--level", type=int, default=0)
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--adjoint", action="store_true")
+    p.add_argument("--precision", type=int, default=64, choices=(64, 32),
+                   help="32: the FP32-sweep instances of the kernels")
     a = p.parse_args(argv)
     import torch
     from . import inputs, mgrit
@@ -48,7 +50,7 @@ def main(argv=None):
         print("adjoint workload: trajectory + one adjoint cycle")
         return 0
     c = CASES[a.case]
-    s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"])
+    s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"], precision=a.precision)
     u0 = torch.as_tensor(inputs.fourier_ic(c["nx"], seed=0), device="cuda")
     s.run_cycles(u0, 0)
     s.launch_kernel(KERNELS[a.kernel], a.level, a.reps)
