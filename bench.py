@@ -180,6 +180,16 @@ def cycle_updates(w, fcf=True):
     return steps * w["nx"]
 
 
+def workload_config(ws):
+    """The config object of both arms' JSON lines (the bench workload)."""
+    return {"workload": "Burgers WENO5-JS/LF-split/SSPRK3 FP64 MGRIT V-cycle: nx=4096, "
+                        "nt=16384, T=1, m=4, 6 levels, FCF, Fourier u0 seed 0",
+            "step": "one V-cycle (all levels) from the initial iterate",
+            "cell_updates_per_step": cycle_updates(WORKLOAD),
+            "l2": "inputs larger than L2: each cycle streams >500 MB of level rows",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 def sample_desc(s):
     return ("one V-cycle of the workload over its first quarter: nx=%d, nt=%d, T=%g, m=%d, "
             "%d levels, seed %d" % (s["nx"], s["nt"], s["T"], s["m"], s["levels"], s["seed"]))
@@ -204,9 +214,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "FP64 C oracle (CPU), " + sample_desc(SAMPLE)},
+        "config": workload_config(ws),
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
-                         "kind": "oracle", "sample": sample_desc(SAMPLE)},
+                         "kind": "oracle",
+                         "sample": "FP64 C oracle on the host cores: " + sample_desc(SAMPLE)},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -554,12 +565,7 @@ def run_mgrit(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "Burgers WENO5-JS/LF-split/SSPRK3 FP64 MGRIT V-cycle: nx=4096, "
-                               "nt=16384, T=1, m=4, 6 levels, FCF, Fourier u0 seed 0",
-                   "step": "one V-cycle (all levels) from the initial iterate",
-                   "cell_updates_per_step": per_cycle,
-                   "l2": "inputs larger than L2: each cycle streams >500 MB of level rows",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": workload_config(ws),
         "roofline": {"bound": "alu", "kernel": "level-0 relaxation (k_slab, MODE_RELAX)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
