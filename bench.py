@@ -86,6 +86,24 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(ms, ws, device=None):
+    """The slowest rank's time: every rank passes its own CUDA-event time and
+    gets the maximum (all-reduce MAX over the default process group)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, units_per_step, steps, ms):
+    """Units processed by all ranks (weak scaling: each rank runs its own
+    replica of the workload) per second of the slowest rank."""
+    return ws * units_per_step * steps / (ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -373,12 +391,8 @@ def run_mgrit(args):
     e1.record(stream)
     barrier_sync()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * per_cycle * args.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    value = whole_job_rate(ws, per_cycle, args.steps, ms)
 
     # ---- end to end through the C ABI with host buffers -----------------
     h_u0 = torch.as_tensor(u0_np).pin_memory()
@@ -400,12 +414,8 @@ def run_mgrit(args):
         e2e_step()
     e1.record(stream)
     barrier_sync()
-    ms_e2e = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = ws * per_cycle * args.steps / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    e2e_value = whole_job_rate(ws, per_cycle, args.steps, ms_e2e)
 
     # ---- per-kernel times (CUDA events, same stream) ----------------------
     # The level-0 relaxation is timed on the cycle's own level-0 input (the
