@@ -523,6 +523,10 @@ def run_mgrit(args):
         bt.autotune(bu0, reps=2)
         tune_s = time.perf_counter() - t0
         per_batch = bt.cycle_cell_updates()
+        tuned = {}
+        for what, name in ((0, "cells_per_thread"), (3, "slabs_per_cta"), (4, "coarsest_cluster_ctas")):
+            vals = [bt.query(i, what) for i in range(len(insts))]
+            tuned[name] = {str(v): vals.count(v) for v in sorted(set(vals))}
         for _ in range(2):
             bt.run_cycles(bu0, 1)
         torch.cuda.synchronize()
@@ -552,7 +556,8 @@ def run_mgrit(args):
                    "value": per_batch * args.steps / (msb / 1e3), "unit": "cell-updates/s",
                    "ms_per_cycle": msb / args.steps,
                    "one_context_at_a_time_ms_per_cycle": mss / args.steps,
-                   "speedup_vs_one_at_a_time": mss / msb, "autotune_seconds": tune_s}
+                   "speedup_vs_one_at_a_time": mss / msb, "autotune_seconds": tune_s,
+                   "autotuned_instances_per_choice": tuned}
 
     adjoint = None if args.no_adjoint else adjoint_gradient(mgrit, inputs, dev, stream)
     variants = None if args.no_variants else paper_variants(mgrit, inputs, dev)

@@ -320,16 +320,24 @@ int mgrit_batch_run_cycles(mgrit_batch *b, const double *const *u0_dev, int ncyc
 int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const *uT_dev,
                       int *status, int *iters, double *final_res, void *stream);
 
-/* Autotuner: for each group of instances with equal (flux, nx), time the
- * level-0 relaxation with 1x, 2x and 4x the minimal cells per thread and
- * keep the fastest CTA shape; the graphs are rebuilt.  reps >= 1 timed
- * launches per candidate.  Synchronises `stream`. */
+/* Autotuner, three stages, each keeping the fastest candidate by CUDA-event
+ * timing (reps >= 1 timed launches per candidate):
+ *   1. CTA shape: for each group of instances with equal (flux, nx), the
+ *      level-0 relaxation with 1x, 2x and 4x the minimal cells per thread;
+ *   2. slabs per CTA: the slab kernels are persistent (CTA b takes work
+ *      items b, b + grid, ...); for each level-0 launch class, 1, 2, 4 or 8
+ *      items per CTA;
+ *   3. cluster shape: for each group whose coarsest solve can use a
+ *      thread-block cluster (nx >= 512), one CTA or a cluster of 2..16 CTAs.
+ * The graphs are then rebuilt.  Synchronises `stream`. */
 int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, void *stream);
 
 /* Cells x Phi applications of one V-cycle of all instances. */
 double mgrit_batch_cycle_cell_updates(const mgrit_batch *b);
 
-/* what = 0: cells per thread, 1: threads per CTA, 2: levels of instance i. */
+/* what = 0: cells per thread, 1: threads per CTA, 2: levels of instance i,
+ * 3: slabs per CTA of its level-0 launch class, 4: CTAs per cluster of its
+ * coarsest solve (1 = one CTA); -1 for an unknown `what` or instance. */
 int mgrit_batch_query(const mgrit_batch *b, int instance, int what);
 
 /* C-points of instance i after its last level-0 relaxation (as

@@ -17,23 +17,29 @@ struct BatchItem {
     int block;      // block index within the item (restriction) or 0
 };
 
+// Persistent over the `nitems` work items of the map: CTA b takes items b,
+// b + gridDim.x, ... (slabs per CTA = nitems / gridDim.x, chosen by the
+// autotuner).  Each item's first shared-memory write follows the barrier that
+// opens Slab::fluxes, so consecutive items of a CTA do not race.
 // `active` (may be null): instances whose entry is 0 have converged and skip all work
 template <typename R, int SCHEME, int FLUX, int CPT>
 __global__ void __launch_bounds__(512) k_slab_batch(const SlabArgs<R> *__restrict__ args,
                                                     const BatchItem *__restrict__ map,
-                                                    const int *__restrict__ active)
+                                                    const int *__restrict__ active, int nitems)
 {
-    const BatchItem it = map[blockIdx.x];
-    if (active && !active[it.instance]) return;
-    const SlabArgs<R> a = args[it.args];
     extern __shared__ __align__(16) unsigned char smem[];
-    Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
-    if (a.mode == MODE_RELAX)
-        relax_chunk(S, a, it.chunk);
-    else if (a.mode == MODE_INTERP)
-        interp_chunk(S, a, it.chunk);
-    else
-        seq_march(S, a);
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const BatchItem it = map[w];
+        if (active && !active[it.instance]) continue;   // uniform over the CTA
+        const SlabArgs<R> a = args[it.args];
+        Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
+        if (a.mode == MODE_RELAX)
+            relax_chunk(S, a, it.chunk);
+        else if (a.mode == MODE_INTERP)
+            interp_chunk(S, a, it.chunk);
+        else
+            seq_march(S, a);
+    }
 }
 
 // Sequential solves of many items, one thread-block cluster per item (all

@@ -862,6 +862,7 @@ struct BLaunch {
     int state_f32, un_f32;
     void *d_args;
     BatchItem *d_map;
+    int nitems;         // slab kernel: work items in the map (nblocks = ceil(nitems / slabs per CTA))
 };
 
 const BatchTable &btable()
@@ -893,6 +894,8 @@ struct mgrit_batch {
     std::vector<mgrit_ctx *> ctx;
     std::vector<int> cpt;        // cells per thread of the sweep kernels, per instance
     std::vector<int> cpt64;      // cells per thread of the FP64 coarsest solve, per instance
+    std::vector<int> ck;         // coarsest solve: cluster size per instance (1: one CTA)
+    std::map<std::tuple<int, int, int>, int> spc;   // slabs per CTA per launch class (default 1)
     int maxL;
     int *d_active;
     int *h_active;
@@ -976,7 +979,10 @@ struct SlabGroups {
                                   : btable().slab64[flux][cpt_index(cpt)];
             L.threads = std::get<2>(kv.first);
             L.smem = slab_smem_bytes<R>(grp.nx_max);
-            L.nblocks = (int)grp.map.size();
+            L.nitems = (int)grp.map.size();
+            const auto it = b->spc.find(kv.first);
+            const int spc = it == b->spc.end() ? 1 : it->second;
+            L.nblocks = (L.nitems + spc - 1) / spc;
             SlabArgs<R> *da;
             int st;
             if ((st = upload(b, grp.args, &da))) return st;
@@ -1048,7 +1054,53 @@ static int emit_interp(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
     return sg.emit(b, out);
 }
 
-static int emit_coarse(mgrit_batch *b, std::vector<BLaunch> &out)
+// launch shape of the batched FP64 coarsest solve of one nx on a cluster of K
+// CTAs (cells per thread 1 or 2); false if K does not fit or cannot be
+// co-scheduled
+static bool batch_cluster_shape(int nx, int flux, int K, ClusterLaunch *lc)
+{
+    memset(lc, 0, sizeof *lc);
+    if (K < 2 || K > CLUSTER_MAX) return false;
+    const int nmax = (nx + K - 1) / K;
+    if (nmax > 2 * MAX_THREADS || nmax < 2 * GHOST) return false;
+    const int cpt = nmax <= MAX_THREADS ? 1 : 2;
+    const void *fn = btable().seqc64[flux][cpt - 1];
+    const size_t smem = cluster_smem_bytes<double>(nx, K);
+    const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+    if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    lc->fn = fn;
+    lc->K = K;
+    lc->cpt = cpt;
+    lc->threads = threads;
+    lc->smem = smem;
+    return true;
+}
+
+static int emit_coarse(mgrit_batch *b, std::vector<BLaunch> &out,
+                       const std::vector<int> *only = nullptr)
 {
     SlabGroups<double> sg;
     // cluster launches grouped by (flux, cells per thread, cluster size, threads)
@@ -1058,13 +1110,15 @@ static int emit_coarse(mgrit_batch *b, std::vector<BLaunch> &out)
     std::vector<BatchItem> cmap;
     for (int i = 0; i < b->n; ++i) {
         mgrit_ctx *c = b->ctx[i];
-        if (c->lc64.fn) {
-            const auto key = std::make_tuple(c->flux, c->lc64.cpt, c->lc64.K, c->lc64.threads);
+        if (only && std::find(only->begin(), only->end(), i) == only->end()) continue;
+        ClusterLaunch lc;
+        if (b->ck[i] >= 2 && batch_cluster_shape(c->nx, c->flux, b->ck[i], &lc)) {
+            const auto key = std::make_tuple(c->flux, lc.cpt, lc.K, lc.threads);
             auto &e = cg[key];
             const int ai = (int)e.first.size();
             e.first.push_back(coarse_args(c));
             e.second.push_back(BatchItem{ai, 0, i, 0});
-            csmem[key] = std::max(csmem[key], c->lc64.smem);
+            csmem[key] = std::max(csmem[key], lc.smem);
         } else {
             sg.add(i, c->flux, b->cpt64[i], coarse_args(c), 1);
         }
@@ -1133,7 +1187,8 @@ static cudaError_t enqueue_blaunch(const mgrit_batch *b, const BLaunch &L, cudaS
         const int *act = b->d_active;
         void *d_args = L.d_args;
         BatchItem *d_map = L.d_map;
-        void *args[] = {&d_args, &d_map, (void *)&act};
+        int nitems = L.nitems;
+        void *args[] = {&d_args, &d_map, (void *)&act, &nitems};
         return cudaLaunchKernel(L.fn, dim3(L.nblocks), dim3(L.threads), args, L.smem, s);
     }
     case 1:
@@ -1255,11 +1310,13 @@ extern "C" int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst,
         }
         b->cpt.push_back(ln.cpt);
         b->cpt64.push_back(c->ln64.cpt);
+        b->ck.push_back(1);   // set from the occupancy rule once the context has allocated
         b->maxL = std::max(b->maxL, d.levels);
         if ((st = mgrit_ensure_alloc(c))) {
             bfail(b, st, "instance %d: %s", i, c->err);
             break;
         }
+        b->ck.back() = c->lc64.fn ? c->lc64.K : 1;
     }
     mgrit_batch *bb = b;
     auto cleanup = [&]() { mgrit_batch_destroy(bb); };
@@ -1366,9 +1423,67 @@ extern "C" int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, do
     return MGRIT_OK;
 }
 
-// Autotuner: for every group of instances with the same (flux, nx), time the
-// level-0 relaxation with 1x, 2x and 4x the minimal cells per thread (fewer,
-// fuller threads) and keep the fastest; then rebuild the batch graphs.
+// time `reps` replays of a list of launches (after one warm-up replay)
+static int time_launches(mgrit_batch *b, const std::vector<BLaunch> &ls, int reps, cudaStream_t s,
+                         cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    for (const BLaunch &L : ls) BCK(enqueue_blaunch(b, L, s));
+    BCK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r)
+        for (const BLaunch &L : ls) BCK(enqueue_blaunch(b, L, s));
+    BCK(cudaEventRecord(e1, s));
+    BCK(cudaEventSynchronize(e1));
+    BCK(cudaEventElapsedTime(ms, e0, e1));
+    return MGRIT_OK;
+}
+
+static void drop_tables(mgrit_batch *b, size_t keep)
+{
+    for (size_t t = keep; t < b->tables.size(); ++t) cudaFree(b->tables[t]);
+    b->tables.resize(keep);
+}
+
+// slabs per CTA of every level-0 launch class: 1, 2, 4 or 8 work items per
+// CTA of the persistent slab kernel, the fastest kept
+template <typename R>
+static int tune_slabs_per_cta(mgrit_batch *b, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+{
+    SlabGroups<R> sg;
+    for (int i = 0; i < b->n; ++i) {
+        mgrit_ctx *c = b->ctx[i];
+        SlabArgs<R> a = relax_args<R>(c, 0);
+        sg.add(i, c->flux, b->cpt[i], a, a.nC + 1);
+    }
+    std::vector<BLaunch> mine;
+    const size_t keep = b->tables.size();
+    int st = sg.emit(b, mine);
+    auto key = sg.g.begin();
+    for (size_t li = 0; st == MGRIT_OK && li < mine.size(); ++li, ++key) {
+        BLaunch L = mine[li];
+        int best = 1;
+        float best_ms = 1e30f;
+        for (int spc = 1; spc <= 8 && spc <= L.nitems; spc *= 2) {
+            L.nblocks = (L.nitems + spc - 1) / spc;
+            float ms = 0.f;
+            if ((st = time_launches(b, std::vector<BLaunch>{L}, reps, s, e0, e1, &ms))) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = spc;
+            }
+        }
+        b->spc[key->first] = best;
+    }
+    drop_tables(b, keep);
+    return st;
+}
+
+// Autotuner.  (1) For every group of instances with the same (flux, nx), time
+// the level-0 relaxation with 1x, 2x and 4x the minimal cells per thread
+// (fewer, fuller threads) and keep the fastest.  (2) Slabs per CTA of the
+// persistent slab kernel per launch class (tune_slabs_per_cta).  (3) For every
+// group whose coarsest solve can run on a cluster, time it on one CTA and on
+// each cluster size 2..16 that fits, and keep the fastest.  Then rebuild the
+// batch graphs.
 extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps,
                                     void *stream)
 {
@@ -1414,6 +1529,32 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
         if (st) break;
         for (int i : ids) b->cpt[i] = best;
     }
+    if (!st) st = f32 ? tune_slabs_per_cta<float>(b, reps, s, e0, e1)
+                      : tune_slabs_per_cta<double>(b, reps, s, e0, e1);
+    for (auto &kv : groups) {
+        if (st) break;
+        const std::vector<int> &ids = kv.second;
+        if (b->ck[ids[0]] < 2) continue;   // below 512 cells the coarsest solve stays on one CTA
+        int best = b->ck[ids[0]];
+        float best_ms = 1e30f;
+        for (int K = 1; K <= CLUSTER_MAX; K *= 2) {
+            ClusterLaunch lc;
+            if (K >= 2 && !batch_cluster_shape(kv.first.second, kv.first.first, K, &lc)) continue;
+            for (int i : ids) b->ck[i] = K;
+            std::vector<BLaunch> mine;
+            const size_t keep = b->tables.size();
+            float ms = 0.f;
+            if ((st = emit_coarse(b, mine, &ids)) == MGRIT_OK)
+                st = time_launches(b, mine, reps, s, e0, e1, &ms);
+            drop_tables(b, keep);
+            if (st) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = K;
+            }
+        }
+        for (int i : ids) b->ck[i] = best;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
@@ -1435,6 +1576,13 @@ extern "C" int mgrit_batch_query(const mgrit_batch *b, int instance, int what)
     case 0: return b->cpt[instance];
     case 1: return threads_for(b->ctx[instance]->nx, b->cpt[instance]);
     case 2: return b->ctx[instance]->L;
+    case 3: {
+        const mgrit_ctx *c = b->ctx[instance];
+        const auto it = b->spc.find(std::make_tuple(c->flux, b->cpt[instance],
+                                                    threads_for(c->nx, b->cpt[instance])));
+        return it == b->spc.end() ? 1 : it->second;
+    }
+    case 4: return b->ck[instance];
     default: return -1;
     }
 }

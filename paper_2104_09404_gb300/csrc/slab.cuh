@@ -83,7 +83,12 @@ __device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
     const R t0 = s1 * s2;              // d_0 = 1  (x 1/10)
     const R t1 = R(6) * (s0 * s2);     // d_1 = 6
     const R t2 = R(3) * (s0 * s1);     // d_2 = 3
-    return (P0 * t0 + P1 * t1 + P2 * t2) / (R(6) * (t0 + t1 + t2));
+    const R num = P0 * t0 + P1 * t1 + P2 * t2;
+    const R den = R(6) * (t0 + t1 + t2);
+    // FP32 sweeps divide with the fast intrinsic (2 ulp; den lies in
+    // [6e-24, 1e30] for |q| <= 1e3, inside its range); FP64 divides exactly
+    if (sizeof(R) == 4) return R(__fdividef(float(num), float(den)));
+    return num / den;
 }
 
 // Roe flux of a scalar law from the reconstructed states a = u^-, b = u^+
