@@ -61,7 +61,16 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per level-0 relaxation launch from an ncu
 # capture, keyed by a hash of the kernel sources it was taken on; reported
 # only while the kernel is unchanged.
-TRAFFIC = {"297c4e1680f32eb2": 147084544 + 345705216}   # profiles/relax_l0_c2_fp64.md
+TRAFFIC = {"427ef0790805ab37": 143645440 + 344634880}   # profiles/relax_l0_c2_fp64.md
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (GB/s), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def kernel_hash():
@@ -447,6 +456,12 @@ def run_mgrit(args):
     time_kernel("interp_l1", 3, 1)
     nC0 = W["nt"] // W["m"]
     relax0_updates = W["nx"] * (2 * nC0 * W["m"] + nC0)
+    # FAS residual + restriction at level 0 (HBM-bound): per C-point value it
+    # reads Phi_0(u^{mi-1}), the relaxed C-point and Phi_1(u^{m(i-1)}) and
+    # writes g_1 and u_1: 5 FP64 values = 40 B algorithmic, over nC x nx values
+    restrict_bytes = 40.0 * nC0 * W["nx"]
+    restrict_gbs = restrict_bytes / (kern["restrict_l0"] / 1e3) / 1e9
+    hbm_peak = measured_hbm_gbs()
     achieved = FLOPS_PER_CELL_UPDATE * relax0_updates / (kern["relax_l0"] / 1e3) / 1e12
     traffic = TRAFFIC.get(kernel_hash())
 
@@ -574,7 +589,10 @@ def run_mgrit(args):
                "sample": sample_desc(SAMPLE), "seconds": secs}
 
     L = W["levels"]
-    launches_per_cycle = 3 + 2 * (L - 2) + 1 + (L - 2) + 1   # graph A, graph B, init broadcast
+    # graph A (relax, restrict, norm), graph B (relax + restrict per level
+    # 1..L-2, coarsest, interpolation per level), and the initial-iterate
+    # broadcasts of each run_cycles call (level-0 C-points, row 0 of levels 2..L-1)
+    launches_per_cycle = 3 + 2 * (L - 2) + 1 + (L - 2) + 1 + (L - 2)
     line = {
         "metric": "fine cell-updates/s", "value": value, "unit": "cell-updates/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -593,6 +611,11 @@ def run_mgrit(args):
         "gpu_launches": launches_per_cycle * args.steps,
         "clocks": clk,
         "kernel_ms": kern,
+        "restriction_roofline": {"bound": "hbm", "kernel": "level-0 FAS residual + restriction "
+                                 "(k_restrict)", "achieved": restrict_gbs, "peak": hbm_peak,
+                                 "unit": "GB/s", "frac": restrict_gbs / hbm_peak if hbm_peak else None,
+                                 "bytes_per_launch": restrict_bytes,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"},
         "serial_gpu": {"steps": W["nt"], "seconds": serial_ms / 1e3,
                        "ms_per_step": serial_ms / W["nt"],
                        "cell_updates_per_s": W["nx"] * W["nt"] / (serial_ms / 1e3),

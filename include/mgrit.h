@@ -327,8 +327,9 @@ int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const
  *   2. slabs per CTA: the slab kernels are persistent (CTA b takes work
  *      items b, b + grid, ...); for each level-0 launch class, 1, 2, 4 or 8
  *      items per CTA;
- *   3. cluster shape: for each group whose coarsest solve can use a
- *      thread-block cluster (nx >= 512), one CTA or a cluster of 2..16 CTAs.
+ *   3. cluster shape of the coarsest solves, one policy for all instances
+ *      timed on the whole coarsest phase: the single-instance occupancy rule
+ *      K0 (nx >= 512), K0/2, 2 K0 (at most 16), or one CTA each.
  * The graphs are then rebuilt.  Synchronises `stream`. */
 int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, void *stream);
 

@@ -1480,10 +1480,11 @@ static int tune_slabs_per_cta(mgrit_batch *b, int reps, cudaStream_t s, cudaEven
 // Autotuner.  (1) For every group of instances with the same (flux, nx), time
 // the level-0 relaxation with 1x, 2x and 4x the minimal cells per thread
 // (fewer, fuller threads) and keep the fastest.  (2) Slabs per CTA of the
-// persistent slab kernel per launch class (tune_slabs_per_cta).  (3) For every
-// group whose coarsest solve can run on a cluster, time it on one CTA and on
-// each cluster size 2..16 that fits, and keep the fastest.  Then rebuild the
-// batch graphs.
+// persistent slab kernel per launch class (tune_slabs_per_cta).  (3) The
+// cluster policy of the coarsest solves, timed on the whole coarsest phase
+// (timed one group at a time, the largest clusters win, but all groups run
+// together and 16-CTA clusters cannot all be resident at once).  Then
+// rebuild the batch graphs.
 extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps,
                                     void *stream)
 {
@@ -1531,29 +1532,40 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
     }
     if (!st) st = f32 ? tune_slabs_per_cta<float>(b, reps, s, e0, e1)
                       : tune_slabs_per_cta<double>(b, reps, s, e0, e1);
-    for (auto &kv : groups) {
-        if (st) break;
-        const std::vector<int> &ids = kv.second;
-        if (b->ck[ids[0]] < 2) continue;   // below 512 cells the coarsest solve stays on one CTA
-        int best = b->ck[ids[0]];
+    // (3) The coarsest solves of all instances run together (one launch per
+    // shape class), so the cluster policy is timed on the whole phase:
+    // the single-instance occupancy rule K0, K0 / 2, 2 K0 (at most 16) and one
+    // CTA for every instance; a size that does not fit falls back to one CTA
+    if (!st) {
+        std::vector<int> rule(b->n);
+        for (int i = 0; i < b->n; ++i) rule[i] = b->ctx[i]->lc64.fn ? b->ctx[i]->lc64.K : 1;
+        int best_policy = 0;
         float best_ms = 1e30f;
-        for (int K = 1; K <= CLUSTER_MAX; K *= 2) {
-            ClusterLaunch lc;
-            if (K >= 2 && !batch_cluster_shape(kv.first.second, kv.first.first, K, &lc)) continue;
-            for (int i : ids) b->ck[i] = K;
+        for (int policy = 0; policy < 4 && !st; ++policy) {
+            for (int i = 0; i < b->n; ++i) {
+                int K = rule[i];
+                if (K >= 2) K = policy == 0 ? K : policy == 1 ? K / 2 : policy == 2 ? std::min(2 * K, CLUSTER_MAX) : 1;
+                ClusterLaunch lc;
+                b->ck[i] = (K >= 2 && batch_cluster_shape(b->ctx[i]->nx, b->ctx[i]->flux, K, &lc)) ? K : 1;
+            }
             std::vector<BLaunch> mine;
             const size_t keep = b->tables.size();
             float ms = 0.f;
-            if ((st = emit_coarse(b, mine, &ids)) == MGRIT_OK)
-                st = time_launches(b, mine, reps, s, e0, e1, &ms);
+            if ((st = emit_coarse(b, mine)) == MGRIT_OK) st = time_launches(b, mine, reps, s, e0, e1, &ms);
             drop_tables(b, keep);
-            if (st) break;
-            if (ms < best_ms) {
+            if (!st && ms < best_ms) {
                 best_ms = ms;
-                best = K;
+                best_policy = policy;
             }
         }
-        for (int i : ids) b->ck[i] = best;
+        for (int i = 0; i < b->n; ++i) {
+            int K = rule[i];
+            if (K >= 2)
+                K = best_policy == 0 ? K : best_policy == 1 ? K / 2
+                  : best_policy == 2 ? std::min(2 * K, CLUSTER_MAX) : 1;
+            ClusterLaunch lc;
+            b->ck[i] = (K >= 2 && batch_cluster_shape(b->ctx[i]->nx, b->ctx[i]->flux, K, &lc)) ? K : 1;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
