@@ -329,7 +329,9 @@ int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const
  *      items per CTA;
  *   3. cluster shape of the coarsest solves, one policy for all instances
  *      timed on the whole coarsest phase: the single-instance occupancy rule
- *      K0 (nx >= 512), K0/2, 2 K0 (at most 16), or one CTA each.
+ *      K0 (nx >= 512), K0/2, 2 K0 (at most 16), or one CTA each;
+ *   4. end to end: whole cycles with the tuned or the untuned choice of
+ *      stages 2 and 3 (one slab per CTA; the rule K0), the fastest of the four.
  * The graphs are then rebuilt.  Synchronises `stream`. */
 int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, void *stream);
 

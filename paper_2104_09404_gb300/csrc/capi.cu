@@ -1567,6 +1567,40 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
             b->ck[i] = (K >= 2 && batch_cluster_shape(b->ctx[i]->nx, b->ctx[i]->flux, K, &lc)) ? K : 1;
         }
     }
+    // (4) End to end: stages 2 and 3 were timed one launch class at a time.
+    // Whole cycles (graphs A and B) are timed for the tuned and the untuned
+    // choice of each (one slab per CTA; the single-instance cluster rule), and
+    // the fastest of the four combinations is kept.
+    if (!st) {
+        const std::map<std::tuple<int, int, int>, int> tuned_spc = b->spc;
+        const std::vector<int> tuned_ck = b->ck;
+        std::vector<int> rule_ck(b->n);
+        for (int i = 0; i < b->n; ++i) rule_ck[i] = b->ctx[i]->lc64.fn ? b->ctx[i]->lc64.K : 1;
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int combo = 0; combo < 4 && !st; ++combo) {
+            if (combo & 1) b->spc.clear(); else b->spc = tuned_spc;
+            b->ck = (combo & 2) ? rule_ck : tuned_ck;
+            if ((st = batch_build(b))) break;
+            float ms = 0.f;
+            BCK(cudaGraphLaunch(b->gA, s));   // warm-up
+            BCK(cudaGraphLaunch(b->gB, s));
+            BCK(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r) {
+                BCK(cudaGraphLaunch(b->gA, s));
+                BCK(cudaGraphLaunch(b->gB, s));
+            }
+            BCK(cudaEventRecord(e1, s));
+            BCK(cudaEventSynchronize(e1));
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = combo;
+            }
+        }
+        if (best & 1) b->spc.clear(); else b->spc = tuned_spc;
+        b->ck = (best & 2) ? rule_ck : tuned_ck;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
