@@ -21,9 +21,12 @@ struct BatchItem {
 // b + gridDim.x, ... (slabs per CTA = nitems / gridDim.x, chosen by the
 // autotuner).  Each item's first shared-memory write follows the barrier that
 // opens Slab::fluxes, so consecutive items of a CTA do not race.
-// `active` (may be null): instances whose entry is 0 have converged and skip all work
+// `active` (may be null): instances whose entry is 0 have converged and skip all work.
+// Up to 4 cells per thread the kernel is held to 64 registers (two 512-thread
+// CTAs per SM): inside the item loop ptxas otherwise takes 121 registers at 4
+// cells per thread, halving the resident CTAs of the small-nx classes.
 template <typename R, int SCHEME, int FLUX, int CPT>
-__global__ void __launch_bounds__(512) k_slab_batch(const SlabArgs<R> *__restrict__ args,
+__global__ void __launch_bounds__(512, (CPT <= 4) ? 2 : 1) k_slab_batch(const SlabArgs<R> *__restrict__ args,
                                                     const BatchItem *__restrict__ map,
                                                     const int *__restrict__ active, int nitems)
 {
