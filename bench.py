@@ -539,7 +539,7 @@ def run_mgrit(args):
         tune_s = time.perf_counter() - t0
         per_batch = bt.cycle_cell_updates()
         tuned = {}
-        for what, name in ((0, "cells_per_thread"), (3, "slabs_per_cta"), (4, "coarsest_cluster_ctas")):
+        for what, name in ((0, "cells_per_thread"), (4, "coarsest_cluster_ctas")):
             vals = [bt.query(i, what) for i in range(len(insts))]
             tuned[name] = {str(v): vals.count(v) for v in sorted(set(vals))}
         for _ in range(2):

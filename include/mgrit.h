@@ -320,27 +320,25 @@ int mgrit_batch_run_cycles(mgrit_batch *b, const double *const *u0_dev, int ncyc
 int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const *uT_dev,
                       int *status, int *iters, double *final_res, void *stream);
 
-/* Autotuner, three stages, each keeping the fastest candidate by CUDA-event
- * timing (reps >= 1 timed launches per candidate):
+/* Autotuner, each stage keeping the fastest candidate by CUDA-event timing
+ * (reps >= 1 timed launches per candidate):
  *   1. CTA shape: for each group of instances with equal (flux, nx), the
  *      level-0 relaxation with 1x, 2x and 4x the minimal cells per thread;
- *   2. slabs per CTA: the slab kernels are persistent (CTA b takes work
- *      items b, b + grid, ...); for each level-0 launch class, 1, 2, 4 or 8
- *      items per CTA;
- *   3. cluster shape of the coarsest solves, one policy for all instances
+ *   2. cluster shape of the coarsest solves, one policy for all instances
  *      timed on the whole coarsest phase: the single-instance occupancy rule
  *      K0 (nx >= 512), K0/2, 2 K0 (at most 16), or one CTA each;
- *   4. end to end: whole cycles with the tuned or the untuned choice of
- *      stages 2 and 3 (one slab per CTA; the rule K0), the fastest of the four.
- * The graphs are then rebuilt.  Synchronises `stream`. */
+ *   3. end to end: whole cycles with the policy of stage 2 and with the rule.
+ * Slabs per CTA stay at one: a persistent variant (CTAs looping over work
+ * items) was slower at every setting.  The graphs are then rebuilt.
+ * Synchronises `stream`. */
 int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, void *stream);
 
 /* Cells x Phi applications of one V-cycle of all instances. */
 double mgrit_batch_cycle_cell_updates(const mgrit_batch *b);
 
 /* what = 0: cells per thread, 1: threads per CTA, 2: levels of instance i,
- * 3: slabs per CTA of its level-0 launch class, 4: CTAs per cluster of its
- * coarsest solve (1 = one CTA); -1 for an unknown `what` or instance. */
+ * 3: slabs per CTA (always 1), 4: CTAs per cluster of its coarsest solve
+ * (1 = one CTA); -1 for an unknown `what` or instance. */
 int mgrit_batch_query(const mgrit_batch *b, int instance, int what);
 
 /* C-points of instance i after its last level-0 relaxation (as

@@ -17,32 +17,29 @@ struct BatchItem {
     int block;      // block index within the item (restriction) or 0
 };
 
-// Persistent over the `nitems` work items of the map: CTA b takes items b,
-// b + gridDim.x, ... (slabs per CTA = nitems / gridDim.x, chosen by the
-// autotuner).  Each item's first shared-memory write follows the barrier that
-// opens Slab::fluxes, so consecutive items of a CTA do not race.
-// `active` (may be null): instances whose entry is 0 have converged and skip all work.
-// Up to 4 cells per thread the kernel is held to 64 registers (two 512-thread
-// CTAs per SM): inside the item loop ptxas otherwise takes 121 registers at 4
-// cells per thread, halving the resident CTAs of the small-nx classes.
+// One CTA per work item of the block map (instance argument block, chunk,
+// instance id).  A persistent variant, CTAs looping over items with 1-8
+// slabs per CTA chosen by the autotuner, was measured slower at every
+// setting: 122 vs 91 ms per batch cycle even at one item per CTA, because
+// inside the item loop the slab code takes more registers (121 instead of
+// 64 at 4 cells per thread; out of line, the call boundary still costs 90).
+// `active` (may be null): instances whose entry is 0 have converged and skip all work
 template <typename R, int SCHEME, int FLUX, int CPT>
-__global__ void __launch_bounds__(512, (CPT <= 4) ? 2 : 1) k_slab_batch(const SlabArgs<R> *__restrict__ args,
+__global__ void __launch_bounds__(512) k_slab_batch(const SlabArgs<R> *__restrict__ args,
                                                     const BatchItem *__restrict__ map,
-                                                    const int *__restrict__ active, int nitems)
+                                                    const int *__restrict__ active)
 {
+    const BatchItem it = map[blockIdx.x];
+    if (active && !active[it.instance]) return;
+    const SlabArgs<R> a = args[it.args];
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-        const BatchItem it = map[w];
-        if (active && !active[it.instance]) continue;   // uniform over the CTA
-        const SlabArgs<R> a = args[it.args];
-        Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
-        if (a.mode == MODE_RELAX)
-            relax_chunk(S, a, it.chunk);
-        else if (a.mode == MODE_INTERP)
-            interp_chunk(S, a, it.chunk);
-        else
-            seq_march(S, a);
-    }
+    Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
+    if (a.mode == MODE_RELAX)
+        relax_chunk(S, a, it.chunk);
+    else if (a.mode == MODE_INTERP)
+        interp_chunk(S, a, it.chunk);
+    else
+        seq_march(S, a);
 }
 
 // Sequential solves of many items, one thread-block cluster per item (all

@@ -862,7 +862,6 @@ struct BLaunch {
     int state_f32, un_f32;
     void *d_args;
     BatchItem *d_map;
-    int nitems;         // slab kernel: work items in the map (nblocks = ceil(nitems / slabs per CTA))
 };
 
 const BatchTable &btable()
@@ -895,7 +894,6 @@ struct mgrit_batch {
     std::vector<int> cpt;        // cells per thread of the sweep kernels, per instance
     std::vector<int> cpt64;      // cells per thread of the FP64 coarsest solve, per instance
     std::vector<int> ck;         // coarsest solve: cluster size per instance (1: one CTA)
-    std::map<std::tuple<int, int, int>, int> spc;   // slabs per CTA per launch class (default 1)
     int maxL;
     int *d_active;
     int *h_active;
@@ -979,10 +977,7 @@ struct SlabGroups {
                                   : btable().slab64[flux][cpt_index(cpt)];
             L.threads = std::get<2>(kv.first);
             L.smem = slab_smem_bytes<R>(grp.nx_max);
-            L.nitems = (int)grp.map.size();
-            const auto it = b->spc.find(kv.first);
-            const int spc = it == b->spc.end() ? 1 : it->second;
-            L.nblocks = (L.nitems + spc - 1) / spc;
+            L.nblocks = (int)grp.map.size();
             SlabArgs<R> *da;
             int st;
             if ((st = upload(b, grp.args, &da))) return st;
@@ -1187,8 +1182,7 @@ static cudaError_t enqueue_blaunch(const mgrit_batch *b, const BLaunch &L, cudaS
         const int *act = b->d_active;
         void *d_args = L.d_args;
         BatchItem *d_map = L.d_map;
-        int nitems = L.nitems;
-        void *args[] = {&d_args, &d_map, (void *)&act, &nitems};
+        void *args[] = {&d_args, &d_map, (void *)&act};
         return cudaLaunchKernel(L.fn, dim3(L.nblocks), dim3(L.threads), args, L.smem, s);
     }
     case 1:
@@ -1443,48 +1437,13 @@ static void drop_tables(mgrit_batch *b, size_t keep)
     b->tables.resize(keep);
 }
 
-// slabs per CTA of every level-0 launch class: 1, 2, 4 or 8 work items per
-// CTA of the persistent slab kernel, the fastest kept
-template <typename R>
-static int tune_slabs_per_cta(mgrit_batch *b, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
-{
-    SlabGroups<R> sg;
-    for (int i = 0; i < b->n; ++i) {
-        mgrit_ctx *c = b->ctx[i];
-        SlabArgs<R> a = relax_args<R>(c, 0);
-        sg.add(i, c->flux, b->cpt[i], a, a.nC + 1);
-    }
-    std::vector<BLaunch> mine;
-    const size_t keep = b->tables.size();
-    int st = sg.emit(b, mine);
-    auto key = sg.g.begin();
-    for (size_t li = 0; st == MGRIT_OK && li < mine.size(); ++li, ++key) {
-        BLaunch L = mine[li];
-        int best = 1;
-        float best_ms = 1e30f;
-        for (int spc = 1; spc <= 8 && spc <= L.nitems; spc *= 2) {
-            L.nblocks = (L.nitems + spc - 1) / spc;
-            float ms = 0.f;
-            if ((st = time_launches(b, std::vector<BLaunch>{L}, reps, s, e0, e1, &ms))) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = spc;
-            }
-        }
-        b->spc[key->first] = best;
-    }
-    drop_tables(b, keep);
-    return st;
-}
-
 // Autotuner.  (1) For every group of instances with the same (flux, nx), time
 // the level-0 relaxation with 1x, 2x and 4x the minimal cells per thread
-// (fewer, fuller threads) and keep the fastest.  (2) Slabs per CTA of the
-// persistent slab kernel per launch class (tune_slabs_per_cta).  (3) The
-// cluster policy of the coarsest solves, timed on the whole coarsest phase
-// (timed one group at a time, the largest clusters win, but all groups run
-// together and 16-CTA clusters cannot all be resident at once).  Then
-// rebuild the batch graphs.
+// (fewer, fuller threads) and keep the fastest.  (2) The cluster policy of the
+// coarsest solves, timed on the whole coarsest phase (timed one group at a
+// time, the largest clusters win, but all groups run together and 16-CTA
+// clusters cannot all be resident at once).  (3) Whole cycles with the tuned
+// and the rule cluster policy, the faster kept.  Then rebuild the graphs.
 extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps,
                                     void *stream)
 {
@@ -1530,9 +1489,7 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
         if (st) break;
         for (int i : ids) b->cpt[i] = best;
     }
-    if (!st) st = f32 ? tune_slabs_per_cta<float>(b, reps, s, e0, e1)
-                      : tune_slabs_per_cta<double>(b, reps, s, e0, e1);
-    // (3) The coarsest solves of all instances run together (one launch per
+    // (2) The coarsest solves of all instances run together (one launch per
     // shape class), so the cluster policy is timed on the whole phase:
     // the single-instance occupancy rule K0, K0 / 2, 2 K0 (at most 16) and one
     // CTA for every instance; a size that does not fit falls back to one CTA
@@ -1567,20 +1524,16 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
             b->ck[i] = (K >= 2 && batch_cluster_shape(b->ctx[i]->nx, b->ctx[i]->flux, K, &lc)) ? K : 1;
         }
     }
-    // (4) End to end: stages 2 and 3 were timed one launch class at a time.
-    // Whole cycles (graphs A and B) are timed for the tuned and the untuned
-    // choice of each (one slab per CTA; the single-instance cluster rule), and
-    // the fastest of the four combinations is kept.
+    // (3) End to end: stage 2 timed the coarsest phase alone; whole cycles
+    // (graphs A and B) with the tuned and the rule policy decide
     if (!st) {
-        const std::map<std::tuple<int, int, int>, int> tuned_spc = b->spc;
         const std::vector<int> tuned_ck = b->ck;
         std::vector<int> rule_ck(b->n);
         for (int i = 0; i < b->n; ++i) rule_ck[i] = b->ctx[i]->lc64.fn ? b->ctx[i]->lc64.K : 1;
         int best = 0;
         float best_ms = 1e30f;
-        for (int combo = 0; combo < 4 && !st; ++combo) {
-            if (combo & 1) b->spc.clear(); else b->spc = tuned_spc;
-            b->ck = (combo & 2) ? rule_ck : tuned_ck;
+        for (int combo = 0; combo < 2 && !st; ++combo) {
+            b->ck = combo ? rule_ck : tuned_ck;
             if ((st = batch_build(b))) break;
             float ms = 0.f;
             BCK(cudaGraphLaunch(b->gA, s));   // warm-up
@@ -1598,8 +1551,7 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
                 best = combo;
             }
         }
-        if (best & 1) b->spc.clear(); else b->spc = tuned_spc;
-        b->ck = (best & 2) ? rule_ck : tuned_ck;
+        b->ck = best ? rule_ck : tuned_ck;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1622,12 +1574,7 @@ extern "C" int mgrit_batch_query(const mgrit_batch *b, int instance, int what)
     case 0: return b->cpt[instance];
     case 1: return threads_for(b->ctx[instance]->nx, b->cpt[instance]);
     case 2: return b->ctx[instance]->L;
-    case 3: {
-        const mgrit_ctx *c = b->ctx[instance];
-        const auto it = b->spc.find(std::make_tuple(c->flux, b->cpt[instance],
-                                                    threads_for(c->nx, b->cpt[instance])));
-        return it == b->spc.end() ? 1 : it->second;
-    }
+    case 3: return 1;   // one work item (slab) per CTA
     case 4: return b->ck[instance];
     default: return -1;
     }

@@ -311,8 +311,7 @@ class Batch:
 
     def query(self, i, what):
         """Instance i: 0 cells per thread, 1 threads per CTA, 2 levels, 3 slabs
-        per CTA of its level-0 launch class, 4 CTAs per cluster of its
-        coarsest solve (1 = one CTA)."""
+        per CTA (always 1), 4 CTAs per cluster of its coarsest solve (1 = one CTA)."""
         return load().mgrit_batch_query(self._h, i, what)
 
     def close(self):

@@ -69,9 +69,9 @@ def test_autotuned_shapes_give_identical_results(M):
     b.autotune(u0s, reps=2)
     shapes = [(b.query(k, 0), b.query(k, 1)) for k in range(len(MIXED))]
     assert all(c in (1, 2, 4, 8, 16) and 32 <= t <= 512 for c, t in shapes)
-    # slabs per CTA of the persistent slab kernel, and the coarsest solve's
-    # cluster size (one CTA below 512 cells)
-    assert all(b.query(k, 3) in (1, 2, 4, 8) for k in range(len(MIXED)))
+    # one slab per CTA, and the coarsest solve's cluster size (one CTA below
+    # 512 cells)
+    assert all(b.query(k, 3) == 1 for k in range(len(MIXED)))
     ks = [b.query(k, 4) for k in range(len(MIXED))]
     assert all(K in (1, 2, 4, 8, 16) for K in ks)
     assert all(K == 1 for K, d in zip(ks, MIXED) if d["nx"] < 512)
