@@ -64,7 +64,22 @@ __device__ __forceinline__ R phys_speed(R u)
 // sum_r alpha_r p_r / sum_r alpha_r by prod_r (eps + beta_r)^2 leaves a
 // single division per reconstruction (the 1/10 of d_r cancels).
 template <typename R>
+__device__ __forceinline__ void weno5_left_nd(R a, R b, R c, R d, R e, R &num, R &den);
+
+template <typename R>
 __device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
+{
+    R num, den;
+    weno5_left_nd(a, b, c, d, e, num, den);
+    // FP32 sweeps divide with the fast intrinsic (2 ulp; den lies in
+    // [6e-24, 1e30] for |q| <= 1e3, inside its range); FP64 divides exactly
+    if (sizeof(R) == 4) return R(__fdividef(float(num), float(den)));
+    return num / den;
+}
+
+// weno5_left as the fraction num / den (the common-denominator form below)
+template <typename R>
+__device__ __forceinline__ void weno5_left_nd(R a, R b, R c, R d, R e, R &num, R &den)
 {
     const R eps = R(1e-6);
     const R k13 = R(13.0 / 12.0);
@@ -83,12 +98,8 @@ __device__ __forceinline__ R weno5_left(R a, R b, R c, R d, R e)
     const R t0 = s1 * s2;              // d_0 = 1  (x 1/10)
     const R t1 = R(6) * (s0 * s2);     // d_1 = 6
     const R t2 = R(3) * (s0 * s1);     // d_2 = 3
-    const R num = P0 * t0 + P1 * t1 + P2 * t2;
-    const R den = R(6) * (t0 + t1 + t2);
-    // FP32 sweeps divide with the fast intrinsic (2 ulp; den lies in
-    // [6e-24, 1e30] for |q| <= 1e3, inside its range); FP64 divides exactly
-    if (sizeof(R) == 4) return R(__fdividef(float(num), float(den)));
-    return num / den;
+    num = P0 * t0 + P1 * t1 + P2 * t2;
+    den = R(6) * (t0 + t1 + t2);
 }
 
 // Roe flux of a scalar law from the reconstructed states a = u^-, b = u^+
@@ -116,6 +127,42 @@ __device__ __forceinline__ R warp_max(R v)
 #pragma unroll
     for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// |x| as an ordered integer: for non-negative IEEE values integer order of
+// the bit patterns is numeric order, so the global max |f'| of the LF alpha
+// is taken on the integer pipes (the FP64 pipe is this kernel's bottleneck);
+// the result is the same value bit for bit, and a NaN (whose magnitude bits
+// exceed every finite value) propagates into alpha.
+__device__ __forceinline__ long long mag_key(double x)
+{
+    return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ int mag_key(float x) { return __float_as_int(x) & 0x7fffffff; }
+__device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k); }
+__device__ __forceinline__ float key_value(int k) { return __int_as_float(k); }
+
+// Block-wide max of magnitude keys; every thread returns it.  One barrier.
+// `red` (NWARP_MAX values of R) holds the per-warp partials.
+template <typename R, typename K>
+__device__ __forceinline__ K block_max_key(K v, R *red)
+{
+    static_assert(sizeof(K) == sizeof(R), "key and value sizes differ");
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const K u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    K *kred = reinterpret_cast<K *>(red);
+    if ((threadIdx.x & 31) == 0) MGRIT_SH(kred, threadIdx.x >> 5, NWARP_MAX) = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    K r = kred[0];
+    for (int k = 1; k < nw; ++k) {
+        const K u = MGRIT_SH(kred, k, NWARP_MAX);
+        r = u > r ? u : r;
+    }
+    return r;
 }
 
 // Block-wide max; every thread returns the result.  Contains one barrier.
@@ -184,6 +231,22 @@ struct Slab {
                              MGRIT_SH(q, s, lim()), MGRIT_SH(q, s - 1, lim()));
     }
 
+    // F_{i+1/2} = W^-(f^+) + W^+(f^-) of the split form.  With WENO5 in FP64
+    // the two fractions share one division, n1/d1 + n2/d2 = (n1 d2 + n2 d1) /
+    // (d1 d2) (each d lies in [6e-24, 1e30] for |q| <= 1e3): the FP64 pipe is
+    // this kernel's bottleneck and an IEEE division is a long sequence on it
+    __device__ __forceinline__ R split_flux(int s) const
+    {
+        if (SCHEME == SCH_FO_FE || sizeof(R) == 4) return rec_minus(qa, s) + rec_plus(qb, s);
+        const int L = lim();
+        R n1, d1, n2, d2;
+        weno5_left_nd<R>(MGRIT_SH(qa, s - 2, L), MGRIT_SH(qa, s - 1, L), MGRIT_SH(qa, s, L),
+                         MGRIT_SH(qa, s + 1, L), MGRIT_SH(qa, s + 2, L), n1, d1);
+        weno5_left_nd<R>(MGRIT_SH(qb, s + 3, L), MGRIT_SH(qb, s + 2, L), MGRIT_SH(qb, s + 1, L),
+                         MGRIT_SH(qb, s, L), MGRIT_SH(qb, s - 1, L), n2, d2);
+        return (n1 * d2 + n2 * d1) / (d1 * d2);
+    }
+
     __device__ __forceinline__ void put_flux(int i, R F) const
     {
         MGRIT_SH(qf, i + 1, nx + 1) = F;
@@ -197,20 +260,25 @@ struct Slab {
         __syncthreads();   // previous readers of qa/qb/qf/red are done
         if (numflux == NF_SPLIT) {
             R alpha = R(1);
-            if (FLUX == FLX_BURGERS) {
-                R v = R(0);
+            if (FLUX == FLX_BURGERS) {   // alpha = max_j |u_j|
+                decltype(mag_key(R(0))) v = 0;
 #pragma unroll
                 for (int c = 0; c < CPT; ++c)
-                    if (cell(c) < nx) v = fmax(v, phys_speed<FLUX>(w[c]));
-                alpha = block_max(v, red);
+                    if (cell(c) < nx) {
+                        const auto k = mag_key(w[c]);
+                        v = k > v ? k : v;
+                    }
+                alpha = key_value(block_max_key(v, red));
             }
+            // f^+/- = f(u)/2 +/- (alpha/2) u, as one multiply-add on f/2
+            const R h = R(0.5) * alpha;
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) {
-                    const R f = phys_flux<FLUX>(w[c]);
-                    put(qa, i, R(0.5) * (f + alpha * w[c]));
-                    put(qb, i, R(0.5) * (f - alpha * w[c]));
+                    const R p = R(0.5) * phys_flux<FLUX>(w[c]);
+                    put(qa, i, fma(h, w[c], p));
+                    put(qb, i, fma(-h, w[c], p));
                 }
             }
             __syncthreads();
@@ -219,7 +287,7 @@ struct Slab {
 #pragma unroll(RECON_UNROLL)
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
-                if (i < nx) put_flux(i, rec_minus(qa, i + GHOST) + rec_plus(qb, i + GHOST));
+                if (i < nx) put_flux(i, split_flux(i + GHOST));
             }
         } else if (numflux == NF_ROE) {
             // local per interface: no global speed, no reduction
@@ -244,7 +312,7 @@ struct Slab {
             __syncthreads();
             // u^-_{i+1/2} parked in qb[i], u^+_{i+1/2} in qf[i+1]; each thread
             // reads back only its own slots, then overwrites qf[i+1] with F
-            R v = R(0);
+            decltype(mag_key(R(0))) v = 0;   // max |u^-|, |u^+| (Burgers)
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
@@ -253,11 +321,13 @@ struct Slab {
                     const R up = rec_plus(qa, i + GHOST);
                     MGRIT_SH(qb, i, nx) = um;
                     MGRIT_SH(qf, i + 1, nx + 1) = up;
-                    v = fmax(v, fmax(phys_speed<FLUX>(um), phys_speed<FLUX>(up)));
+                    const auto km = mag_key(um), kp = mag_key(up);
+                    const auto k = km > kp ? km : kp;
+                    v = k > v ? k : v;
                 }
             }
             R alpha = R(1);
-            if (FLUX == FLX_BURGERS) alpha = block_max(v, red);
+            if (FLUX == FLX_BURGERS) alpha = key_value(block_max_key(v, red));
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
