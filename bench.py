@@ -520,6 +520,28 @@ def run_mgrit(args):
     b.record(stream)
     torch.cuda.synchronize()
     relax32_ms = a.elapsed_time(b) / reps
+
+    # ---- A/B: one CTA per chunk on every level (chunk_clusters = 0) --------
+    def cycle_ms(sv, n):
+        for _ in range(3):
+            sv.run_cycles(u0, 1)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(n):
+            sv.run_cycles(u0, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    chunks = {"cluster_ctas_per_level": [s.query(100 + l) for l in range(W["levels"] - 1)],
+              "ms_per_step": ms / args.steps,
+              "fp32_cluster_ctas_per_level": [s32.query(100 + l) for l in range(W["levels"] - 1)],
+              "fp32_ms_per_step": ms32 / args.steps}
+    s.set_params(chunk_clusters=0)
+    s32.set_params(chunk_clusters=0)
+    chunks["one_cta_chunks_ms_per_step"] = cycle_ms(s, args.steps)
+    chunks["one_cta_chunks_fp32_ms_per_step"] = cycle_ms(s32, args.steps)
+    s.set_params(chunk_clusters=1)
     ach32 = FLOPS_PER_CELL_UPDATE * relax0_updates / (relax32_ms / 1e3) / 1e12
     fp32 = {"value": per_cycle * args.steps / (ms32 / 1e3), "unit": "cell-updates/s",
             "ms_per_step": ms32 / args.steps, "relax_l0_ms": relax32_ms,
@@ -611,6 +633,7 @@ def run_mgrit(args):
         "gpu_launches": launches_per_cycle * args.steps,
         "clocks": clk,
         "kernel_ms": kern,
+        "chunk_clusters": chunks,
         "restriction_roofline": {"bound": "hbm", "kernel": "level-0 FAS residual + restriction "
                                  "(k_restrict)", "achieved": restrict_gbs, "peak": hbm_peak,
                                  "unit": "GB/s", "frac": restrict_gbs / hbm_peak if hbm_peak else None,

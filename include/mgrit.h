@@ -79,7 +79,7 @@ typedef struct {
     int relax;       /* MGRIT_RELAX_F / MGRIT_RELAX_FCF (default FCF) */
     int cycle;       /* MGRIT_CYCLE_V (Algorithm 1, default) or MGRIT_CYCLE_F (the
                         F-cycle of Sec. 3.2: below each level an F-cycle, then
-                        one V-cycle; batches accept V only) */
+                        one V-cycle) */
     int guess;       /* MGRIT_GUESS_EQ17 (default) / MGRIT_GUESS_INJECT */
     int numflux;     /* MGRIT_LF_SPLIT (default) / MGRIT_LF_STATE / MGRIT_ROE */
     double tol;      /* stop when the level-0 residual 2-norm < tol (default 1e-10) */
@@ -94,6 +94,11 @@ typedef struct {
                         MGRIT_LF_FE accepts 64 only. */
     int coarse;      /* MGRIT_COARSE_REDISC (default), or PSI0 / PSI1 with the
                         MGRIT_LF_FE scheme (MGRIT_EINVAL otherwise) */
+    int chunk_clusters; /* 1 (default): the relaxation / interpolation chunks of
+                        a level whose chunks alone would leave SMs idle run
+                        on thread-block clusters (mgrit_query 100 + l);
+                        0: one CTA per chunk wherever a slice fits one CTA.
+                        FP64 slices beyond one CTA use clusters either way. */
 } mgrit_params;
 
 typedef struct {
@@ -113,9 +118,11 @@ void mgrit_default_params(mgrit_params *p);
  * Create a solver for nx cells, nt fine steps, coarsening factor m and
  * `levels` time levels (level l has nt/m^l steps).  Requires m >= 2,
  * levels >= 2, nt divisible by m^(levels-1), nx >= 5 (WENO5) or nx >= 3
- * (first order, classical Lax-Friedrichs), and nx within the single-CTA slab limit of the build
- * (MGRIT_EINVAL otherwise).  Device memory is allocated on the current
- * device at the first solve.  Sec. 3.1 (C/F splitting, time chunks of m
+ * (first order, classical Lax-Friedrichs), and nx <= 16384 (MGRIT_EINVAL
+ * otherwise).  One CTA holds a slice of up to 8192 cells in FP64 and 16384 in
+ * FP32; wider FP64 slices (WENO5 and first order) run every chunk on a
+ * thread-block cluster, and the classical Lax-Friedrichs scheme stops at
+ * 8192.  Device memory is allocated on the current device at the first solve.  Sec. 3.1 (C/F splitting, time chunks of m
  * steps); Eq. (monolithicSystem) for nt and the time grid.
  */
 int mgrit_create(mgrit_ctx **out, int nx, int nt, int m, int levels, int scheme, int flux);
@@ -218,7 +225,11 @@ int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numfl
  * what = 0: cells per thread of the slab kernel; 1: threads per CTA;
  * 2: CTAs per thread-block cluster used for sequential stepping (the
  * coarsest solve and mgrit_serial_step; 1 = a single CTA), known after the
- * first call that allocates (0 before).  -1 for an unknown `what`. */
+ * first call that allocates (0 before); 100 + l (0 <= l <= levels-2): CTAs
+ * per cluster of each relaxation / interpolation chunk of level l (1 = one
+ * CTA per chunk; clusters are used where a level's chunks alone leave SMs
+ * idle, and for FP64 slices beyond one CTA), 0 before the first allocating
+ * call.  -1 for an unknown `what`. */
 int mgrit_query(const mgrit_ctx *ctx, int what);
 
 /* Cells x Phi applications of one cycle (V or F, for throughput figures). */
@@ -288,9 +299,12 @@ int mgrit_adjoint_query(const mgrit_ctx *ctx, int what);
  * Batches: many independent problems advanced together (the paper treats
  * one problem at a time; batching is a throughput feature of this library).
  * Every instance has its own nx, nt, m, levels, flux and T (WENO5/SSPRK3
- * only); the other parameters are shared.  Each phase of the V-cycle is one
- * launch per launch class (flux x CTA shape) over the work items of all
- * instances, and a cycle is two CUDA graphs, as for one instance.
+ * only); the other parameters are shared, the cycle (V or F) included.  Each
+ * phase of a cycle is one launch per launch class (flux x CTA shape) over the
+ * work items of all instances, and a cycle is two CUDA graphs, as for one
+ * instance.  V-cycle phases align the instances by level; F-cycle phases
+ * merge each instance's own launch order (one phase per operation kind that
+ * most instances have next).
  * ------------------------------------------------------------------------ */
 typedef struct mgrit_batch mgrit_batch;
 
@@ -308,7 +322,7 @@ typedef struct {
 int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst, int n,
                        const mgrit_params *params);
 
-/* Exactly ncycles V-cycles of every instance from u0_dev[i] (host array of n
+/* Exactly ncycles cycles (V or F) of every instance from u0_dev[i] (host array of n
  * device pointers).  Asynchronous. */
 int mgrit_batch_run_cycles(mgrit_batch *b, const double *const *u0_dev, int ncycles, void *stream);
 
@@ -333,7 +347,7 @@ int mgrit_batch_solve(mgrit_batch *b, const double *const *u0_dev, double *const
  * Synchronises `stream`. */
 int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, void *stream);
 
-/* Cells x Phi applications of one V-cycle of all instances. */
+/* Cells x Phi applications of one cycle (V or F) of all instances. */
 double mgrit_batch_cycle_cell_updates(const mgrit_batch *b);
 
 /* what = 0: cells per thread, 1: threads per CTA, 2: levels of instance i,

@@ -91,6 +91,7 @@ extern "C" void mgrit_default_params(mgrit_params *p)
     p->max_iter = 64;
     p->precision = 64;
     p->coarse = MGRIT_COARSE_REDISC;
+    p->chunk_clusters = 1;
 }
 
 static int check_params(mgrit_ctx *ctx, const mgrit_params *p)
@@ -112,12 +113,14 @@ static int check_params(mgrit_ctx *ctx, const mgrit_params *p)
         return mgrit_fail(ctx, MGRIT_EINVAL, "precision must be 64 or 32");
     if (p->coarse < MGRIT_COARSE_REDISC || p->coarse > MGRIT_COARSE_PSI1)
         return mgrit_fail(ctx, MGRIT_EINVAL, "coarse must be 0, 1 or 2");
+    if (p->chunk_clusters != 0 && p->chunk_clusters != 1)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "chunk_clusters must be 0 or 1");
     if (ctx && p->coarse != MGRIT_COARSE_REDISC && ctx->scheme != MGRIT_LF_FE)
         return mgrit_fail(ctx, MGRIT_EINVAL, "matched coarse integrators need the MGRIT_LF_FE scheme");
     if (ctx && ctx->scheme == MGRIT_LF_FE && p->precision != 64)
         return mgrit_fail(ctx, MGRIT_EINVAL, "the MGRIT_LF_FE scheme runs in FP64 only");
-    if (p->precision == 64 && !ctx->ln64.slab)
-        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 single-CTA slab limit", ctx->nx);
+    if (p->precision == 64 && !ctx->ln64.slab && !ctx->cluster64)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 slab limit", ctx->nx);
     if (p->precision == 32 && !ctx->ln32.slab)
         return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP32 single-CTA slab limit", ctx->nx);
     return MGRIT_OK;
@@ -153,8 +156,11 @@ extern "C" int mgrit_create(mgrit_ctx **out, int nx, int nt, int m, int levels, 
     Launch ln64, ln32;
     const bool ok64 = choose_launch(nx, scheme, flux, 0, &ln64);
     const bool ok32 = choose_launch(nx, scheme, flux, 1, &ln32);
-    if (!ok64 && !ok32)
-        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the single-CTA slab limit", nx);
+    // FP64 slices beyond one CTA run on clusters of up to 16 CTAs with at most
+    // 1024 cells each (the limit of the cluster coarsest solve)
+    const bool cl64 = !ok64 && scheme != MGRIT_LF_FE && nx <= CLUSTER_MAX * 2 * MAX_THREADS;
+    if (!ok64 && !ok32 && !cl64)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the slab limit", nx);
 
     ctx = new (std::nothrow) mgrit_ctx;
     if (!ctx) return mgrit_fail(nullptr, MGRIT_ENOMEM, "host allocation failed");
@@ -167,8 +173,9 @@ extern "C" int mgrit_create(mgrit_ctx **out, int nx, int nt, int m, int levels, 
     ctx->flux = flux;
     ctx->ln64 = ln64;
     ctx->ln32 = ln32;
+    ctx->cluster64 = cl64;
     mgrit_default_params(&ctx->p);
-    if (!ok64) ctx->p.precision = 32;   // only FP32 sweeps fit in one CTA
+    if (!ok64 && !cl64) ctx->p.precision = 32;   // only FP32 sweeps fit
     long long n = nt;
     for (int l = 0; l < levels; ++l) {
         ctx->nt_l[l] = (int)n;
@@ -213,18 +220,26 @@ static void free_workspaces(mgrit_ctx *ctx)
     ctx->alloc = ctx->prepared = ctx->have_state = false;
 }
 
+static int choose_levels(mgrit_ctx *ctx);
+
 extern "C" int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p)
 {
     if (!ctx || !p) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
     int st = check_params(ctx, p);
     if (st) return st;
+    // the captured graphs hold every parameter but the stopping rules
     const bool same_graph = ctx->p.T == p->T && ctx->p.L == p->L && ctx->p.relax == p->relax &&
-                            ctx->p.guess == p->guess && ctx->p.numflux == p->numflux &&
-                            ctx->p.precision == p->precision;
+                            ctx->p.cycle == p->cycle && ctx->p.guess == p->guess &&
+                            ctx->p.numflux == p->numflux && ctx->p.precision == p->precision &&
+                            ctx->p.coarse == p->coarse &&
+                            ctx->p.chunk_clusters == p->chunk_clusters;
+    const bool rechoose = ctx->alloc && ctx->p.chunk_clusters != p->chunk_clusters;
     if (ctx->alloc && (p->precision == 32) != (ctx->f32 != 0)) free_workspaces(ctx);
     ctx->p = *p;
     set_level_steps(ctx);
+    if (rechoose && ctx->alloc && (st = choose_levels(ctx))) return st;
     if (!same_graph) {
+        mgrit_adj_drop_graphs(ctx);
         if (ctx->gA) cudaGraphExecDestroy(ctx->gA);
         if (ctx->gB) cudaGraphExecDestroy(ctx->gB);
         ctx->gA = ctx->gB = nullptr;
@@ -262,7 +277,7 @@ static void choose_cluster(mgrit_ctx *ctx, int f32, ClusterLaunch *lc)
         const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
         if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
             continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN))
             continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(K);
@@ -290,12 +305,85 @@ static void choose_cluster(mgrit_ctx *ctx, int f32, ClusterLaunch *lc)
     cudaGetLastError();   // clear a refused attribute or occupancy query
 }
 
-// sequential stepping in the precision of `lc`/`ln` (cluster if available)
-static cudaError_t launch_seq(const ClusterLaunch &lc, const Launch &ln, cudaStream_t s, void *a)
+// Cluster shape for the chunks of level l (relaxation: nC_l + 1 chunks,
+// interpolation: nC_l).  With a one-CTA slab available, clusters are used only
+// where the chunks alone leave SMs idle: the largest power of two K <= 16 with
+// chunks x K <= SMs and at least 256 cells per CTA (a level of 17 chunks then
+// runs on 136 CTAs instead of 17).  Without one (FP64 nx > 8192), the same
+// K if there is one, else the smallest K whose blocks fit (at most 2048 cells
+// per CTA): many chunks fill the SMs anyway, and fewer CTAs per chunk means
+// less exchange.  Each candidate must be co-schedulable.
+static void choose_level_cluster(const mgrit_ctx *ctx, int f32, int l, ClusterLaunch *lc)
 {
-    if (!lc.fn) return ln.slab ? launch1(ln.slab, 1, ln, s, a) : cudaErrorInvalidConfiguration;
+    memset(lc, 0, sizeof *lc);
+    if (ctx->scheme == MGRIT_LF_FE || l > ctx->L - 2) return;
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    if (ln.slab && !ctx->p.chunk_clusters) return;
+    const int nx = ctx->nx, items = ctx->nC_l[l] + 1;
+    ClusterLaunch fill, any;   // largest K that fills the SMs; smallest K that fits
+    memset(&fill, 0, sizeof fill);
+    memset(&any, 0, sizeof any);
+    for (int K = CLUSTER_MAX; K >= 2; K /= 2) {
+        const int nmax = (nx + K - 1) / K;
+        if (nmax > 4 * MAX_THREADS) break;   // smaller K would not fit either
+        const bool fills = (long long)items * K <= ctx->nsm;
+        if (ln.slab && (!fills || nmax < 256)) continue;
+        const int cpt = nmax <= MAX_THREADS ? 1 : nmax <= 2 * MAX_THREADS ? 2 : 4;
+        const int ci = cpt == 1 ? 0 : cpt == 2 ? 1 : 2;
+        const void *fn = f32 ? table().relc32[ctx->scheme][ctx->flux][ci]
+                             : table().relc64[ctx->scheme][ctx->flux][ci];
+        const size_t smem = f32 ? cluster_smem_bytes<float>(nx, K) : cluster_smem_bytes<double>(nx, K);
+        const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+        if (!fn) continue;
+        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+            continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN))
+            continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(K);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = K;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const ClusterLaunch c{fn, K, cpt, threads, smem};
+        if (fills && !fill.fn) fill = c;
+        any = c;
+    }
+    cudaGetLastError();   // clear a refused attribute or occupancy query
+    *lc = fill.fn ? fill : ln.slab ? ClusterLaunch{} : any;
+}
+
+// the chunk launch shapes of every level below the coarsest, in the
+// allocated precision and in FP64 (mgrit_residual's operator)
+static int choose_levels(mgrit_ctx *ctx)
+{
+    for (int l = 0; l < ctx->L - 1; ++l) {
+        choose_level_cluster(ctx, 0, l, &ctx->lr64[l]);
+        if (ctx->f32) choose_level_cluster(ctx, 1, l, &ctx->lr32[l]);
+        else memset(&ctx->lr32[l], 0, sizeof ctx->lr32[l]);
+        const bool ok = ctx->f32 ? (ctx->ln32.slab || ctx->lr32[l].fn) : (ctx->ln64.slab || ctx->lr64[l].fn);
+        if (!ok)
+            return mgrit_fail(ctx, MGRIT_EINVAL, "no slab or cluster shape fits nx = %d at level %d",
+                              ctx->nx, l);
+    }
+    return MGRIT_OK;
+}
+
+// `clusters` clusters of lc.K CTAs
+static cudaError_t launch_clusters(const ClusterLaunch &lc, int clusters, cudaStream_t s, void *a)
+{
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(lc.K);
+    cfg.gridDim = dim3((unsigned)clusters * (unsigned)lc.K);
     cfg.blockDim = dim3(lc.threads);
     cfg.dynamicSmemBytes = lc.smem;
     cfg.stream = s;
@@ -308,6 +396,22 @@ static cudaError_t launch_seq(const ClusterLaunch &lc, const Launch &ln, cudaStr
     cfg.numAttrs = 1;
     void *args[] = {a};
     return cudaLaunchKernelExC(&cfg, lc.fn, args);
+}
+
+// `chunks` relaxation or interpolation chunks: one cluster each, else one CTA each
+static cudaError_t launch_chunks(const ClusterLaunch &lc, const Launch &ln, int chunks,
+                                 cudaStream_t s, void *a)
+{
+    if (chunks <= 0) return cudaSuccess;
+    if (lc.fn) return launch_clusters(lc, chunks, s, a);
+    return ln.slab ? launch1(ln.slab, chunks, ln, s, a) : cudaErrorInvalidConfiguration;
+}
+
+// sequential stepping in the precision of `lc`/`ln` (cluster if available)
+static cudaError_t launch_seq(const ClusterLaunch &lc, const Launch &ln, cudaStream_t s, void *a)
+{
+    if (!lc.fn) return ln.slab ? launch1(ln.slab, 1, ln, s, a) : cudaErrorInvalidConfiguration;
+    return launch_clusters(lc, 1, s, a);
 }
 
 int mgrit_ensure_alloc(mgrit_ctx *ctx)
@@ -341,15 +445,18 @@ int mgrit_ensure_alloc(mgrit_ctx *ctx)
     CK(cudaEventCreate(&ctx->ev1));
     if (ctx->ln64.slab)
         CK(cudaFuncSetAttribute(ctx->ln64.slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ctx->ln64.smem));
+                                SMEM_OPTIN));
     if (ctx->ln32.slab)
         CK(cudaFuncSetAttribute(ctx->ln32.slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ctx->ln32.smem));
+                                SMEM_OPTIN));
+    CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     choose_cluster(ctx, 0, &ctx->lc64);
     if (ctx->f32) choose_cluster(ctx, 1, &ctx->lc32);
     if (!ctx->ln64.slab && !ctx->lc64.fn)
         return mgrit_fail(ctx, MGRIT_EINVAL, "no FP64 slab or cluster fits nx = %d for the coarsest solve",
                     ctx->nx);
+    int st2;
+    if ((st2 = choose_levels(ctx))) return st2;
     ctx->alloc = true;
     return MGRIT_OK;
 }
@@ -455,16 +562,17 @@ static SlabArgs<R> interp_args(const mgrit_ctx *ctx, int l)
 }
 
 template <typename R>
-static cudaError_t enqueue_relax_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln)
+static cudaError_t enqueue_relax_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln,
+                                   const ClusterLaunch &lc)
 {
     SlabArgs<R> a = relax_args<R>(ctx, l);
-    return launch1(ln.slab, a.nC + 1, ln, s, &a);
+    return launch_chunks(lc, ln, a.nC + 1, s, &a);
 }
 
 static cudaError_t enqueue_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
 {
-    return ctx->f32 ? enqueue_relax_t<float>(ctx, l, s, ctx->ln32)
-                    : enqueue_relax_t<double>(ctx, l, s, ctx->ln64);
+    return ctx->f32 ? enqueue_relax_t<float>(ctx, l, s, ctx->ln32, ctx->lr32[l])
+                    : enqueue_relax_t<double>(ctx, l, s, ctx->ln64, ctx->lr64[l]);
 }
 
 static cudaError_t enqueue_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
@@ -486,16 +594,17 @@ static cudaError_t enqueue_coarse(mgrit_ctx *ctx, cudaStream_t s)
 }
 
 template <typename R>
-static cudaError_t enqueue_interp_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln)
+static cudaError_t enqueue_interp_t(mgrit_ctx *ctx, int l, cudaStream_t s, const Launch &ln,
+                                    const ClusterLaunch &lc)
 {
     SlabArgs<R> a = interp_args<R>(ctx, l);
-    return launch1(ln.slab, a.nC, ln, s, &a);
+    return launch_chunks(lc, ln, a.nC, s, &a);
 }
 
 static cudaError_t enqueue_interp(mgrit_ctx *ctx, int l, cudaStream_t s)
 {
-    return ctx->f32 ? enqueue_interp_t<float>(ctx, l, s, ctx->ln32)
-                    : enqueue_interp_t<double>(ctx, l, s, ctx->ln64);
+    return ctx->f32 ? enqueue_interp_t<float>(ctx, l, s, ctx->ln32, ctx->lr32[l])
+                    : enqueue_interp_t<double>(ctx, l, s, ctx->ln64, ctx->lr64[l]);
 }
 
 static cudaError_t enqueue_part_a(mgrit_ctx *ctx, cudaStream_t s)
@@ -744,9 +853,10 @@ extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm
 {
     if (!ctx) return MGRIT_EINVAL;
     if (!uC_dev || !norm_out) return mgrit_fail(ctx, MGRIT_EINVAL, "NULL argument");
-    if (!ctx->ln64.slab) return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 slab limit", ctx->nx);
     int st;
     if ((st = mgrit_ensure_alloc(ctx))) return st;
+    if (!ctx->ln64.slab && !ctx->lr64[0].fn)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the FP64 slab limit", ctx->nx);
     if (!ctx->resid_rows &&
         (st = mgrit_dalloc(ctx, (void **)&ctx->resid_rows, ctx->nC_l[0] + 1, sizeof(double))))
         return st;
@@ -758,7 +868,7 @@ extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm
     a.fcf = 0;
     a.phirow = ctx->resid_rows;
     a.nrows_uC = a.nrows_phirow = a.nC + 1;
-    CK(launch1(ctx->ln64.slab, a.nC, ctx->ln64, s, &a));
+    CK(launch_chunks(ctx->lr64[0], ctx->ln64, a.nC, s, &a));
     RestrictArgs r;
     memset(&r, 0, sizeof r);
     r.newC = uC_dev;
@@ -816,7 +926,13 @@ extern "C" int mgrit_query(const mgrit_ctx *ctx, int what)
     case 0: return ln.cpt;
     case 1: return ln.threads;
     case 2: return ctx->alloc ? (lc.fn ? lc.K : 1) : 0;
-    default: return -1;
+    default:
+        if (what >= 100 && what < 100 + ctx->L - 1) {   // level what-100 relaxation / interpolation
+            if (!ctx->alloc) return 0;
+            const ClusterLaunch &lr = f32 ? ctx->lr32[what - 100] : ctx->lr64[what - 100];
+            return lr.fn ? lr.K : 1;
+        }
+        return -1;
     }
 }
 
@@ -835,12 +951,13 @@ extern "C" void mgrit_destroy(mgrit_ctx *ctx)
 // ===========================================================================
 // Batches: many independent instances (uneven nx, nt, levels, flux) advanced
 // together.  Each instance keeps its own level workspaces (an mgrit_ctx);
-// every phase of the V-cycle is one batched launch per launch class, with a
-// block map telling each CTA its instance and chunk.  Phases are ordered by
-// level depth: relaxation + restriction of depth d for every instance that
-// has a level d below its coarsest, then every coarsest solve, then the
-// interpolations from the deepest depth up.  A device-side mask lets
-// converged instances skip all work while the others continue.
+// every phase of a cycle is one batched launch per launch class, with a
+// block map telling each CTA its instance and chunk.  V-cycle phases are
+// ordered by level depth: relaxation + restriction of depth d for every
+// instance that has a level d below its coarsest, then every coarsest solve,
+// then the interpolations from the deepest depth up.  F-cycle phases merge
+// the instances' own launch orders (emit_merged_cycle).  A device-side mask
+// lets converged instances skip all work while the others continue.
 // ===========================================================================
 
 #include <algorithm>
@@ -983,22 +1100,38 @@ struct SlabGroups {
             if ((st = upload(b, grp.args, &da))) return st;
             if ((st = upload(b, grp.map, &L.d_map))) return st;
             L.d_args = da;
-            BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
             out.push_back(L);
         }
         return MGRIT_OK;
     }
 };
 
-static int emit_restrict(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
+// (instance, level) pairs of one batched phase
+typedef std::vector<std::pair<int, int>> InstLevels;
+
+static InstLevels at_depth(const mgrit_batch *b, int depth, int lo_margin, int hi_margin,
+                           const std::vector<int> *only = nullptr)
+{
+    // every instance with lo_margin <= depth <= L - hi_margin
+    InstLevels il;
+    for (int i = 0; i < b->n; ++i) {
+        if (depth < lo_margin || depth > b->ctx[i]->L - hi_margin) continue;
+        if (only && std::find(only->begin(), only->end(), i) == only->end()) continue;
+        il.push_back(std::make_pair(i, depth));
+    }
+    return il;
+}
+
+static int emit_restrict_at(mgrit_batch *b, const InstLevels &il, std::vector<BLaunch> &out)
 {
     std::map<std::pair<int, int>, std::pair<std::vector<RestrictBatchArgs>, std::vector<BatchItem>>> grp;
-    for (int i = 0; i < b->n; ++i) {
+    for (const auto &x : il) {
+        const int i = x.first, l = x.second;
         mgrit_ctx *c = b->ctx[i];
-        if (depth > c->L - 2) continue;
         RestrictBatchArgs ra;
-        ra.r = restrict_args(c, depth);
-        ra.nblocks = depth == 0 ? c->nparts : restrict_blocks(ra.r.nC, ra.r.nx);
+        ra.r = restrict_args(c, l);
+        ra.nblocks = l == 0 ? c->nparts : restrict_blocks(ra.r.nC, ra.r.nx);
         auto &e = grp[std::make_pair(ra.r.state_f32, ra.r.un_f32)];
         const int ai = (int)e.first.size();
         e.first.push_back(ra);
@@ -1021,17 +1154,38 @@ static int emit_restrict(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
     return MGRIT_OK;
 }
 
+static int emit_restrict(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
+{
+    return emit_restrict_at(b, at_depth(b, depth, 0, 2), out);
+}
+
+template <typename R>
+static int emit_relax_at(mgrit_batch *b, const InstLevels &il, std::vector<BLaunch> &out)
+{
+    SlabGroups<R> sg;
+    for (const auto &x : il) {
+        mgrit_ctx *c = b->ctx[x.first];
+        SlabArgs<R> a = relax_args<R>(c, x.second);
+        sg.add(x.first, c->flux, b->cpt[x.first], a, a.nC + 1);
+    }
+    return sg.emit(b, out);
+}
+
 template <typename R>
 static int emit_relax(mgrit_batch *b, int depth, std::vector<BLaunch> &out,
                       const std::vector<int> *only = nullptr)
 {
+    return emit_relax_at<R>(b, at_depth(b, depth, 0, 2, only), out);
+}
+
+template <typename R>
+static int emit_interp_at(mgrit_batch *b, const InstLevels &il, std::vector<BLaunch> &out)
+{
     SlabGroups<R> sg;
-    for (int i = 0; i < b->n; ++i) {
-        mgrit_ctx *c = b->ctx[i];
-        if (depth > c->L - 2) continue;
-        if (only && std::find(only->begin(), only->end(), i) == only->end()) continue;
-        SlabArgs<R> a = relax_args<R>(c, depth);
-        sg.add(i, c->flux, b->cpt[i], a, a.nC + 1);
+    for (const auto &x : il) {
+        mgrit_ctx *c = b->ctx[x.first];
+        SlabArgs<R> a = interp_args<R>(c, x.second);
+        sg.add(x.first, c->flux, b->cpt[x.first], a, a.nC);
     }
     return sg.emit(b, out);
 }
@@ -1039,14 +1193,7 @@ static int emit_relax(mgrit_batch *b, int depth, std::vector<BLaunch> &out,
 template <typename R>
 static int emit_interp(mgrit_batch *b, int depth, std::vector<BLaunch> &out)
 {
-    SlabGroups<R> sg;
-    for (int i = 0; i < b->n; ++i) {
-        mgrit_ctx *c = b->ctx[i];
-        if (depth < 1 || depth > c->L - 2) continue;
-        SlabArgs<R> a = interp_args<R>(c, depth);
-        sg.add(i, c->flux, b->cpt[i], a, a.nC);
-    }
-    return sg.emit(b, out);
+    return emit_interp_at<R>(b, at_depth(b, depth, 1, 2), out);
 }
 
 // launch shape of the batched FP64 coarsest solve of one nx on a cluster of K
@@ -1066,7 +1213,7 @@ static bool batch_cluster_shape(int nx, int flux, int K, ClusterLaunch *lc)
         cudaGetLastError();
         return false;
     }
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN)) {
         cudaGetLastError();
         return false;
     }
@@ -1141,7 +1288,7 @@ static int emit_coarse(mgrit_batch *b, std::vector<BLaunch> &out,
         if ((st = upload(b, kv.second.second, &L.d_map))) return st;
         L.d_args = da;
         if (L.un_f32 > 8) BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+        BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
         out.push_back(L);
     }
     if (!cv.empty()) {
@@ -1235,6 +1382,66 @@ static int batch_capture(mgrit_batch *b, const std::vector<BLaunch> &ls, cudaGra
     return MGRIT_OK;
 }
 
+// One operation of an instance's cycle below level 0 at level l (kind 0
+// relaxation, 1 restriction, 2 coarsest solve, 3 interpolation), in the
+// order emit_cycle launches them for a single instance
+struct BOp {
+    int kind, l;
+};
+
+static void cycle_ops(const mgrit_ctx *c, int l, bool fcycle, std::vector<BOp> &out)
+{
+    if (l == c->L - 1) {
+        out.push_back(BOp{2, l});
+        return;
+    }
+    for (int pass = 0; pass < (fcycle ? 2 : 1); ++pass) {
+        out.push_back(BOp{0, l});
+        out.push_back(BOp{1, l});
+        cycle_ops(c, l + 1, fcycle && pass == 0, out);   // F-cycle, then one V-cycle
+        out.push_back(BOp{3, l});
+    }
+}
+
+// Graph B from each instance's own launch order.  The F-cycle's order depends
+// on the instance's depth, so instances are not aligned by level: each phase
+// takes the operation kind that most instances have next (ties: the lower
+// kind) and advances every instance whose next operation is of that kind, at
+// that instance's own level.  Instances are independent, so any interleaving
+// that keeps each instance's order computes what the single-instance graphs do.
+static int emit_merged_cycle(mgrit_batch *b, bool fcycle, std::vector<BLaunch> &out)
+{
+    const bool f32 = b->p.precision == 32;
+    std::vector<std::vector<BOp>> ops(b->n);
+    for (int i = 0; i < b->n; ++i) cycle_ops(b->ctx[i], 1, fcycle, ops[i]);
+    std::vector<size_t> pos(b->n, 0);
+    for (;;) {
+        int cnt[4] = {0, 0, 0, 0};
+        for (int i = 0; i < b->n; ++i)
+            if (pos[i] < ops[i].size()) ++cnt[ops[i][pos[i]].kind];
+        int k = 0;
+        for (int q = 1; q < 4; ++q)
+            if (cnt[q] > cnt[k]) k = q;
+        if (cnt[k] == 0) return MGRIT_OK;
+        InstLevels il;
+        std::vector<int> inst;
+        for (int i = 0; i < b->n; ++i) {
+            if (pos[i] >= ops[i].size() || ops[i][pos[i]].kind != k) continue;
+            il.push_back(std::make_pair(i, ops[i][pos[i]].l));
+            inst.push_back(i);
+            ++pos[i];
+        }
+        int st;
+        switch (k) {
+        case 0: st = f32 ? emit_relax_at<float>(b, il, out) : emit_relax_at<double>(b, il, out); break;
+        case 1: st = emit_restrict_at(b, il, out); break;
+        case 2: st = emit_coarse(b, out, &inst); break;
+        default: st = f32 ? emit_interp_at<float>(b, il, out) : emit_interp_at<double>(b, il, out); break;
+        }
+        if (st) return st;
+    }
+}
+
 static int batch_build(mgrit_batch *b)
 {
     batch_free_tables(b);
@@ -1245,6 +1452,11 @@ static int batch_build(mgrit_batch *b)
     if ((st = emit_restrict(b, 0, b->A))) return st;
     if ((st = emit_norm(b, b->A))) return st;
     // graph B: deeper levels, coarsest solves, interpolation
+    if (b->p.cycle == MGRIT_CYCLE_F) {
+        if ((st = emit_merged_cycle(b, true, b->B))) return st;
+        if ((st = batch_capture(b, b->A, &b->gA))) return st;
+        return batch_capture(b, b->B, &b->gB);
+    }
     for (int d = 1; d <= b->maxL - 2; ++d) {
         if ((st = f32 ? emit_relax<float>(b, d, b->B) : emit_relax<double>(b, d, b->B))) return st;
         if ((st = emit_restrict(b, d, b->B))) return st;
@@ -1264,7 +1476,6 @@ extern "C" int mgrit_batch_create(mgrit_batch **out, const mgrit_instance *inst,
     *out = nullptr;
     mgrit_params p;
     if (params) p = *params; else mgrit_default_params(&p);
-    if (p.cycle != MGRIT_CYCLE_V) return bfail(nullptr, MGRIT_EINVAL, "batches run the V-cycle only");
     b = new (std::nothrow) mgrit_batch();
     if (!b) return bfail(nullptr, MGRIT_ENOMEM, "host allocation failed");
     b->n = n;

@@ -60,6 +60,15 @@ static const AdjTable &adj_table()
     return t;
 }
 
+void mgrit_adj_drop_graphs(mgrit_ctx *ctx)
+{
+    AdjWork *w = ctx->adj;
+    if (!w) return;
+    if (w->gA) cudaGraphExecDestroy(w->gA);
+    if (w->gB) cudaGraphExecDestroy(w->gB);
+    w->gA = w->gB = nullptr;
+}
+
 void mgrit_adj_free(mgrit_ctx *ctx)
 {
     AdjWork *w = ctx->adj;
@@ -137,7 +146,7 @@ static int adj_alloc(mgrit_ctx *ctx, AdjWork *w)
     w->nparts = restrict_blocks(ctx->nC_l[0], ctx->nx);
     CK(cudaMalloc((void **)&w->partials, sizeof(double) * w->nparts));
     CK(cudaMalloc((void **)&w->d_norm, sizeof(double)));
-    CK(cudaFuncSetAttribute(w->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem));
+    CK(cudaFuncSetAttribute(w->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
     return MGRIT_OK;
 }
 
@@ -160,7 +169,7 @@ static void adj_choose_cluster(const mgrit_ctx *ctx, AdjWork *w)
         const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
         if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
             continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN)) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(K);
         cfg.blockDim = dim3(threads);

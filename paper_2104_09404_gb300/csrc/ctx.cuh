@@ -12,6 +12,12 @@ namespace mgrit {
 
 constexpr int MAXLEV = 32;
 
+// Every kernel's dynamic shared-memory limit is raised to the opt-in maximum
+// (227 KB per CTA) once, not to the size one launch needs: kernel instances
+// are shared between contexts of different nx, and a later, smaller setting
+// would make an earlier context's launches fail.
+constexpr int SMEM_OPTIN = 227 * 1024;
+
 struct Launch {
     const void *slab;   // k_slab instance for (precision, scheme, flux, cells per thread); null: unsupported
     int threads;
@@ -19,9 +25,10 @@ struct Launch {
     size_t smem;
 };
 
-// sequential stepping on a thread-block cluster (coarsest solve, serial stepper)
+// stepping on thread-block clusters: the sequential chain (coarsest solve,
+// serial stepper) or one cluster per chunk (relaxation, interpolation)
 struct ClusterLaunch {
-    const void *fn;     // k_seq_cluster instance; null: single-CTA k_slab
+    const void *fn;     // k_seq_cluster / k_slab_cluster instance; null: one-CTA k_slab
     int K;              // CTAs in the cluster
     int cpt;            // cells per thread (1 or 2)
     int threads;
@@ -39,6 +46,11 @@ struct mgrit_ctx {
     double dt_l[mgrit::MAXLEV];
     mgrit::Launch ln64, ln32;
     mgrit::ClusterLaunch lc64, lc32;
+    // relaxation / interpolation of level l on clusters (fn null: one CTA per
+    // chunk), chosen when the workspaces are allocated
+    mgrit::ClusterLaunch lr64[mgrit::MAXLEV], lr32[mgrit::MAXLEV];
+    bool cluster64;      // FP64 slices only fit on clusters (nx > 8192)
+    int nsm;             // SMs of the device
     int f32;             // precision the workspaces were allocated for (1: FP32 sweeps)
     bool alloc;
     bool prepared;       // workspaces, graphs and an initial iterate exist
@@ -69,6 +81,8 @@ int mgrit_dalloc(mgrit_ctx *ctx, void **ptr, size_t rows, size_t elem);
 int mgrit_ensure_alloc(mgrit_ctx *ctx);
 // release the adjoint workspaces (no-op if none)
 void mgrit_adj_free(mgrit_ctx *ctx);
+// drop the adjoint's captured graphs (parameters changed); no-op if none
+void mgrit_adj_drop_graphs(mgrit_ctx *ctx);
 // enqueue the part of one cycle below level 0 (V- or F-cycle by ctx->p.cycle)
 // from the given level operations
 cudaError_t mgrit_emit_below_level0(mgrit_ctx *ctx, cudaError_t (*relax)(mgrit_ctx *, int, cudaStream_t),

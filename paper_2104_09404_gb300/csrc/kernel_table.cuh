@@ -1,6 +1,6 @@
 // Table of kernel instances, indexed by [scheme][flux][cells-per-thread].
 #pragma once
-#include "cluster_seq.cuh"
+#include "cluster_relax.cuh"
 
 namespace mgrit {
 
@@ -11,6 +11,8 @@ constexpr int MAX_THREADS = 512;   // matches __launch_bounds__ of k_slab
 
 constexpr int NSCHEME = 3;         // WENO5 + SSPRK3, first order + FE, classical LF + FE
 
+constexpr int NCPT_RELAXC = 3;     // k_slab_cluster: 1, 2 or 4 cells per thread
+
 // scheme 2 (classical Lax-Friedrichs + forward Euler) exists in FP64 slabs
 // only; the cluster kernels cover schemes 0 and 1
 struct KernelTable {
@@ -18,6 +20,8 @@ struct KernelTable {
     const void *slab32[NSCHEME][2][NCPT];
     const void *seqc64[2][2][2];   // k_seq_cluster, cells per thread 1 or 2
     const void *seqc32[2][2][2];
+    const void *relc64[2][2][NCPT_RELAXC];   // k_slab_cluster, cells per thread 1, 2, 4
+    const void *relc32[2][2][NCPT_RELAXC];
 };
 
 template <typename R, int S, int F>
@@ -44,6 +48,14 @@ void fill_cluster(const void *(&t)[2][2][2])
     t[S][F][1] = (const void *)&k_seq_cluster<R, S, F, 2>;
 }
 
+template <typename R, int S, int F>
+void fill_cluster_relax(const void *(&t)[2][2][NCPT_RELAXC])
+{
+    t[S][F][0] = (const void *)&k_slab_cluster<R, S, F, 1>;
+    t[S][F][1] = (const void *)&k_slab_cluster<R, S, F, 2>;
+    t[S][F][2] = (const void *)&k_slab_cluster<R, S, F, 4>;
+}
+
 // one translation unit per (precision, scheme, flux) and kind (slab or
 // cluster kernels), compiled in parallel
 void fill_f64_weno_burgers(KernelTable &t);
@@ -55,6 +67,10 @@ void fill_f32_weno_burgers(KernelTable &t);
 void fill_f32_weno_advection(KernelTable &t);
 void fill_f32_weno_cluster(KernelTable &t);
 void fill_f32_fo(KernelTable &t);
+void fill_f64_relaxc_burgers(KernelTable &t);
+void fill_f64_relaxc_advection(KernelTable &t);
+void fill_f32_relaxc_burgers(KernelTable &t);
+void fill_f32_relaxc_advection(KernelTable &t);
 
 inline void fill_all(KernelTable &t)
 {
@@ -67,6 +83,10 @@ inline void fill_all(KernelTable &t)
     fill_f32_weno_advection(t);
     fill_f32_weno_cluster(t);
     fill_f32_fo(t);
+    fill_f64_relaxc_burgers(t);
+    fill_f64_relaxc_advection(t);
+    fill_f32_relaxc_burgers(t);
+    fill_f32_relaxc_advection(t);
 }
 
 }  // namespace mgrit

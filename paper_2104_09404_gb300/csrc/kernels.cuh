@@ -54,10 +54,13 @@ struct SlabArgs {
     R psiDt;
 };
 
-template <typename R, int SCHEME, int FLUX, int CPT>
-__device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a,
-                                            const int j)
+// relax_chunk and interp_chunk take any slab type with load/store/add/step
+// and the constants kScheme and kCpt: the one-CTA Slab, or a slab spread over
+// a thread-block cluster (cluster_relax.cuh)
+template <typename SL, typename R>
+__device__ __forceinline__ void relax_chunk(SL &S, const SlabArgs<R> &a, const int j)
 {
+    constexpr int SCHEME = SL::kScheme, CPT = SL::kCpt;
     // CTA j = 0..nC.  FCF: new C_j = (Phi_l + g) applied m times from the old
     // C_{j-1} (F- then C-relaxation of chunk j-1); F: C_j kept.  Then the
     // F-relaxation of chunk j from the new C_j.  Chunks are independent
@@ -92,10 +95,10 @@ __device__ __forceinline__ void relax_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const
     S.store(u, rowp(a.phirow, j + 1, nx, a.nrows_phirow));
 }
 
-template <typename R, int SCHEME, int FLUX, int CPT>
-__device__ __forceinline__ void interp_chunk(Slab<R, SCHEME, FLUX, CPT> &S, const SlabArgs<R> &a,
-                                             const int j)
+template <typename SL, typename R>
+__device__ __forceinline__ void interp_chunk(SL &S, const SlabArgs<R> &a, const int j)
 {
+    constexpr int CPT = SL::kCpt;
     // Eq. (interpolation): u_l^{mj} = u_{l+1}^j, u_l^{mj+r} = Phi_l(u_l^{mj+r-1}) + g_l^{mj+r}
     const int nx = a.nx, m = a.m;
     R u[CPT];

@@ -93,7 +93,9 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     double *rows = scratch;
     double *partials = scratch + ROWS_MAX;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaFuncSetAttribute(slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    // the opt-in maximum, not this launch's size: the kernel instance is shared
+    // with solver contexts whose slices may be wider
+    if (cudaFuncSetAttribute(slab, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
         cudaSuccess)
         return MGRIT_ECUDA;
 

@@ -193,6 +193,7 @@ struct Slab {
     // (psiOrder 0, Eq. coarseLFord0) or first order (1, Eq. coarseLFord1)
     int psiM, psiOrder;
     R psiDt;
+    static constexpr int kScheme = SCHEME, kCpt = CPT;
 
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
         : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))

@@ -30,7 +30,7 @@ class mgrit_params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_double), ("L", ctypes.c_double), ("relax", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("guess", ctypes.c_int), ("numflux", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("coarse", ctypes.c_int)]
+                ("coarse", ctypes.c_int), ("chunk_clusters", ctypes.c_int)]
 
 
 class mgrit_stats(ctypes.Structure):
@@ -193,7 +193,9 @@ class Solver:
 
     def query(self, what):
         """0: cells per thread, 1: threads per CTA, 2: cluster size of the
-        sequential stepper (0 before the first allocating call)."""
+        sequential stepper, 100 + l: cluster size of the level-l relaxation
+        and interpolation chunks (1: one CTA per chunk; 0 before the first
+        allocating call)."""
         return load().mgrit_query(self._h, what)
 
     # ---- discrete adjoint ----------------------------------------------

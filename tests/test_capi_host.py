@@ -50,6 +50,7 @@ def test_default_params(lib):
     lib.mgrit_default_params(ctypes.byref(p))
     assert (p.T, p.L, p.relax, p.cycle, p.guess, p.numflux) == (1.0, 1.0, 1, 0, 0, 0)
     assert p.tol == 1e-10 and p.max_iter == 64 and p.precision == 64 and p.coarse == 0
+    assert p.chunk_clusters == 1
 
 
 @pytest.mark.parametrize("args,frag", [
@@ -82,7 +83,8 @@ def test_create_set_params_destroy_without_gpu(lib):
     assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK
     for field, bad in (("relax", 3), ("cycle", 2), ("guess", 2), ("numflux", 5), ("coarse", 3),
                        ("coarse", 1),
-                       ("tol", -1.0), ("max_iter", 1000), ("precision", 16), ("T", 0.0)):
+                       ("tol", -1.0), ("max_iter", 1000), ("precision", 16), ("T", 0.0),
+                       ("chunk_clusters", 2)):
         q = M.mgrit_params.from_buffer_copy(p)
         setattr(q, field, bad)
         assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field
@@ -152,3 +154,23 @@ def test_lf_scheme_host_checks_without_gpu(lib):
     assert lib.mgrit_adjoint_query(h, 0) == 0
     lib.mgrit_destroy(h)
     assert lib.mgrit_create(ctypes.byref(h), 2, 64, 2, 2, M.LF_FE, M.BURGERS) == M.EINVAL
+
+
+def test_slice_width_limits_without_gpu(lib):
+    # one CTA holds 8192 FP64 or 16384 FP32 cells; wider FP64 slices run
+    # every chunk on a thread-block cluster (up to 16 CTAs x 1024 cells),
+    # except under the classical LF scheme, which has one-CTA kernels only
+    from paper_2104_09404_gb300 import mgrit as M
+    h = ctypes.c_void_p()
+    p = M.mgrit_params()
+    for nx in (8193, 16384):
+        assert lib.mgrit_create(ctypes.byref(h), nx, 64, 2, 2, M.WENO5_SSPRK3, M.BURGERS) == M.OK
+        lib.mgrit_default_params(ctypes.byref(p))
+        assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK       # FP64 sweeps
+        p.precision = 32
+        assert lib.mgrit_set_params(h, ctypes.byref(p)) == M.OK
+        lib.mgrit_destroy(h)
+    assert lib.mgrit_create(ctypes.byref(h), 16385, 64, 2, 2, M.WENO5_SSPRK3, M.BURGERS) == M.EINVAL
+    assert lib.mgrit_create(ctypes.byref(h), 8193, 64, 2, 2, M.LF_FE, M.BURGERS) == M.EINVAL
+    assert lib.mgrit_create(ctypes.byref(h), 8192, 64, 2, 2, M.LF_FE, M.BURGERS) == M.OK
+    lib.mgrit_destroy(h)

@@ -38,8 +38,10 @@ MIXED = [
 ]
 
 
-def single_cpoints(M, d, u0, ncycles, precision):
-    s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], precision=precision)
+def single_cpoints(M, d, u0, ncycles, precision, **params):
+    # batches run one CTA per chunk; so does the reference context here
+    s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], precision=precision,
+                 chunk_clusters=0, **params)
     s.run_cycles(dev(u0), ncycles)
     torch.cuda.synchronize()
     return s.cpoints()
@@ -58,6 +60,42 @@ def test_batch_cycles_match_single_instances(M, precision):
     for k, d in enumerate(MIXED):
         ref = single_cpoints(M, d, u0s[k], 2, precision)
         assert close(b.cpoints(k), ref), k
+
+
+# deeper hierarchies, so that the instances' F-cycle launch orders differ
+F_MIXED = MIXED + [
+    dict(nx=256, nt=512, m=2, levels=5, flux=0, T=0.025),
+    dict(nx=160, nt=1024, m=4, levels=4, flux=1, T=0.05),
+]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_f_cycles_match_single_instances(M, precision):
+    # batched F-cycle phases interleave the instances' own launch orders
+    u0s = [inputs.fourier_ic(d["nx"], seed=40 + k) for k, d in enumerate(F_MIXED)]
+    b = M.Batch(F_MIXED, precision=precision, cycle=M.CYCLE_F)
+    b.run_cycles([dev(u) for u in u0s], 2)
+    torch.cuda.synchronize()
+    for k, d in enumerate(F_MIXED):
+        ref = single_cpoints(M, d, u0s[k], 2, precision, cycle=M.CYCLE_F)
+        assert close(b.cpoints(k), ref), k
+
+
+def test_batch_f_cycle_solve_matches_single_solves(M):
+    insts = [F_MIXED[0], F_MIXED[6], F_MIXED[7], MIXED[4]]
+    u0s = [inputs.fourier_ic(d["nx"], seed=50 + k) for k, d in enumerate(insts)]
+    b = M.Batch(insts, max_iter=40, cycle=M.CYCLE_F)
+    uTs, status, iters, res = b.solve([dev(u) for u in u0s])
+    for k, d in enumerate(insts):
+        s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], max_iter=40,
+                     cycle=M.CYCLE_F, chunk_clusters=0)
+        st, uT, _, stats = s.solve(dev(u0s[k]))
+        assert status[k] == st and iters[k] == stats.iters, (k, status, iters)
+        if st == M.OK:
+            assert close(uTs[k], uT), k
+    # an F-cycle does more work per cycle than a V-cycle of the same hierarchy
+    v = M.Batch(insts, max_iter=40)
+    assert b.cycle_cell_updates() > v.cycle_cell_updates()
 
 
 def test_autotuned_shapes_give_identical_results(M):
@@ -92,7 +130,8 @@ def test_batch_solve_masks_converged_instances(M):
     uTs, status, iters, res = b.solve([dev(u) for u in u0s])
     assert len(set(iters)) > 1          # genuinely different stopping cycles
     for k, d in enumerate(insts):
-        s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], max_iter=40)
+        s = M.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"], max_iter=40,
+                     chunk_clusters=0)
         st, uT, _, stats = s.solve(dev(u0s[k]))
         assert status[k] == st and iters[k] == stats.iters, (k, status, iters)
         assert close(uTs[k], uT), k

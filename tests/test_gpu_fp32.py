@@ -112,15 +112,23 @@ def test_precision_switch_on_one_context(M):
     assert errs(uC32.cpu().numpy(), ref["uC"])[0] <= MAX_REL
 
 
-def test_fp32_only_size_refuses_fp64(M):
-    # nx = 16384 fits one CTA only in FP32 (its FP64 coarsest solve runs on a
-    # thread-block cluster): FP64 sweeps are refused with a clear error
-    T = 64 * 0.3 / 16384
-    s = M.Solver(16384, 64, 8, 2, T=T, precision=32)
-    with pytest.raises(M.MGRITError):
-        s.set_params(precision=64)
-    with pytest.raises(M.MGRITError):
-        M.Solver(16384, 64, 8, 2, T=T)          # default FP64 sweeps
+def test_nx16384_runs_in_both_precisions(M):
+    # nx = 16384 fits one CTA in FP32; in FP64 every chunk runs on a
+    # thread-block cluster (here, with 17 chunks, FP32 uses clusters as well).
+    # FP64 reaches the oracle's cycle count and C-points; FP32 its bound.
+    nx, nt, m, L = 16384, 32, 2, 3
+    u0 = inputs.fourier_ic(nx, seed=5)
+    T = 0.1 * nt / (nx * np.abs(u0).max() * m ** (L - 1))
+    ref = O.mgrit(u0, nt, m, L, T)
+    assert ref["status"] == O.OK
+    s = M.Solver(nx, nt, m, L, T=T, precision=32)
+    st, _, uC32, stats32 = s.solve(dev(u0))
+    s.set_params(precision=64)
+    st64, _, uC64, stats64 = s.solve(dev(u0))
+    assert s.query(100) > 1                   # clusters in FP64
+    assert st64 == M.OK and stats64.iters == ref["iters"]
+    assert np.abs(uC64.cpu().numpy() - ref["uC"]).max() <= 1e-11 * np.abs(ref["uC"]).max()
+    assert errs(uC32.cpu().numpy(), ref["uC"])[0] <= MAX_REL
 
 
 def test_fp32_large_slab_mgrit_small_horizon(M):
