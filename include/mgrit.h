@@ -244,9 +244,12 @@ double mgrit_cycle_cell_updates(const mgrit_ctx *ctx);
  * alpha = max|f'| differentiated at its first maximising cell) is applied
  * stage by stage with the forward stage states recomputed.  Split numerical
  * flux only (MGRIT_LF_SPLIT; MGRIT_EINVAL otherwise); FP64 in every
- * precision mode; nx <= 4096 (the adjoint slab's shared memory), else
- * MGRIT_EINVAL.  Workspaces (the regenerated fine trajectory, nt x nx, and
- * the adjoint levels) are allocated on the first call.
+ * precision mode; nx <= 16384 (MGRIT_EINVAL otherwise).  One CTA holds a
+ * transposed step of up to 4096 cells; wider slices, and the chunks of levels
+ * whose chunks alone would leave SMs idle (unless chunk_clusters = 0), run on
+ * thread-block clusters of up to 16 CTAs x 1024 cells.  Workspaces (the
+ * regenerated fine trajectory, nt x nx, and the adjoint levels) are
+ * allocated on the first call.
  * ------------------------------------------------------------------------ */
 
 /* out_dev = Phi'(u_dev)^T lam_dev for one fine step (dt = T/nt).  Each
@@ -288,11 +291,13 @@ int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const double *lam
 int mgrit_adjoint(mgrit_ctx *ctx, const double *uC_dev, const double *lamT_dev, double *lam0_dev,
                   double *lamC_dev, void *stream, mgrit_stats *stats);
 
-/* Adjoint launch shape: what = 0 cells per thread, 1 threads per CTA
- * (0 when the context's nx or numerical flux has no adjoint); 2 CTAs per
- * thread-block cluster of the sequential adjoint chains (the coarsest
- * adjoint solve and mgrit_adjoint_serial; 1 = a single CTA), known after the
- * first adjoint call (0 before); -1 otherwise. */
+/* Adjoint launch shape: what = 0 cells per thread, 1 threads per CTA of
+ * the one-CTA adjoint slab (0 when the context's nx or numerical flux has
+ * none); 2 CTAs per thread-block cluster of the sequential adjoint chains
+ * (the coarsest adjoint solve and mgrit_adjoint_serial; 1 = a single CTA);
+ * 100 + l (0 <= l <= levels-2): CTAs per cluster of each adjoint chunk of
+ * level l (1 = one CTA per chunk); 2 and 100 + l are known after the first
+ * adjoint call (0 before); -1 otherwise. */
 int mgrit_adjoint_query(const mgrit_ctx *ctx, int what);
 
 /* ------------------------------------------------------------------------

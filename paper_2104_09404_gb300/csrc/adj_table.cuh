@@ -4,11 +4,12 @@
 
 namespace mgrit {
 
-constexpr int NCPT_ADJ = 4;   // 1, 2, 4, 8 cells per thread: nx <= 4096 at 512 threads
+constexpr int NCPT_ADJ = 4;   // 1, 2, 4, 8 cells per thread: one-CTA slabs up to nx = 4096
 
 struct AdjTable {
     const void *k[2][2][NCPT_ADJ];
     const void *kc[2][2][2];   // k_adjoint_cluster, cells per thread 1 or 2
+    const void *kcc[2][2][2];  // k_adjoint_cluster_chunk, cells per thread 1 or 2
 };
 
 template <int S, int F>
@@ -20,6 +21,8 @@ void fill_adj_sf(AdjTable &t)
     t.k[S][F][3] = (const void *)&k_adjoint<S, F, 8>;
     t.kc[S][F][0] = (const void *)&k_adjoint_cluster<S, F, 1>;
     t.kc[S][F][1] = (const void *)&k_adjoint_cluster<S, F, 2>;
+    t.kcc[S][F][0] = (const void *)&k_adjoint_cluster_chunk<S, F, 1>;
+    t.kcc[S][F][1] = (const void *)&k_adjoint_cluster_chunk<S, F, 2>;
 }
 
 // one translation unit per (scheme, flux) group, compiled in parallel

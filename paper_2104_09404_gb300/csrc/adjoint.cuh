@@ -99,6 +99,7 @@ struct AdjSlab {
     int *ired;
     int nx;
     R dxinv;
+    static constexpr int kCpt = CPT;
 
     __device__ __forceinline__ AdjSlab(unsigned char *smem, int nx_, R dxinv_)
         : F(smem, nx_, dxinv_, NF_SPLIT), nx(nx_), dxinv(dxinv_)
@@ -358,10 +359,13 @@ __device__ __forceinline__ const double *adj_fwd(const AdjArgs &a, long long i, 
     return rowp(a.traj, a.N - i * s, a.nx, a.nrows_traj);
 }
 
-template <int SCHEME, int FLUX, int CPT>
-__device__ __forceinline__ void adj_relax_chunk(AdjSlab<double, SCHEME, FLUX, CPT> &S, const AdjArgs &a,
-                                                const int j, double *st)
+// adj_relax_chunk and adj_interp_chunk take any adjoint slab
+// with S.F.load/store/add/step, S.vjp and the constant kCpt: the one-CTA
+// AdjSlab, or one spread over a thread-block cluster (cluster_adjoint.cuh)
+template <typename SL>
+__device__ __forceinline__ void adj_relax_chunk(SL &S, const AdjArgs &a, const int j, double *st)
 {
+    constexpr int CPT = SL::kCpt;
     // CTA j = 0..nC, as relax_chunk: FCF recomputes C_j from the old
     // C_{j-1}; then the F-relaxation of chunk j, the coarse step of the FAS
     // term from the new C_j, and the fine step into the next C-point.
@@ -393,10 +397,10 @@ __device__ __forceinline__ void adj_relax_chunk(AdjSlab<double, SCHEME, FLUX, CP
     S.F.store(v, rowp(a.phirow, j + 1, nx, a.nrows_phirow));
 }
 
-template <int SCHEME, int FLUX, int CPT>
-__device__ __forceinline__ void adj_interp_chunk(AdjSlab<double, SCHEME, FLUX, CPT> &S,
-                                                 const AdjArgs &a, const int j, double *st)
+template <typename SL>
+__device__ __forceinline__ void adj_interp_chunk(SL &S, const AdjArgs &a, const int j, double *st)
 {
+    constexpr int CPT = SL::kCpt;
     const int nx = a.nx, m = a.m;
     double v[CPT];
     S.F.load(v, rowp(a.uC, j, nx, a.nrows_uC));

@@ -36,6 +36,15 @@ struct AdjWork {
     const void *cfn;
     int cK, cthreads;
     size_t csmem, cfwd;
+    // chunks of level l (relaxation, interpolation, trajectory at level 0,
+    // the single VJP) on clusters: k_adjoint_cluster_chunk instance, null for
+    // one CTA per chunk; chosen for the chunk_clusters value in lr_cc
+    struct Shape {
+        const void *fn;
+        int K, threads;
+        size_t smem, fwd;
+    } lr[MAXLEV];
+    int lr_cc;
     double *traj;
     double *u[MAXLEV], *g[MAXLEV];
     double *newC[MAXLEV], *phirow[MAXLEV], *cstep[MAXLEV];
@@ -120,8 +129,10 @@ static int adj_check(mgrit_ctx *ctx)
         return mgrit_fail(ctx, MGRIT_EINVAL, "the adjoint differentiates the split numerical flux only");
     AdjWork probe;
     memset(&probe, 0, sizeof probe);
-    if (!adj_choose(ctx, &probe))
-        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the adjoint slab limit (4096)", ctx->nx);
+    // one CTA holds up to 4096 cells; wider slices run on clusters of up to
+    // 16 CTAs x 1024 cells
+    if (!adj_choose(ctx, &probe) && ctx->nx > CLUSTER_MAX * 1024)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "nx = %d exceeds the adjoint limit (16384)", ctx->nx);
     return MGRIT_OK;
 }
 
@@ -146,7 +157,7 @@ static int adj_alloc(mgrit_ctx *ctx, AdjWork *w)
     w->nparts = restrict_blocks(ctx->nC_l[0], ctx->nx);
     CK(cudaMalloc((void **)&w->partials, sizeof(double) * w->nparts));
     CK(cudaMalloc((void **)&w->d_norm, sizeof(double)));
-    CK(cudaFuncSetAttribute(w->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
+    if (w->fn) CK(cudaFuncSetAttribute(w->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
     return MGRIT_OK;
 }
 
@@ -196,13 +207,79 @@ static void adj_choose_cluster(const mgrit_ctx *ctx, AdjWork *w)
     cudaGetLastError();   // clear a refused attribute or occupancy query
 }
 
+// Cluster shape for the adjoint chunks of level l, by the forward rule: with a
+// one-CTA adjoint slab, the largest K in {16, 8, 4, 2} with chunks x K <= SMs
+// and 256..1024 cells per CTA, else none; without one (nx > 4096), that K if
+// it exists, else the smallest K with at most 1024 cells per CTA.
+static void adj_choose_level(const mgrit_ctx *ctx, AdjWork *w, int l)
+{
+    AdjWork::Shape fill, any;   // largest K that fills the SMs; smallest K that fits
+    memset(&fill, 0, sizeof fill);
+    memset(&any, 0, sizeof any);
+    memset(&w->lr[l], 0, sizeof w->lr[l]);
+    if (w->fn && !ctx->p.chunk_clusters) return;
+    const int nx = ctx->nx, items = ctx->nC_l[l] + 1;
+    for (int K = CLUSTER_MAX; K >= 2; K /= 2) {
+        const int nmax = (nx + K - 1) / K;
+        if (nmax > 1024) break;   // smaller K would not fit either
+        const bool fills = (long long)items * K <= ctx->nsm;
+        if (w->fn && (!fills || nmax < 256)) continue;
+        const int cpt = nmax <= 512 ? 1 : 2;
+        const void *fn = adj_table().kcc[ctx->scheme][ctx->flux][cpt - 1];
+        const size_t fwd = cluster_smem_bytes<double>(nx, K);
+        const size_t smem = fwd + cluster_adj_extra_bytes<double>(nx, K);
+        const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+        if (!fn || smem > (size_t)SMEM_OPTIN) continue;
+        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+            continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN)) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(K);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = K;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const AdjWork::Shape c{fn, K, threads, smem, fwd};
+        if (fills && !fill.fn) fill = c;
+        any = c;
+    }
+    cudaGetLastError();   // clear a refused attribute or occupancy query
+    if (fill.fn) w->lr[l] = fill;
+    else if (!w->fn) w->lr[l] = any;
+}
+
+static int adj_choose_levels(mgrit_ctx *ctx, AdjWork *w)
+{
+    for (int l = 0; l < ctx->L - 1; ++l) {
+        adj_choose_level(ctx, w, l);
+        if (!w->fn && !w->lr[l].fn)
+            return mgrit_fail(ctx, MGRIT_EINVAL, "no adjoint slab or cluster fits nx = %d", ctx->nx);
+    }
+    w->lr_cc = ctx->p.chunk_clusters;
+    return MGRIT_OK;
+}
+
 // adjoint workspaces on first use; a failed allocation leaves none behind
 static int adj_ensure(mgrit_ctx *ctx)
 {
     int st;
     if ((st = adj_check(ctx))) return st;
     if ((st = mgrit_ensure_alloc(ctx))) return st;
-    if (ctx->adj) return MGRIT_OK;
+    if (ctx->adj) {
+        // chunk shapes follow chunk_clusters (set_params dropped the graphs)
+        if (ctx->adj->lr_cc != ctx->p.chunk_clusters) return adj_choose_levels(ctx, ctx->adj);
+        return MGRIT_OK;
+    }
     AdjWork *w = new (std::nothrow) AdjWork;
     if (!w) return mgrit_fail(ctx, MGRIT_ENOMEM, "host allocation failed");
     memset(w, 0, sizeof *w);
@@ -213,6 +290,14 @@ static int adj_ensure(mgrit_ctx *ctx)
         return st;
     }
     adj_choose_cluster(ctx, w);
+    if (!w->fn && !w->cfn) {
+        mgrit_adj_free(ctx);
+        return mgrit_fail(ctx, MGRIT_EINVAL, "no adjoint cluster fits nx = %d", ctx->nx);
+    }
+    if ((st = adj_choose_levels(ctx, w))) {
+        mgrit_adj_free(ctx);
+        return st;
+    }
     return MGRIT_OK;
 }
 
@@ -245,6 +330,31 @@ static cudaError_t adj_launch(const mgrit_ctx *ctx, int grid, cudaStream_t s, Ad
     const AdjWork *w = ctx->adj;
     void *args[] = {a};
     return cudaLaunchKernel(w->fn, dim3(grid), dim3(w->threads), args, w->smem, s);
+}
+
+// `chunks` chunks of level l (ADJ_RELAX, ADJ_INTERP, ADJ_TRAJ, ADJ_VJP): one
+// cluster each if chosen, else one CTA each
+static cudaError_t adj_launch_chunks(const mgrit_ctx *ctx, int l, int chunks, cudaStream_t s, AdjArgs *a)
+{
+    const AdjWork *w = ctx->adj;
+    const AdjWork::Shape &c = w->lr[l];
+    if (chunks <= 0) return cudaSuccess;
+    if (!c.fn) return w->fn ? adj_launch(ctx, chunks, s, a) : cudaErrorInvalidConfiguration;
+    unsigned long long fwd = c.fwd;
+    void *args[] = {a, &fwd};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)chunks * (unsigned)c.K);
+    cfg.blockDim = dim3(c.threads);
+    cfg.dynamicSmemBytes = c.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c.K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, c.fn, args);
 }
 
 // a sequential chain (ADJ_SEQ, ADJ_SERIAL): one cluster if chosen, else one CTA
@@ -282,7 +392,7 @@ static cudaError_t adj_relax(mgrit_ctx *ctx, int l, cudaStream_t s)
     a.nrows_uC = a.nrows_newC = a.nrows_phirow = a.nC + 1;
     a.nrows_cstep = a.nC;
     a.nrows_g = ctx->nt_l[l] + 1;
-    return adj_launch(ctx, a.nC + 1, s, &a);
+    return adj_launch_chunks(ctx, l, a.nC + 1, s, &a);
 }
 
 static cudaError_t adj_restrict(mgrit_ctx *ctx, int l, cudaStream_t s)
@@ -327,7 +437,7 @@ static cudaError_t adj_interp(mgrit_ctx *ctx, int l, cudaStream_t s)
     a.rows = w->u[l];
     a.nrows_uC = a.nC + 1;
     a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
-    return adj_launch(ctx, a.nC, s, &a);
+    return adj_launch_chunks(ctx, l, a.nC, s, &a);
 }
 
 static cudaError_t adj_part_a(mgrit_ctx *ctx, cudaStream_t s)
@@ -373,7 +483,7 @@ extern "C" int mgrit_step_vjp(mgrit_ctx *ctx, const double *u_dev, const double 
     a.src = u_dev;
     a.uC = lam_dev;
     a.out = out_dev;
-    CK(adj_launch(ctx, 1, (cudaStream_t)stream, &a));
+    CK(adj_launch_chunks(ctx, 0, 1, (cudaStream_t)stream, &a));
     return MGRIT_OK;
 }
 
@@ -391,7 +501,7 @@ extern "C" int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const 
     a.out = lam0_dev;
     a.rows = w->cps;
     a.nrows_rows = ctx->nC_l[0];
-    CK(adj_launch_seq(ctx, (cudaStream_t)stream, &a));
+    CK(adj_launch_seq(ctx, (cudaStream_t)stream, &a));   // a cluster whenever no one-CTA slab fits
     return MGRIT_OK;
 }
 
@@ -414,7 +524,7 @@ extern "C" int mgrit_adjoint(mgrit_ctx *ctx, const double *uC_dev, const double 
     t.uC = uC_dev;
     t.rows = w->traj;
     t.nrows_uC = nC + 1;
-    CK(adj_launch(ctx, nC, s, &t));
+    CK(adj_launch_chunks(ctx, 0, nC, s, &t));
     // initial iterate: every level-0 C-point = lamT; row 0 of every u_l, g_l = lamT
     CK(launch_broadcast_row(lamT_dev, w->u[1], 0, nx, (long long)nC + 1, s));
     for (int l = 1; l < ctx->L; ++l) {
@@ -472,6 +582,12 @@ extern "C" int mgrit_adjoint_query(const mgrit_ctx *ctx, int what)
     case 0: return ok ? w.cpt : 0;
     case 1: return ok ? w.threads : 0;
     case 2: return ctx->adj ? (ctx->adj->cfn ? ctx->adj->cK : 1) : 0;
-    default: return -1;
+    default:
+        if (what >= 100 && what < 100 + ctx->L - 1) {   // level what-100 chunks
+            if (!ctx->adj) return 0;
+            const AdjWork::Shape &c = ctx->adj->lr[what - 100];
+            return c.fn ? c.K : 1;
+        }
+        return -1;
     }
 }

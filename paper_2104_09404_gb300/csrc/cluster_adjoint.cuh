@@ -349,4 +349,82 @@ __global__ void __launch_bounds__(512) k_adjoint_cluster(AdjArgs a, unsigned lon
     S.F.cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
 }
 
+// ClusterAdj with its own stage counter, in the interface adj_relax_chunk,
+// adj_interp_chunk and adj_traj_chunk expect.  The transposed step is one
+// out-of-line function, as in the one-CTA kernel: inlined at every call site
+// of the chunk functions it would multiply the compile time.
+template <int SCHEME, int FLUX, int CPT>
+struct ClusterAdjChunk {
+    static constexpr int kCpt = CPT;
+    struct Fwd {
+        ClusterSlab<double, SCHEME, FLUX, CPT> &C;
+        int &stage;
+        __device__ __forceinline__ void load(double (&u)[CPT], const double *row) const { C.load(u, row); }
+        __device__ __forceinline__ void store(const double (&u)[CPT], double *row) const { C.store(u, row); }
+        __device__ __forceinline__ void add(double (&u)[CPT], const double *row) const { C.add(u, row); }
+        __device__ __forceinline__ void step(double (&u)[CPT], double dt) { C.step(u, dt, stage); }
+    };
+    ClusterAdj<SCHEME, FLUX, CPT> &A;
+    int stage;
+    Fwd F;
+
+    __device__ __forceinline__ ClusterAdjChunk(ClusterAdj<SCHEME, FLUX, CPT> &adj)
+        : A(adj), stage(0), F{adj.F, stage} {}
+    __device__ __noinline__ void vjp(const double *__restrict__ urow, double *__restrict__ st,
+                                     double (&lam)[CPT], double dt)
+    {
+        A.vjp(urow, st, lam, dt, stage);
+    }
+};
+
+// forward fine states of chunk j from its C-point, u^{mj+r} = Phi^r(uC_j)
+// (the ADJ_TRAJ case of k_adjoint)
+template <typename SL>
+__device__ __forceinline__ void adj_traj_chunk(SL &S, const AdjArgs &a, const int j)
+{
+    double v[SL::kCpt];
+    S.F.load(v, rowp(a.uC, j, a.nx, a.nrows_uC));
+    S.F.store(v, rowp(a.rows, (long long)a.m * j, a.nx, a.nrows_traj));
+    for (int r = 1; r < a.m; ++r) {
+        S.F.step(v, a.dt);
+        S.F.store(v, rowp(a.rows, (long long)a.m * j + r, a.nx, a.nrows_traj));
+    }
+}
+
+// ADJ_RELAX / ADJ_INTERP / ADJ_TRAJ (grid chunks x K) and ADJ_VJP (one
+// cluster) with one cluster of K CTAs per chunk: cluster c = blockIdx / K
+// takes chunk c, with the one-CTA kernel's chunk logic and one scratch row per
+// chunk.  Shared memory as k_adjoint_cluster.  Every CTA of a cluster takes
+// the same branches, so all of them reach every cluster barrier.
+template <int SCHEME, int FLUX, int CPT>
+__global__ void __launch_bounds__(512) k_adjoint_cluster_chunk(AdjArgs a, unsigned long long fwd_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    ClusterAdj<SCHEME, FLUX, CPT> A(smem, a.nx, a.dxinv, (size_t)fwd_bytes);
+    ClusterAdjChunk<SCHEME, FLUX, CPT> S(A);
+    const int j = (int)(blockIdx.x / A.F.cl.num_blocks());
+    double *st = a.scratch ? a.scratch + (long long)j * a.nx : nullptr;
+    switch (a.mode) {
+    case ADJ_RELAX:
+        adj_relax_chunk(S, a, j, st);
+        break;
+    case ADJ_INTERP:
+        adj_interp_chunk(S, a, j, st);
+        break;
+    case ADJ_TRAJ:
+        adj_traj_chunk(S, a, j);
+        break;
+    case ADJ_VJP: {
+        double v[CPT];
+        S.F.load(v, a.uC);
+        S.vjp(a.src, st, v, a.dt);
+        S.F.store(v, a.out);
+        break;
+    }
+    default:
+        break;
+    }
+    A.F.cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
+}
+
 }  // namespace mgrit

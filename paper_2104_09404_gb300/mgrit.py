@@ -232,8 +232,9 @@ class Solver:
         return st, lam0, lamC, stats
 
     def adjoint_query(self, what):
-        """0: cells per thread, 1: threads per CTA of the adjoint kernels (0: unsupported);
-        2: CTAs per cluster of the sequential adjoint chains (after the first adjoint call)."""
+        """0: cells per thread, 1: threads per CTA of the one-CTA adjoint slab (0: none);
+        2: CTAs per cluster of the sequential adjoint chains; 100 + l: CTAs per cluster
+        of the adjoint chunks of level l (2 and 100 + l after the first adjoint call)."""
         return load().mgrit_adjoint_query(self._h, what)
 
     def close(self):
