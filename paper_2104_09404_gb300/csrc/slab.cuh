@@ -102,6 +102,36 @@ __device__ __forceinline__ void weno5_left_nd(R a, R b, R c, R d, R e, R &num, R
     den = R(6) * (t0 + t1 + t2);
 }
 
+// FP32: the same fraction with every multiply-add explicit, in the order of
+// the packed-pair version below (weno5_left_x2), so that an FP32
+// reconstruction gives the same bits whether it runs alone or in a pair
+template <>
+__device__ __forceinline__ void weno5_left_nd<float>(float a, float b, float c, float d, float e,
+                                                     float &num, float &den)
+{
+    const float P0 = __fmaf_rn(2.f, a, __fmaf_rn(-7.f, b, __fmul_rn(11.f, c)));
+    const float P1 = __fmaf_rn(-1.f, b, __fmaf_rn(5.f, c, __fmul_rn(2.f, d)));
+    const float P2 = __fmaf_rn(2.f, c, __fmaf_rn(5.f, d, __fmul_rn(-1.f, e)));
+    const float x0 = __fmaf_rn(-2.f, b, __fadd_rn(a, c));
+    const float y0 = __fmaf_rn(-4.f, b, __fmaf_rn(3.f, c, a));
+    const float x1 = __fmaf_rn(-2.f, c, __fadd_rn(b, d));
+    const float y1 = __fmaf_rn(-1.f, d, b);
+    const float x2 = __fmaf_rn(-2.f, d, __fadd_rn(c, e));
+    const float y2 = __fmaf_rn(-4.f, d, __fmaf_rn(3.f, c, e));
+    const float k13 = 13.f / 12.f, q = 0.25f, eps = 1e-6f;
+    float s0 = __fmaf_rn(__fmul_rn(k13, x0), x0, __fmaf_rn(__fmul_rn(q, y0), y0, eps));
+    float s1 = __fmaf_rn(__fmul_rn(k13, x1), x1, __fmaf_rn(__fmul_rn(q, y1), y1, eps));
+    float s2 = __fmaf_rn(__fmul_rn(k13, x2), x2, __fmaf_rn(__fmul_rn(q, y2), y2, eps));
+    s0 = __fmul_rn(s0, s0);
+    s1 = __fmul_rn(s1, s1);
+    s2 = __fmul_rn(s2, s2);
+    const float t0 = __fmul_rn(s1, s2);
+    const float t1 = __fmul_rn(6.f, __fmul_rn(s0, s2));
+    const float t2 = __fmul_rn(3.f, __fmul_rn(s0, s1));
+    num = __fmaf_rn(P0, t0, __fmaf_rn(P1, t1, __fmul_rn(P2, t2)));
+    den = __fmul_rn(6.f, __fadd_rn(t0, __fadd_rn(t1, t2)));
+}
+
 // Roe flux of a scalar law from the reconstructed states a = u^-, b = u^+
 // (Sec. 2.1.2, Eq. roeflux): Roe speed lam = (u^+ + u^-)/2 for Burgers, 1 for
 // advection; eigenvalues at the states lam^-/+ = f'(u^-/+); Harten-Hyman fix
@@ -178,6 +208,39 @@ __device__ __forceinline__ R block_max(R v, R *red)
     return r;
 }
 
+// Two WENO5 reconstructions at once on packed FP32 pairs: the operations of
+// weno5_left_nd<float> in the same order, each a single packed instruction
+// for both lanes (FP32 slabs are bound by instruction issue, not by the FMA
+// pipe).  Lane k reconstructs from the k-th components of a..e.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 weno5_left_x2(float2 a, float2 b, float2 c, float2 d, float2 e)
+{
+    const float2 P0 = __ffma2_rn(f2(2.f), a, __ffma2_rn(f2(-7.f), b, __fmul2_rn(f2(11.f), c)));
+    const float2 P1 = __ffma2_rn(f2(-1.f), b, __ffma2_rn(f2(5.f), c, __fmul2_rn(f2(2.f), d)));
+    const float2 P2 = __ffma2_rn(f2(2.f), c, __ffma2_rn(f2(5.f), d, __fmul2_rn(f2(-1.f), e)));
+    const float2 x0 = __ffma2_rn(f2(-2.f), b, __fadd2_rn(a, c));
+    const float2 y0 = __ffma2_rn(f2(-4.f), b, __ffma2_rn(f2(3.f), c, a));
+    const float2 x1 = __ffma2_rn(f2(-2.f), c, __fadd2_rn(b, d));
+    const float2 y1 = __ffma2_rn(f2(-1.f), d, b);
+    const float2 x2 = __ffma2_rn(f2(-2.f), d, __fadd2_rn(c, e));
+    const float2 y2 = __ffma2_rn(f2(-4.f), d, __ffma2_rn(f2(3.f), c, e));
+    const float2 k13 = f2(13.f / 12.f), q = f2(0.25f), eps = f2(1e-6f);
+    float2 s0 = __ffma2_rn(__fmul2_rn(k13, x0), x0, __ffma2_rn(__fmul2_rn(q, y0), y0, eps));
+    float2 s1 = __ffma2_rn(__fmul2_rn(k13, x1), x1, __ffma2_rn(__fmul2_rn(q, y1), y1, eps));
+    float2 s2 = __ffma2_rn(__fmul2_rn(k13, x2), x2, __ffma2_rn(__fmul2_rn(q, y2), y2, eps));
+    s0 = __fmul2_rn(s0, s0);
+    s1 = __fmul2_rn(s1, s1);
+    s2 = __fmul2_rn(s2, s2);
+    const float2 t0 = __fmul2_rn(s1, s2);                          // d_0 = 1  (x 1/10)
+    const float2 t1 = __fmul2_rn(f2(6.f), __fmul2_rn(s0, s2));     // d_1 = 6
+    const float2 t2 = __fmul2_rn(f2(3.f), __fmul2_rn(s0, s1));     // d_2 = 3
+    const float2 num = __ffma2_rn(P0, t0, __ffma2_rn(P1, t1, __fmul2_rn(P2, t2)));
+    const float2 den = __fmul2_rn(f2(6.f), __fadd2_rn(t0, __fadd2_rn(t1, t2)));
+    // the fast division as in weno5_left (den in [6e-24, 1e30] for |q| <= 1e3)
+    return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
 template <typename R, int SCHEME, int FLUX, int CPT>
 struct Slab {
     R *qa;        // nx + 6: f^+ (split form) or the stage state (state form)
@@ -248,6 +311,34 @@ struct Slab {
         return (n1 * d2 + n2 * d1) / (d1 * d2);
     }
 
+    // FP32 WENO5 split fluxes of the owned interfaces two at a time (cells
+    // c and c+1 of this thread) on packed pairs; a cell beyond nx reads slot
+    // GHOST instead (in range) and its result is dropped
+    __device__ __forceinline__ void split_fluxes_x2() const
+    {
+        const int L = lim();
+#pragma unroll 1
+        for (int c = 0; c < CPT; c += 2) {
+            const int i0 = cell(c), i1 = c + 1 < CPT ? cell(c + 1) : nx;
+            if (i0 >= nx) break;   // cells grow with c
+            const int s0 = i0 + GHOST, s1 = (i1 < nx ? i1 : 0) + GHOST;
+            const float2 m = weno5_left_x2(
+                make_float2(MGRIT_SH(qa, s0 - 2, L), MGRIT_SH(qa, s1 - 2, L)),
+                make_float2(MGRIT_SH(qa, s0 - 1, L), MGRIT_SH(qa, s1 - 1, L)),
+                make_float2(MGRIT_SH(qa, s0, L), MGRIT_SH(qa, s1, L)),
+                make_float2(MGRIT_SH(qa, s0 + 1, L), MGRIT_SH(qa, s1 + 1, L)),
+                make_float2(MGRIT_SH(qa, s0 + 2, L), MGRIT_SH(qa, s1 + 2, L)));
+            const float2 p = weno5_left_x2(
+                make_float2(MGRIT_SH(qb, s0 + 3, L), MGRIT_SH(qb, s1 + 3, L)),
+                make_float2(MGRIT_SH(qb, s0 + 2, L), MGRIT_SH(qb, s1 + 2, L)),
+                make_float2(MGRIT_SH(qb, s0 + 1, L), MGRIT_SH(qb, s1 + 1, L)),
+                make_float2(MGRIT_SH(qb, s0, L), MGRIT_SH(qb, s1, L)),
+                make_float2(MGRIT_SH(qb, s0 - 1, L), MGRIT_SH(qb, s1 - 1, L)));
+            put_flux(i0, m.x + p.x);
+            if (i1 < nx) put_flux(i1, m.y + p.y);
+        }
+    }
+
     __device__ __forceinline__ void put_flux(int i, R F) const
     {
         MGRIT_SH(qf, i + 1, nx + 1) = F;
@@ -283,12 +374,17 @@ struct Slab {
                 }
             }
             __syncthreads();
+            // (beyond 8 cells per thread the pairs' live registers spill)
+            if constexpr (sizeof(R) == 4 && SCHEME == SCH_WENO5_SSPRK3 && CPT <= 8) {
+                split_fluxes_x2();
+            } else {
             // this loop touches no register array, so FP32 slabs keep it rolled
             // (fewer live registers for 16-32 cells per thread); FP64 unrolls it
 #pragma unroll(RECON_UNROLL)
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) put_flux(i, split_flux(i + GHOST));
+            }
             }
         } else if (numflux == NF_ROE) {
             // local per interface: no global speed, no reduction

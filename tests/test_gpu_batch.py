@@ -104,6 +104,7 @@ def test_autotuned_shapes_give_identical_results(M):
     b.run_cycles(u0s, 2)
     torch.cuda.synchronize()
     before = [b.cpoints(k) for k in range(len(MIXED))]
+    ks_before = [b.query(k, 4) for k in range(len(MIXED))]
     b.autotune(u0s, reps=2)
     shapes = [(b.query(k, 0), b.query(k, 1)) for k in range(len(MIXED))]
     assert all(c in (1, 2, 4, 8, 16) and 32 <= t <= 512 for c, t in shapes)
@@ -116,9 +117,12 @@ def test_autotuned_shapes_give_identical_results(M):
     b.run_cycles(u0s, 2)
     torch.cuda.synchronize()
     for k in range(len(MIXED)):
-        # same slab arithmetic in every shape; a coarsest solve moved between
-        # one CTA and a cluster may contract multiply-adds differently
-        assert close(b.cpoints(k), before[k]), k
+        # every FP32 sweep shape gives the same bits; a coarsest solve moved
+        # between one CTA and a cluster (FP64) differs in rounding, which the
+        # FP32 copy of the coarse rows can turn into one-ulp FP32 differences
+        got, ref = b.cpoints(k), before[k]
+        rel = float((got - ref).abs().max() / ref.abs().max())
+        assert rel <= (1e-12 if ks[k] == ks_before[k] else 1e-5), (k, rel, ks_before[k], ks[k])
 
 
 def test_batch_solve_masks_converged_instances(M):
