@@ -275,26 +275,7 @@ static void choose_cluster(mgrit_ctx *ctx, int f32, ClusterLaunch *lc)
                              : table().seqc64[ctx->scheme][ctx->flux][cpt - 1];
         const size_t smem = f32 ? cluster_smem_bytes<float>(nx, K) : cluster_smem_bytes<double>(nx, K);
         const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
-        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
-            continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN))
-            continue;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(K);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = K;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        if (!cluster_fits(fn, K, threads, smem)) continue;
         lc->fn = fn;
         lc->K = K;
         lc->cpt = cpt;
@@ -302,7 +283,6 @@ static void choose_cluster(mgrit_ctx *ctx, int f32, ClusterLaunch *lc)
         lc->smem = smem;
         return;
     }
-    cudaGetLastError();   // clear a refused attribute or occupancy query
 }
 
 // Cluster shape for the chunks of level l (relaxation: nC_l + 1 chunks,
@@ -335,31 +315,11 @@ static void choose_level_cluster(const mgrit_ctx *ctx, int f32, int l, ClusterLa
         const size_t smem = f32 ? cluster_smem_bytes<float>(nx, K) : cluster_smem_bytes<double>(nx, K);
         const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
         if (!fn) continue;
-        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
-            continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN))
-            continue;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(K);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = K;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        if (!cluster_fits(fn, K, threads, smem)) continue;
         const ClusterLaunch c{fn, K, cpt, threads, smem};
         if (fills && !fill.fn) fill = c;
         any = c;
     }
-    cudaGetLastError();   // clear a refused attribute or occupancy query
     *lc = fill.fn ? fill : ln.slab ? ClusterLaunch{} : any;
 }
 
@@ -382,20 +342,8 @@ static int choose_levels(mgrit_ctx *ctx)
 // `clusters` clusters of lc.K CTAs
 static cudaError_t launch_clusters(const ClusterLaunch &lc, int clusters, cudaStream_t s, void *a)
 {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)clusters * (unsigned)lc.K);
-    cfg.blockDim = dim3(lc.threads);
-    cfg.dynamicSmemBytes = lc.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = lc.K;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
     void *args[] = {a};
-    return cudaLaunchKernelExC(&cfg, lc.fn, args);
+    return launch_in_clusters(lc.fn, lc.K, (long long)clusters * lc.K, lc.threads, lc.smem, s, args);
 }
 
 // `chunks` relaxation or interpolation chunks: one cluster each, else one CTA each
@@ -1209,30 +1157,7 @@ static bool batch_cluster_shape(int nx, int flux, int K, ClusterLaunch *lc)
     const void *fn = btable().seqc64[flux][cpt - 1];
     const size_t smem = cluster_smem_bytes<double>(nx, K);
     const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
-    if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) {
-        cudaGetLastError();
-        return false;
-    }
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN)) {
-        cudaGetLastError();
-        return false;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(K);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = K;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
-        cudaGetLastError();
-        return false;
-    }
+    if (!cluster_fits(fn, K, threads, smem)) return false;
     lc->fn = fn;
     lc->K = K;
     lc->cpt = cpt;
@@ -1346,19 +1271,7 @@ static cudaError_t enqueue_blaunch(const mgrit_batch *b, const BLaunch &L, cudaS
         void *d_args = L.d_args;
         BatchItem *d_map = L.d_map;
         void *args[] = {&d_args, &d_map, (void *)&act};
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(L.nblocks);
-        cfg.blockDim = dim3(L.threads);
-        cfg.dynamicSmemBytes = L.smem;
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = L.un_f32;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelExC(&cfg, L.fn, args);
+        return launch_in_clusters(L.fn, L.un_f32, L.nblocks, L.threads, L.smem, s, args);
     }
     }
 }

@@ -178,25 +178,7 @@ static void adj_choose_cluster(const mgrit_ctx *ctx, AdjWork *w)
         const size_t fwd = cluster_smem_bytes<double>(nx, K);
         const size_t smem = fwd + cluster_adj_extra_bytes<double>(nx, K);
         const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
-        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
-            continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN)) continue;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(K);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = K;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        if (!cluster_fits(fn, K, threads, smem)) continue;
         w->cfn = fn;
         w->cK = K;
         w->cthreads = threads;
@@ -204,7 +186,6 @@ static void adj_choose_cluster(const mgrit_ctx *ctx, AdjWork *w)
         w->cfwd = fwd;
         return;
     }
-    cudaGetLastError();   // clear a refused attribute or occupancy query
 }
 
 // Cluster shape for the adjoint chunks of level l, by the forward rule: with a
@@ -230,30 +211,11 @@ static void adj_choose_level(const mgrit_ctx *ctx, AdjWork *w, int l)
         const size_t smem = fwd + cluster_adj_extra_bytes<double>(nx, K);
         const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
         if (!fn || smem > (size_t)SMEM_OPTIN) continue;
-        if (K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
-            continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN)) continue;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(K);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = K;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        if (!cluster_fits(fn, K, threads, smem)) continue;
         const AdjWork::Shape c{fn, K, threads, smem, fwd};
         if (fills && !fill.fn) fill = c;
         any = c;
     }
-    cudaGetLastError();   // clear a refused attribute or occupancy query
     if (fill.fn) w->lr[l] = fill;
     else if (!w->fn) w->lr[l] = any;
 }
@@ -342,19 +304,7 @@ static cudaError_t adj_launch_chunks(const mgrit_ctx *ctx, int l, int chunks, cu
     if (!c.fn) return w->fn ? adj_launch(ctx, chunks, s, a) : cudaErrorInvalidConfiguration;
     unsigned long long fwd = c.fwd;
     void *args[] = {a, &fwd};
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)chunks * (unsigned)c.K);
-    cfg.blockDim = dim3(c.threads);
-    cfg.dynamicSmemBytes = c.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = c.K;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, c.fn, args);
+    return launch_in_clusters(c.fn, c.K, (long long)chunks * c.K, c.threads, c.smem, s, args);
 }
 
 // a sequential chain (ADJ_SEQ, ADJ_SERIAL): one cluster if chosen, else one CTA
@@ -364,19 +314,7 @@ static cudaError_t adj_launch_seq(const mgrit_ctx *ctx, cudaStream_t s, AdjArgs 
     if (!w->cfn) return adj_launch(ctx, 1, s, a);
     unsigned long long fwd = w->cfwd;
     void *args[] = {a, &fwd};
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(w->cK);
-    cfg.blockDim = dim3(w->cthreads);
-    cfg.dynamicSmemBytes = w->csmem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = w->cK;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, w->cfn, args);
+    return launch_in_clusters(w->cfn, w->cK, w->cK, w->cthreads, w->csmem, s, args);
 }
 
 static cudaError_t adj_relax(mgrit_ctx *ctx, int l, cudaStream_t s)

@@ -37,6 +37,54 @@ struct ClusterLaunch {
 
 struct AdjWork;   // adjoint workspaces (capi_adjoint.cu), allocated on first use
 
+// Raise fn's cluster-size (K > 8) and shared-memory limits and report whether
+// one cluster of K CTAs x `threads` with `smem` dynamic bytes can be
+// co-scheduled on the device.  A refused attribute or query leaves no error.
+inline bool cluster_fits(const void *fn, int K, int threads, size_t smem)
+{
+    if ((K > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// nblocks CTAs of fn (a multiple of K) in clusters of K; args as for cudaLaunchKernel
+inline cudaError_t launch_in_clusters(const void *fn, int K, long long nblocks, int threads, size_t smem,
+                                      cudaStream_t s, void **args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 }  // namespace mgrit
 
 struct mgrit_ctx {
