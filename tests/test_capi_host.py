@@ -175,3 +175,37 @@ def test_slice_width_limits_without_gpu(lib):
     assert lib.mgrit_create(ctypes.byref(h), 8193, 64, 2, 2, M.LF_FE, M.BURGERS) == M.EINVAL
     assert lib.mgrit_create(ctypes.byref(h), 8192, 64, 2, 2, M.LF_FE, M.BURGERS) == M.OK
     lib.mgrit_destroy(h)
+
+
+def _header_struct_fields(name):
+    # (type, field) pairs of `typedef struct { ... } name;` in include/mgrit.h,
+    # in declaration order (comments removed; "int a, b;" gives two fields)
+    src = open(os.path.join(ROOT, "include", "mgrit.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        for n in names.split(","):
+            n = n.strip()
+            m = re.match(r"(\w+)\s*\[(\d+)\]", n)
+            out.append((ctype, m.group(1), int(m.group(2))) if m else (ctype, n, 1))
+    return out
+
+
+@pytest.mark.parametrize("name", ["mgrit_params", "mgrit_stats", "mgrit_instance"])
+def test_binding_structs_match_the_header(name):
+    # the ctypes mirrors declare the header's fields in the header's order
+    # with the same C types, so the layouts (and sizes) agree
+    from paper_2104_09404_gb300 import mgrit as M
+    ctypes_of = {"double": ctypes.c_double, "int": ctypes.c_int}
+    cls = getattr(M, name)
+    want = _header_struct_fields(name)
+    got = list(cls._fields_)
+    assert [f for f, _ in got] == [n for _, n, _ in want]
+    for (fname, ftype), (ctype, _, count) in zip(got, want):
+        base = ctypes_of[ctype]
+        assert ftype == (base * count if count > 1 else base), fname
