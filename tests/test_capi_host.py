@@ -90,6 +90,9 @@ def test_create_set_params_destroy_without_gpu(lib):
         assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field
     assert lib.mgrit_query(h, 0) == 1 and lib.mgrit_query(h, 1) == 128   # 100 cells, 1 per thread
     assert lib.mgrit_query(h, 2) == 0 and lib.mgrit_query(h, 9) == -1    # nothing allocated yet
+    # chunk cluster sizes of levels 0 and 1 (3 levels): unknown before allocation
+    assert lib.mgrit_query(h, 100) == 0 and lib.mgrit_query(h, 101) == 0
+    assert lib.mgrit_query(h, 102) == -1 and lib.mgrit_query(h, 99) == -1
     # 3 levels, m = 4: (2*4 + 1) * 16 + (2*4 + 1 + 3) * 4 + 4 steps per cycle at FCF
     assert lib.mgrit_cycle_cell_updates(h) == 100 * ((2 * 4 + 1) * 16 + (2 * 4 + 1 + 3) * 4 + 4)
     # F-cycle: level 1 is visited twice (relaxation, coarsest solve, interpolation each time)
