@@ -66,6 +66,9 @@ def build(force=False, verbose=False, extra=(), debug=False):
             raise RuntimeError("nvcc failed for " + cmd[-3])
         return r.stdout + r.stderr
 
+    # the kernel-table units instantiate the templates and take longest:
+    # start them first so that the short units fill in around them
+    jobs.sort(key=lambda cmd: (not os.path.basename(cmd[-3]).startswith("table_"), cmd[-3]))
     t_start = time.time()
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
