@@ -190,6 +190,19 @@ int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void 
 int mgrit_launch_kernel(mgrit_ctx *ctx, int which, int level, int reps, void *stream);
 
 /*
+ * Measurement aid (the paper has no counterpart): the multiply-add throughput
+ * of one SIMT pipe on the current device, the roofline denominator of the
+ * arithmetic-bound sweeps.  kind = 0: FP64 fused multiply-add; 1: FP32;
+ * 2: FP32 on packed pairs (one instruction, two multiply-adds).  Launches
+ * blocks_per_sm x SMs CTAs of 256 threads, each thread running 8 independent
+ * chains of 64 x iters multiply-adds, times the launch with CUDA events on
+ * `stream` and writes the rate in flop/s (one multiply-add = 2 flops) to the
+ * host double *flops_out.  Synchronises `stream`.  MGRIT_EINVAL for
+ * kind outside 0..2, iters < 1 or blocks_per_sm outside 1..64.
+ */
+int mgrit_fma_probe(int kind, int iters, int blocks_per_sm, double *flops_out, void *stream);
+
+/*
  * Allocation-free variant of mgrit_residual (the paper has no counterpart:
  * this is a deployment convenience).  Some callers cannot call cudaMalloc:
  * code that runs while the application owns all device memory through its

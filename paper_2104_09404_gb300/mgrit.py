@@ -61,6 +61,7 @@ _SIGS = {
     "mgrit_residual": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "mgrit_launch_kernel": (_I, [_P, _I, _I, _I, _P]),
     "mgrit_residual_static": (_I, [_I, _I, _I, _I, _I, _I, _D, _D, _P, _P, _P]),
+    "mgrit_fma_probe": (_I, [_I, _I, _I, ctypes.POINTER(_D), _P]),
     "mgrit_cycle_cell_updates": (_D, [_P]),
     "mgrit_query": (_I, [_P, _I]),
     "mgrit_step_vjp": (_I, [_P, _P, _P, _P, _P]),
@@ -119,6 +120,18 @@ def _stream_handle(stream):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+FMA_FP64, FMA_FP32, FMA_FP32X2 = 0, 1, 2
+
+
+def fma_probe(kind, iters, blocks_per_sm=8, stream=None):
+    """Multiply-add throughput (flop/s) of one SIMT pipe (mgrit_fma_probe)."""
+    out = ctypes.c_double(0.0)
+    st = load().mgrit_fma_probe(kind, iters, blocks_per_sm, ctypes.byref(out), _stream_handle(stream))
+    if st != OK:
+        raise MGRITError(st, "mgrit_fma_probe failed")
+    return out.value
 
 
 class Solver:

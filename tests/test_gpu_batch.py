@@ -162,3 +162,85 @@ def test_uneven_batch_workload_runs(M):
         assert uC.shape == (d["nt"] // d["m"] + 1, d["nx"])
         # FP32 sweeps: the C-point rows hold u0 rounded to FP32
         assert torch.equal(uC[0], dev(u0s[k]).float().double())
+
+
+# ----------------------------------------------- batched solves vs the oracle ---
+# Every instance of an uneven batch must solve its own problem: the batched
+# C-points and u(T) are compared with the oracle's Algorithm 1 on that
+# instance alone (Sec. 3.2), with the same outcome and cycle count, so that
+# an instance mapped to the wrong arguments, masked at the wrong cycle or
+# relaxed with another instance's step would fail here even if the
+# single-instance path shared the mistake.
+ORACLE_MIX = [
+    dict(nx=64, nt=256, m=2, levels=3, flux=0, T=0.2),
+    dict(nx=100, nt=128, m=4, levels=2, flux=1, T=0.1),
+    dict(nx=512, nt=256, m=4, levels=2, flux=0, T=0.02),
+    dict(nx=777, nt=64, m=4, levels=3, flux=1, T=0.004),
+    dict(nx=128, nt=256, m=4, levels=2, flux=0, T=0.25),
+    dict(nx=2048, nt=128, m=2, levels=3, flux=0, T=0.004),
+    dict(nx=256, nt=512, m=2, levels=5, flux=0, T=0.025),
+    dict(nx=160, nt=1024, m=4, levels=4, flux=1, T=0.05),
+    dict(nx=1000, nt=256, m=4, levels=3, flux=1, T=0.01),
+    dict(nx=4096, nt=64, m=4, levels=2, flux=0, T=0.001),
+]
+ORACLE_SEED = 100
+
+
+def oracle_solve(d, u0, cycle):
+    import oracle as O
+    return O.mgrit(u0, d["nt"], d["m"], d["levels"], d["T"], flux=d["flux"], max_iter=40,
+                   cycle=cycle)
+
+
+def rel_max(got, ref):
+    ref = np.asarray(ref)
+    return float(np.abs(np.asarray(got) - ref).max() / np.abs(ref).max())
+
+
+def near_tol(hist, tol=1e-10):
+    return bool(np.any(np.abs(np.asarray(hist) - tol) <= 1e-3 * tol))
+
+
+@pytest.mark.parametrize("tuned", [False, True], ids=["rule", "autotuned"])
+@pytest.mark.parametrize("cycle", [0, 1], ids=["V", "F"])
+def test_batch_solve_matches_oracle_fp64(M, cycle, tuned):
+    import oracle as O
+    u0s = [inputs.fourier_ic(d["nx"], seed=ORACLE_SEED + k) for k, d in enumerate(ORACLE_MIX)]
+    du0 = [dev(u) for u in u0s]
+    b = M.Batch(ORACLE_MIX, max_iter=40, cycle=cycle)
+    if tuned:
+        b.autotune(du0, reps=2)
+    uTs, status, iters, res = b.solve(du0)
+    assert len(set(iters)) > 1   # instances stop (and are masked) at different cycles
+    for k, d in enumerate(ORACLE_MIX):
+        ref = oracle_solve(d, u0s[k], cycle)
+        assert status[k] == ref["status"] == O.OK, (k, status[k], ref["status"])
+        if not near_tol(ref["res_hist"]):
+            assert iters[k] == ref["iters"], (k, iters[k], ref["iters"])
+        # the masked instance keeps the C-points of its own final cycle
+        assert rel_max(b.cpoints(k).cpu().numpy(), ref["uC"]) <= 1e-11, k
+        assert rel_max(uTs[k].cpu().numpy(), ref["uT"]) <= 1e-11, k
+        floor = 1e-14 * np.abs(ref["uC"]).max() * np.sqrt(ref["uC"].size)
+        assert res[k] == pytest.approx(ref["res_hist"][ref["iters"]], rel=1e-8, abs=floor), k
+
+
+@pytest.mark.parametrize("tuned", [False, True], ids=["rule", "autotuned"])
+def test_batch_fp32_solve_within_bound_of_oracle(M, tuned):
+    # FP32 sweeps stop at the FP32 fixed point (or on stagnation); their
+    # result is compared with the FP64 oracle's converged solution within the
+    # stated FP32 bound: relative max-norm 1e-4, relative L1 5e-5
+    import oracle as O
+    u0s = [inputs.fourier_ic(d["nx"], seed=ORACLE_SEED + k) for k, d in enumerate(ORACLE_MIX)]
+    du0 = [dev(u) for u in u0s]
+    b = M.Batch(ORACLE_MIX, max_iter=40, precision=32)
+    if tuned:
+        b.autotune(du0, reps=2)
+    uTs, status, iters, res = b.solve(du0)
+    for k, d in enumerate(ORACLE_MIX):
+        ref = oracle_solve(d, u0s[k], 0)
+        assert status[k] == O.OK, (k, status[k])
+        got = uTs[k].cpu().numpy()
+        assert rel_max(got, ref["uT"]) <= 1e-4, k
+        assert np.abs(got - ref["uT"]).sum() / np.abs(ref["uT"]).sum() <= 5e-5, k
+        uC = b.cpoints(k).cpu().numpy()
+        assert rel_max(uC, ref["uC"]) <= 1e-4, k

@@ -312,3 +312,23 @@ def test_full_size_cycles_conserve_mass(M):
     steps = m * np.arange(uC.shape[0])
     bound = 2e-16 * nx * (steps + 1) * np.abs(u0).max() + 1e-13
     assert np.all(np.abs(uC.sum(axis=1) - u0.sum()) <= bound)
+
+
+def test_full_width_multicycle_solve_matches_oracle(M):
+    # the bench workload's width (nx = 4096, dt = 1/16384) through a
+    # hierarchy that converges: two levels (coarse CFL 0.72 for this u0),
+    # T = 0.5 past shock formation, several cycles.  Same outcome, the
+    # oracle's cycle count and residual history, and C-points and u(T) to
+    # 1e-11 (Algorithm 1; the fixed point is sequential stepping, Sec. 3.1)
+    nx, nt, m, L, T = 4096, 8192, 4, 2, 0.5
+    st, uT, uC, stats, ref, s, u0 = run_pair(M, nx, nt, m, L, T, {}, 0)
+    assert ref["status"] == O.OK and ref["iters"] >= 3
+    assert st == M.OK
+    if not near_tol(ref["res_hist"], 1e-10):
+        assert stats.iters == ref["iters"]
+    hist = np.array(stats.res_hist[: stats.iters + 1])
+    floor = 1e-14 * np.abs(ref["uC"]).max() * np.sqrt(ref["uC"].size)
+    k = min(len(hist), len(ref["res_hist"]))
+    np.testing.assert_allclose(hist[:k], ref["res_hist"][:k], rtol=1e-8, atol=floor)
+    assert relerr(uC, ref["uC"]) <= RTOL
+    assert relerr(uT, ref["uT"]) <= RTOL
