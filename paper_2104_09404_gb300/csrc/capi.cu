@@ -56,13 +56,13 @@ static const KernelTable &table()
 static bool choose_launch(int nx, int scheme, int flux, int f32, Launch *ln)
 {
     memset(ln, 0, sizeof *ln);
-    const size_t smem = f32 ? slab_smem_bytes<float>(nx) : slab_smem_bytes<double>(nx);
-    if (smem > 227 * 1024) return false;
     const int ncpt = f32 ? NCPT : NCPT64;
     for (int ci = 0; ci < ncpt; ++ci) {
         const int cpt = CPT_VALUES[ci];
         const int need = (nx + cpt - 1) / cpt;
         if (need <= MAX_THREADS) {
+            const size_t smem = f32 ? slab_smem_bytes<float>(nx, cpt) : slab_smem_bytes<double>(nx, cpt);
+            if (smem > 227 * 1024) return false;
             ln->cpt = cpt;
             ln->threads = ((need + 31) / 32) * 32;
             ln->smem = smem;
@@ -1041,7 +1041,7 @@ struct SlabGroups {
             L.fn = sizeof(R) == 4 ? btable().slab32[flux][cpt_index(cpt)]
                                   : btable().slab64[flux][cpt_index(cpt)];
             L.threads = std::get<2>(kv.first);
-            L.smem = slab_smem_bytes<R>(grp.nx_max);
+            L.smem = slab_smem_bytes<R>(grp.nx_max, cpt);
             L.nblocks = (int)grp.map.size();
             SlabArgs<R> *da;
             int st;

@@ -49,7 +49,7 @@ cudaError_t scratch_address(double **out)
     return cudaSuccess;
 }
 
-const void *select_slab(int nx, int scheme, int flux, int *threads)
+const void *select_slab(int nx, int scheme, int flux, int *threads, int *cpt)
 {
     KernelTable t;
     memset(&t, 0, sizeof t);
@@ -58,6 +58,7 @@ const void *select_slab(int nx, int scheme, int flux, int *threads)
         const int need = (nx + CPT_VALUES[ci] - 1) / CPT_VALUES[ci];
         if (need <= MAX_THREADS) {
             *threads = ((need + 31) / 32) * 32;
+            *cpt = CPT_VALUES[ci];
             return t.slab64[scheme][flux][ci];
         }
     }
@@ -80,11 +81,11 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     if (!(T > 0) || !(L > 0) || !std::isfinite(T) || !std::isfinite(L)) return MGRIT_EINVAL;
     const int nC = nt / m;
     if ((size_t)(nC + 1) * (size_t)nx > ROWS_MAX) return MGRIT_EINVAL;   // beyond the scratch
-    const size_t smem = slab_smem_bytes<double>(nx);
-    if (smem > 227 * 1024) return MGRIT_EINVAL;
-    int threads = 0;
-    const void *slab = select_slab(nx, scheme, flux, &threads);
+    int threads = 0, cpt = 0;
+    const void *slab = select_slab(nx, scheme, flux, &threads, &cpt);
     if (!slab) return MGRIT_EINVAL;
+    const size_t smem = slab_smem_bytes<double>(nx, cpt);
+    if (smem > 227 * 1024) return MGRIT_EINVAL;
     const int blocks = restrict_blocks(nC, nx);
     if ((size_t)blocks > PARTIALS_MAX) return MGRIT_EINVAL;
 

@@ -14,6 +14,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 #ifdef MGRIT_DEBUG
 #include <cstdio>
 #endif
@@ -208,44 +210,185 @@ __device__ __forceinline__ R block_max(R v, R *red)
     return r;
 }
 
-// Two WENO5 reconstructions at once on packed FP32 pairs: the operations of
-// weno5_left_nd<float> in the same order, each a single packed instruction
-// for both lanes (FP32 slabs are bound by instruction issue, not by the FMA
-// pipe).  Lane k reconstructs from the k-th components of a..e.
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+// ---------------------------------------------------------------------------
+// Windowed WENO5-JS for the split form (Sec. 2.1.1, k = 2; Sec. 2.1.2).
+//
+// The arrays hold q = f^{+/-}/2 (a power-of-two scaling, exact).  With the
+// first differences e_j = q_{j+1} - q_j, every quantity of Eqs. (C), (B) and
+// (omega) at the interface i+1/2 is a short expression in e_{i-2..i+1}:
+//   candidates   p_r = f_i + g_r / 6 (in units of f), g = 2 (5e_{i-1} - 2e_{i-2},
+//                e_{i-1} + 2e_i, 4e_i - e_{i+1}) in units of q;
+//   indicators   beta_r = (13/3) z_r^2 + y_r^2 with the second differences
+//                z = e_j - e_{j-1} of the three 3-cell windows j = i-1, i, i+1
+//                and y = (3e_{i-1} - e_{i-2}, e_{i-1} + e_i, e_{i+1} - 3e_i)
+//                (the quadratic forms B_r of the paper, scaled by q = f/2);
+//   weights      alpha_r = d_r / (eps + beta_r)^2, d = (1, 6, 3)/10,
+//                normalised over a common denominator.
+// The term Z_j = eps + (13/3) z_j^2 of window j is used by three
+// neighbouring interfaces, and e_j by four, so a thread that owns a run of
+// consecutive interfaces slides a window along them and forms each e_j and
+// Z_j once.  The right-biased reconstruction of f^- is the same expression on
+// the mirrored stencil, i.e. on (e_{i+2}, e_{i+1}, e_i, e_{i-1}) and
+// (Z_{i+2}, Z_{i+1}, Z_i), with g and y negated.
+//
+// Every operation has explicit rounding, so each e_j, Z_j and interface
+// flux is the same bit pattern whichever thread or CTA shape computes it
+// (FP32 also on packed pairs, one instruction for two lanes).
 
-__device__ __forceinline__ float2 weno5_left_x2(float2 a, float2 b, float2 c, float2 d, float2 e)
+template <typename V> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double k(double c) { return c; }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double neg(double a) { return -a; }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float k(double c) { return (float)c; }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    // the fast division (2 ulp; the denominators stay inside [1e-24, 1e30])
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+};
+template <> struct Ar<float2> {
+    static __device__ __forceinline__ float2 k(double c) { return make_float2((float)c, (float)c); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // a - b rounded once, as __fsub_rn
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, k(-1.0), a); }
+    static __device__ __forceinline__ float2 div(float2 a, float2 b)
+    {
+        return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+    }
+    static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+};
+
+// Z of a 3-cell window from its two first differences (e_j, e_{j-1})
+template <typename V>
+__device__ __forceinline__ V weno_z(V ej, V ejm)
 {
-    const float2 P0 = __ffma2_rn(f2(2.f), a, __ffma2_rn(f2(-7.f), b, __fmul2_rn(f2(11.f), c)));
-    const float2 P1 = __ffma2_rn(f2(-1.f), b, __ffma2_rn(f2(5.f), c, __fmul2_rn(f2(2.f), d)));
-    const float2 P2 = __ffma2_rn(f2(2.f), c, __ffma2_rn(f2(5.f), d, __fmul2_rn(f2(-1.f), e)));
-    const float2 x0 = __ffma2_rn(f2(-2.f), b, __fadd2_rn(a, c));
-    const float2 y0 = __ffma2_rn(f2(-4.f), b, __ffma2_rn(f2(3.f), c, a));
-    const float2 x1 = __ffma2_rn(f2(-2.f), c, __fadd2_rn(b, d));
-    const float2 y1 = __ffma2_rn(f2(-1.f), d, b);
-    const float2 x2 = __ffma2_rn(f2(-2.f), d, __fadd2_rn(c, e));
-    const float2 y2 = __ffma2_rn(f2(-4.f), d, __ffma2_rn(f2(3.f), c, e));
-    const float2 k13 = f2(13.f / 12.f), q = f2(0.25f), eps = f2(1e-6f);
-    float2 s0 = __ffma2_rn(__fmul2_rn(k13, x0), x0, __ffma2_rn(__fmul2_rn(q, y0), y0, eps));
-    float2 s1 = __ffma2_rn(__fmul2_rn(k13, x1), x1, __ffma2_rn(__fmul2_rn(q, y1), y1, eps));
-    float2 s2 = __ffma2_rn(__fmul2_rn(k13, x2), x2, __ffma2_rn(__fmul2_rn(q, y2), y2, eps));
-    s0 = __fmul2_rn(s0, s0);
-    s1 = __fmul2_rn(s1, s1);
-    s2 = __fmul2_rn(s2, s2);
-    const float2 t0 = __fmul2_rn(s1, s2);                          // d_0 = 1  (x 1/10)
-    const float2 t1 = __fmul2_rn(f2(6.f), __fmul2_rn(s0, s2));     // d_1 = 6
-    const float2 t2 = __fmul2_rn(f2(3.f), __fmul2_rn(s0, s1));     // d_2 = 3
-    const float2 num = __ffma2_rn(P0, t0, __ffma2_rn(P1, t1, __fmul2_rn(P2, t2)));
-    const float2 den = __fmul2_rn(f2(6.f), __fadd2_rn(t0, __fadd2_rn(t1, t2)));
-    // the fast division as in weno5_left (den in [6e-24, 1e30] for |q| <= 1e3)
-    return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    using A = Ar<V>;
+    const V z = A::sub(ej, ejm);
+    return A::fma(A::mul(A::k(13.0 / 3.0), z), z, A::k(1e-6));
+}
+
+// Numerator N and denominator D of sum_r omega_r g_r = N / D for the
+// stencil direction with first differences E0..E3 (e_{i-2..i+1} for the
+// left-biased value) and window terms Z0..Z2 (Z_{i-1}, Z_i, Z_{i+1}):
+//   N = g0 S1 S2 + 6 g1 S0 S2 + 3 g2 S0 S1,  D = S1 S2 + 6 S0 S2 + 3 S0 S1,
+// S_r = (eps + beta_r)^2; the reconstructed value is q_i + N / (6 D).
+template <typename V>
+__device__ __forceinline__ void weno_nd_win(V E0, V E1, V E2, V E3, V Z0, V Z1, V Z2, V &N, V &D)
+{
+    using A = Ar<V>;
+    const V y0 = A::fma(A::k(3.0), E1, A::neg(E0));
+    const V y1 = A::add(E1, E2);
+    const V y2 = A::fma(A::k(-3.0), E2, E3);
+    const V g0 = A::fma(A::k(2.0), y0, A::neg(E1));   // 5 e_{i-1} - 2 e_{i-2}
+    const V g1 = A::add(y1, E2);                                   // e_{i-1} + 2 e_i
+    const V g2 = A::sub(E2, y2);                                   // 4 e_i - e_{i+1}
+    V s0 = A::fma(y0, y0, Z0);
+    V s1 = A::fma(y1, y1, Z1);
+    V s2 = A::fma(y2, y2, Z2);
+    s0 = A::mul(s0, s0);
+    s1 = A::mul(s1, s1);
+    s2 = A::mul(s2, s2);
+    const V t = A::mul(s1, s2);                 // d_0 = 1  (x 1/10)
+    const V a = A::mul(A::k(3.0), s1);          // d_2 = 3
+    const V b = A::mul(A::k(6.0), s2);          // d_1 = 6
+    D = A::fma(s0, A::add(a, b), t);
+    N = A::fma(g0, t, A::mul(s0, A::fma(g1, b, A::mul(g2, a))));
+}
+
+// the window of one array along a run of interfaces (see above):
+// f^+ (left-biased at i+1/2): e = (e_{i-2}, e_{i-1}, e_i, e_{i+1}),
+//     z = (Z_{i-1}, Z_i, Z_{i+1}), last = q_{i+2};
+// f^- (right-biased at i+1/2): e = (e_{i-1}, e_i, e_{i+1}, e_{i+2}),
+//     z = (Z_i, Z_{i+1}, Z_{i+2}), last = q_{i+3}.
+// The base values (q^+_i, q^-_{i+1}) are read from shared memory when needed,
+// which keeps the window at eight registers (sixteen in FP64) per array.
+template <typename V>
+struct WenoWin {
+    V last, e0, e1, e2, e3, z0, z1, z2;
+    // from the values v0..v4 at five consecutive cells of the stencil
+    __device__ __forceinline__ void init(V v0, V v1, V v2, V v3, V v4)
+    {
+        using A = Ar<V>;
+        last = v4;
+        e0 = A::sub(v1, v0);
+        e1 = A::sub(v2, v1);
+        e2 = A::sub(v3, v2);
+        e3 = A::sub(v4, v3);
+        z0 = weno_z(e1, e0);
+        z1 = weno_z(e2, e1);
+        z2 = weno_z(e3, e2);
+    }
+    // one interface to the right, given the next cell value
+    __device__ __forceinline__ void advance(V v)
+    {
+        using A = Ar<V>;
+        const V en = A::sub(v, last);
+        const V zn = weno_z(en, e3);
+        last = v;
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
+        e3 = en;
+        z0 = z1;
+        z1 = z2;
+        z2 = zn;
+    }
+    __device__ __forceinline__ void left(V &N, V &D) const { weno_nd_win(e0, e1, e2, e3, z0, z1, z2, N, D); }
+    // mirrored stencil: N carries the sign of the negated g
+    __device__ __forceinline__ void right(V &N, V &D) const { weno_nd_win(e3, e2, e1, e0, z2, z1, z0, N, D); }
+};
+
+// interface flux F = W^-(f^+) + W^+(f^-) from the two windows and the base
+// values qp = q^+_i, qm = q^-_{i+1} (Burgers):
+//   F = 2 (q^+_i + q^-_{i+1}) + (N^+ D^- - N^- D^+) / (3 D^+ D^-)
+// with one division in FP64 (each D lies in [1e-23, 1e33] for |q| <= 1e3, so
+// the product stays far inside the FP64 range) and two in FP32
+template <typename V>
+__device__ __forceinline__ V split_flux_win(const WenoWin<V> &P, const WenoWin<V> &M, V qp, V qm)
+{
+    using A = Ar<V>;
+    V Np, Dp, Nm, Dm;
+    P.left(Np, Dp);
+    M.right(Nm, Dm);
+    const V base = A::add(qp, qm);
+    if constexpr (std::is_same<V, double>::value) {
+        const V num = A::fma(Np, Dm, A::neg(A::mul(Nm, Dp)));
+        const V den = A::mul(A::k(3.0), A::mul(Dp, Dm));
+        return A::fma(A::k(2.0), base, A::div(num, den));
+    } else {
+        const V fr = A::sub(A::div(Np, A::mul(A::k(3.0), Dp)), A::div(Nm, A::mul(A::k(3.0), Dm)));
+        return A::fma(A::k(2.0), base, fr);
+    }
+}
+
+// advection (alpha = 1): f^- = (u - u)/2 is zero, so its reconstruction is
+// exactly zero and F = W^-(f^+) = 2 q^+_i + N^+ / (3 D^+)
+template <typename V>
+__device__ __forceinline__ V split_flux_win_adv(const WenoWin<V> &P, V qp)
+{
+    using A = Ar<V>;
+    V Np, Dp;
+    P.left(Np, Dp);
+    return A::fma(A::k(2.0), qp, A::div(Np, A::mul(A::k(3.0), Dp)));
 }
 
 template <typename R, int SCHEME, int FLUX, int CPT>
 struct Slab {
-    R *qa;        // nx + 6: f^+ (split form) or the stage state (state form)
-    R *qb;        // nx + 6: f^- (split form)
-    R *qf;        // nx + 1: interface fluxes, qf[i+1] = F_{i+1/2}, qf[0] = F_{-1/2}
+    R *qa;        // slots of cells -3..nx+2: f^+ / 2 (WENO5 split form), f^+ (first
+                  // order), or the stage state (state form, Roe)
+    R *qb;        // the same slots: f^- / 2 or f^-
+    R *qf;        // slots 0..nx: interface fluxes, qf[i+1] = F_{i+1/2}, qf[0] = F_{-1/2}
     R *red;       // NWARP_MAX
     int nx;
     int numflux;
@@ -258,91 +401,146 @@ struct Slab {
     R psiDt;
     static constexpr int kScheme = SCHEME, kCpt = CPT;
 
+    // FP32 slabs pad the shared arrays with one slot after every CPT slots:
+    // thread t reads the window of interfaces t*CPT.., i.e. lanes CPT slots
+    // apart, and CPT + 1 slots apart spread over distinct banks.  FP64 slabs
+    // are bound by the FP64 pipe, not by shared memory, and keep the plain
+    // layout (the adjoint slab overlays it).
+    static constexpr bool PAD = sizeof(R) == 4 && CPT >= 2;
+    static __host__ __device__ __forceinline__ int phys(int s) { return PAD ? s + s / CPT : s; }
+    static __host__ __device__ __forceinline__ int extent(int nx) { return phys(nx + 2 * GHOST - 1) + 1; }
+
+    int pstride;  // slots between a thread's consecutive interleaved cells
+
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
         : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))
     {
+        // blockDim.x is a multiple of 32, hence of CPT, so the padded slot of
+        // cell t + c*blockDim.x + o is phys(t + o) + c * pstride
+        pstride = PAD ? (int)blockDim.x + (int)blockDim.x / CPT : (int)blockDim.x;
+        const int E = extent(nx);
         qa = reinterpret_cast<R *>(smem);
-        qb = qa + (nx + 2 * GHOST);
-        qf = qb + (nx + 2 * GHOST);
-        red = qf + (nx + 2 * GHOST);
+        qb = qa + E;
+        qf = qb + E;
+        red = qf + E;
     }
 
     static constexpr int RECON_UNROLL = sizeof(R) == 4 ? 1 : CPT;
 
     __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
-    __device__ __forceinline__ int lim() const { return nx + 2 * GHOST; }   // extent of qa, qb, qf
+    __device__ __forceinline__ int lim() const { return extent(nx); }   // extent of qa, qb, qf
+
+    // element of logical slot s (cell s - GHOST for qa/qb; interface s - 1 for qf)
+    __device__ __forceinline__ R &at(R *arr, int s) const { return MGRIT_SH(arr, phys(s), lim()); }
+    __device__ __forceinline__ R at(const R *arr, int s) const { return MGRIT_SH(arr, phys(s), lim()); }
 
     // store cell i (and its periodic ghost copy) into slot i + GHOST
     __device__ __forceinline__ void put(R *arr, int i, R v) const
     {
-        MGRIT_SH(arr, i + GHOST, lim()) = v;
-        if (i < GHOST) MGRIT_SH(arr, i + GHOST + nx, lim()) = v;
-        if (i >= nx - GHOST) MGRIT_SH(arr, i + GHOST - nx, lim()) = v;
+        at(arr, i + GHOST) = v;
+        if (i < GHOST) at(arr, i + GHOST + nx) = v;
+        if (i >= nx - GHOST) at(arr, i + GHOST - nx) = v;
+    }
+    // interfaces i0 .. i0 + run() - 1 (i0 = t * CPT) of this thread's contiguous run
+    __device__ __forceinline__ int run() const
+    {
+        const int r = nx - (int)threadIdx.x * CPT;
+        return r < 0 ? 0 : (r < CPT ? r : CPT);
+    }
+    // physical index of slot cell(c) + o (affine in c, see pstride)
+    __device__ __forceinline__ int pc(int c, int o) const { return phys((int)threadIdx.x + o) + c * pstride; }
+    // put() for this thread's owned cell c
+    __device__ __forceinline__ void put_c(R *arr, int c, R v) const
+    {
+        const int i = cell(c);
+        MGRIT_SH(arr, pc(c, GHOST), lim()) = v;
+        if (i < GHOST) at(arr, i + GHOST + nx) = v;
+        if (i >= nx - GHOST) at(arr, i + GHOST - nx) = v;
     }
 
     // left-biased reconstruction at i+1/2 from slots around s = i + GHOST
     __device__ __forceinline__ R rec_minus(const R *q, int s) const
     {
-        if (SCHEME == SCH_FO_FE) return MGRIT_SH(q, s, lim());
-        return weno5_left<R>(MGRIT_SH(q, s - 2, lim()), MGRIT_SH(q, s - 1, lim()), MGRIT_SH(q, s, lim()),
-                             MGRIT_SH(q, s + 1, lim()), MGRIT_SH(q, s + 2, lim()));
+        if (SCHEME == SCH_FO_FE) return at(q, s);
+        return weno5_left<R>(at(q, s - 2), at(q, s - 1), at(q, s), at(q, s + 1), at(q, s + 2));
     }
     // right-biased reconstruction at i+1/2: the mirrored stencil
     __device__ __forceinline__ R rec_plus(const R *q, int s) const
     {
-        if (SCHEME == SCH_FO_FE) return MGRIT_SH(q, s + 1, lim());
-        return weno5_left<R>(MGRIT_SH(q, s + 3, lim()), MGRIT_SH(q, s + 2, lim()), MGRIT_SH(q, s + 1, lim()),
-                             MGRIT_SH(q, s, lim()), MGRIT_SH(q, s - 1, lim()));
-    }
-
-    // F_{i+1/2} = W^-(f^+) + W^+(f^-) of the split form.  With WENO5 in FP64
-    // the two fractions share one division, n1/d1 + n2/d2 = (n1 d2 + n2 d1) /
-    // (d1 d2) (each d lies in [6e-24, 1e30] for |q| <= 1e3): the FP64 pipe is
-    // this kernel's bottleneck and an IEEE division is a long sequence on it
-    __device__ __forceinline__ R split_flux(int s) const
-    {
-        if (SCHEME == SCH_FO_FE || sizeof(R) == 4) return rec_minus(qa, s) + rec_plus(qb, s);
-        const int L = lim();
-        R n1, d1, n2, d2;
-        weno5_left_nd<R>(MGRIT_SH(qa, s - 2, L), MGRIT_SH(qa, s - 1, L), MGRIT_SH(qa, s, L),
-                         MGRIT_SH(qa, s + 1, L), MGRIT_SH(qa, s + 2, L), n1, d1);
-        weno5_left_nd<R>(MGRIT_SH(qb, s + 3, L), MGRIT_SH(qb, s + 2, L), MGRIT_SH(qb, s + 1, L),
-                         MGRIT_SH(qb, s, L), MGRIT_SH(qb, s - 1, L), n2, d2);
-        return (n1 * d2 + n2 * d1) / (d1 * d2);
-    }
-
-    // FP32 WENO5 split fluxes of the owned interfaces two at a time (cells
-    // c and c+1 of this thread) on packed pairs; a cell beyond nx reads slot
-    // GHOST instead (in range) and its result is dropped
-    __device__ __forceinline__ void split_fluxes_x2() const
-    {
-        const int L = lim();
-#pragma unroll 1
-        for (int c = 0; c < CPT; c += 2) {
-            const int i0 = cell(c), i1 = c + 1 < CPT ? cell(c + 1) : nx;
-            if (i0 >= nx) break;   // cells grow with c
-            const int s0 = i0 + GHOST, s1 = (i1 < nx ? i1 : 0) + GHOST;
-            const float2 m = weno5_left_x2(
-                make_float2(MGRIT_SH(qa, s0 - 2, L), MGRIT_SH(qa, s1 - 2, L)),
-                make_float2(MGRIT_SH(qa, s0 - 1, L), MGRIT_SH(qa, s1 - 1, L)),
-                make_float2(MGRIT_SH(qa, s0, L), MGRIT_SH(qa, s1, L)),
-                make_float2(MGRIT_SH(qa, s0 + 1, L), MGRIT_SH(qa, s1 + 1, L)),
-                make_float2(MGRIT_SH(qa, s0 + 2, L), MGRIT_SH(qa, s1 + 2, L)));
-            const float2 p = weno5_left_x2(
-                make_float2(MGRIT_SH(qb, s0 + 3, L), MGRIT_SH(qb, s1 + 3, L)),
-                make_float2(MGRIT_SH(qb, s0 + 2, L), MGRIT_SH(qb, s1 + 2, L)),
-                make_float2(MGRIT_SH(qb, s0 + 1, L), MGRIT_SH(qb, s1 + 1, L)),
-                make_float2(MGRIT_SH(qb, s0, L), MGRIT_SH(qb, s1, L)),
-                make_float2(MGRIT_SH(qb, s0 - 1, L), MGRIT_SH(qb, s1 - 1, L)));
-            put_flux(i0, m.x + p.x);
-            if (i1 < nx) put_flux(i1, m.y + p.y);
-        }
+        if (SCHEME == SCH_FO_FE) return at(q, s + 1);
+        return weno5_left<R>(at(q, s + 3), at(q, s + 2), at(q, s + 1), at(q, s), at(q, s - 1));
     }
 
     __device__ __forceinline__ void put_flux(int i, R F) const
     {
-        MGRIT_SH(qf, i + 1, nx + 1) = F;
-        if (i == nx - 1) qf[0] = F;
+        at(qf, i + 1) = F;
+        if (i == nx - 1) at(qf, 0) = F;
+    }
+
+    // WENO5 split fluxes of the interfaces i0 .. i0 + CPT - 1 (i0 = t * CPT)
+    // from qa = f^+/2 and qb = f^-/2, one sliding window per array (see
+    // WenoWin).  Reads slots i0 - 1 .. i0 + n + 2 (+ GHOST), all inside the
+    // arrays for every interface i < nx.
+    __device__ __forceinline__ void split_fluxes_win() const
+    {
+        const int i0 = threadIdx.x * CPT;
+        if (i0 >= nx) return;
+        const int n = nx - i0 < CPT ? nx - i0 : CPT;
+        const int s = i0 + GHOST;
+        WenoWin<R> P, M;
+        P.init(at(qa, s - 2), at(qa, s - 1), at(qa, s), at(qa, s + 1), at(qa, s + 2));
+        if (FLUX == FLX_BURGERS)
+            M.init(at(qb, s - 1), at(qb, s), at(qb, s + 1), at(qb, s + 2), at(qb, s + 3));
+        // rolled: the window shifts by register moves, and its live state
+        // stays independent of CPT (unrolled, the FP64 slabs spill)
+#pragma unroll 1
+        for (int k = 0; k < n; ++k) {
+            const R qp = at(qa, s + k);
+            put_flux(i0 + k, FLUX == FLX_BURGERS ? split_flux_win(P, M, qp, at(qb, s + k + 1))
+                                                 : split_flux_win_adv(P, qp));
+            if (k + 1 < n) {
+                P.advance(at(qa, s + k + 3));
+                if (FLUX == FLX_BURGERS) M.advance(at(qb, s + k + 4));
+            }
+        }
+    }
+
+    // FP32: the same windows on packed pairs.  Lane x of the pair walks
+    // interfaces i0 .. i0 + CPT/2 - 1, lane y i0 + CPT/2 .. i0 + CPT - 1;
+    // each lane performs the scalar window's operations, so the bits do not
+    // depend on the pairing.  Lane y's slots are clamped into the arrays
+    // where its interfaces run past nx (those results are dropped).
+    __device__ __forceinline__ void split_fluxes_win2() const
+    {
+        static_assert(sizeof(R) == 4 && CPT >= 2, "packed windows are FP32 with CPT >= 2");
+        constexpr int H = CPT / 2;
+        const int i0 = threadIdx.x * CPT;
+        if (i0 >= nx) return;
+        const int n = nx - i0 < CPT ? nx - i0 : CPT;
+        const int sx = i0 + GHOST;
+        const bool yok = n > H;
+        const int sy = yok ? sx + H : sx;
+        const int top = nx + 2 * GHOST - 1;   // last slot
+        auto ld = [&](const R *q, int ox, int oy) {
+            const int y = sy + oy < top ? sy + oy : top;
+            return make_float2(at(q, sx + ox), at(q, y));
+        };
+        WenoWin<float2> P, M;
+        P.init(ld(qa, -2, -2), ld(qa, -1, -1), ld(qa, 0, 0), ld(qa, 1, 1), ld(qa, 2, 2));
+        if (FLUX == FLX_BURGERS) M.init(ld(qb, -1, -1), ld(qb, 0, 0), ld(qb, 1, 1), ld(qb, 2, 2), ld(qb, 3, 3));
+        const int nxl = n < H ? n : H;   // interfaces of lane x
+#pragma unroll 1
+        for (int k = 0; k < nxl; ++k) {
+            const float2 qp = ld(qa, k, k);
+            const float2 F = FLUX == FLX_BURGERS ? split_flux_win(P, M, qp, ld(qb, k + 1, k + 1))
+                                                 : split_flux_win_adv(P, qp);
+            put_flux(i0 + k, F.x);
+            if (yok && H + k < n) put_flux(i0 + H + k, F.y);
+            if (k + 1 < nxl) {
+                P.advance(ld(qa, k + 3, k + 3));
+                if (FLUX == FLX_BURGERS) M.advance(ld(qb, k + 4, k + 4));
+            }
+        }
     }
 
     // Interface fluxes F_{i+1/2} of the stage input w into qf (Sec. 2.1.2).
@@ -362,77 +560,89 @@ struct Slab {
                     }
                 alpha = key_value(block_max_key(v, red));
             }
-            // f^+/- = f(u)/2 +/- (alpha/2) u, as one multiply-add on f/2
-            const R h = R(0.5) * alpha;
+            if (SCHEME == SCH_WENO5_SSPRK3) {
+                // q^+/- = f^+/-/2 = u (u/8 +/- alpha/4) (Burgers), u/2 and 0 (advection)
+                const R a4 = R(0.25) * alpha;
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                const int i = cell(c);
-                if (i < nx) {
-                    const R p = R(0.5) * phys_flux<FLUX>(w[c]);
-                    put(qa, i, fma(h, w[c], p));
-                    put(qb, i, fma(-h, w[c], p));
+                for (int c = 0; c < CPT; ++c) {
+                    const int i = cell(c);
+                    if (i < nx) {
+                        if (FLUX == FLX_BURGERS) {
+                            put_c(qa, c, Ar<R>::mul(Ar<R>::fma(R(0.125), w[c], a4), w[c]));
+                            put_c(qb, c, Ar<R>::mul(Ar<R>::fma(R(0.125), w[c], -a4), w[c]));
+                        } else {
+                            put_c(qa, c, R(0.5) * w[c]);
+                        }
+                    }
                 }
-            }
-            __syncthreads();
-            // (beyond 8 cells per thread the pairs' live registers spill)
-            if constexpr (sizeof(R) == 4 && SCHEME == SCH_WENO5_SSPRK3 && CPT <= 8) {
-                split_fluxes_x2();
+                __syncthreads();
+                // (packed FP32 windows beyond 8 cells per thread would spill)
+                if constexpr (sizeof(R) == 4 && CPT >= 2 && CPT <= 8)
+                    split_fluxes_win2();
+                else
+                    split_fluxes_win();
             } else {
-            // this loop touches no register array, so FP32 slabs keep it rolled
-            // (fewer live registers for 16-32 cells per thread); FP64 unrolls it
-#pragma unroll(RECON_UNROLL)
-            for (int c = 0; c < CPT; ++c) {
-                const int i = cell(c);
-                if (i < nx) put_flux(i, split_flux(i + GHOST));
-            }
+                // first order: f^+/- = f(u)/2 +/- (alpha/2) u, one multiply-add on f/2
+                const R h = R(0.5) * alpha;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    const int i = cell(c);
+                    if (i < nx) {
+                        const R p = R(0.5) * phys_flux<FLUX>(w[c]);
+                        put_c(qa, c, fma(h, w[c], p));
+                        put_c(qb, c, fma(-h, w[c], p));
+                    }
+                }
+                __syncthreads();
+                const int i0 = threadIdx.x * CPT, n = run();
+#pragma unroll 1
+                for (int k = 0; k < n; ++k)
+                    put_flux(i0 + k, rec_minus(qa, i0 + k + GHOST) + rec_plus(qb, i0 + k + GHOST));
             }
         } else if (numflux == NF_ROE) {
             // local per interface: no global speed, no reduction
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
-                if (i < nx) put(qa, i, w[c]);
+                if (i < nx) put_c(qa, c, w[c]);
             }
             __syncthreads();
-#pragma unroll(RECON_UNROLL)
-            for (int c = 0; c < CPT; ++c) {
-                const int i = cell(c);
-                if (i < nx)
-                    put_flux(i, roe_flux<FLUX>(rec_minus(qa, i + GHOST), rec_plus(qa, i + GHOST)));
+            const int i0 = threadIdx.x * CPT, n = run();
+#pragma unroll 1
+            for (int k = 0; k < n; ++k) {
+                const int s = i0 + k + GHOST;
+                put_flux(i0 + k, roe_flux<FLUX>(rec_minus(qa, s), rec_plus(qa, s)));
             }
         } else {
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
-                if (i < nx) put(qa, i, w[c]);
+                if (i < nx) put_c(qa, c, w[c]);
             }
             __syncthreads();
-            // u^-_{i+1/2} parked in qb[i], u^+_{i+1/2} in qf[i+1]; each thread
-            // reads back only its own slots, then overwrites qf[i+1] with F
+            // u^-_{i+1/2} parked in qb slot i, u^+_{i+1/2} in qf slot i+1 for this
+            // thread's run of interfaces; each thread reads back only its own
+            // slots, then overwrites qf slot i+1 with F
+            const int i0 = threadIdx.x * CPT, n = run();
             decltype(mag_key(R(0))) v = 0;   // max |u^-|, |u^+| (Burgers)
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                const int i = cell(c);
-                if (i < nx) {
-                    const R um = rec_minus(qa, i + GHOST);
-                    const R up = rec_plus(qa, i + GHOST);
-                    MGRIT_SH(qb, i, nx) = um;
-                    MGRIT_SH(qf, i + 1, nx + 1) = up;
-                    const auto km = mag_key(um), kp = mag_key(up);
-                    const auto k = km > kp ? km : kp;
-                    v = k > v ? k : v;
-                }
+#pragma unroll 1
+            for (int k = 0; k < n; ++k) {
+                const int i = i0 + k;
+                const R um = rec_minus(qa, i + GHOST);
+                const R up = rec_plus(qa, i + GHOST);
+                at(qb, i) = um;
+                at(qf, i + 1) = up;
+                const auto km = mag_key(um), kp = mag_key(up);
+                const auto kk = km > kp ? km : kp;
+                v = kk > v ? kk : v;
             }
             R alpha = R(1);
             if (FLUX == FLX_BURGERS) alpha = key_value(block_max_key(v, red));
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                const int i = cell(c);
-                if (i < nx) {
-                    const R um = MGRIT_SH(qb, i, nx), up = MGRIT_SH(qf, i + 1, nx + 1);
-                    put_flux(i, R(0.5) * (phys_flux<FLUX>(up) + phys_flux<FLUX>(um)) -
-                                    R(0.5) * alpha * (up - um));
-                }
+#pragma unroll 1
+            for (int k = 0; k < n; ++k) {
+                const int i = i0 + k;
+                const R um = at(qb, i), up = at(qf, i + 1);
+                put_flux(i, R(0.5) * (phys_flux<FLUX>(up) + phys_flux<FLUX>(um)) - R(0.5) * alpha * (up - um));
             }
         }
         __syncthreads();
@@ -442,8 +652,7 @@ struct Slab {
     // valid after fluxes().
     __device__ __forceinline__ R A(int c) const
     {
-        const int i = cell(c);
-        return -(MGRIT_SH(qf, i + 1, nx + 1) - MGRIT_SH(qf, i, nx + 1)) * dxinv;
+        return -(MGRIT_SH(qf, pc(c, 1), lim()) - MGRIT_SH(qf, pc(c, 0), lim())) * dxinv;
     }
 
     // Eq. (fineLF): u <- E u - dt D f(u), (E v)_i = (v_{i+1} + v_{i-1})/2,
@@ -481,13 +690,13 @@ struct Slab {
                 const int i = cell(c);
                 if (i < nx) {
                     const int s = i + GHOST;
-                    const R Df = (MGRIT_SH(qb, s + 1, lim()) - MGRIT_SH(qb, s - 1, lim())) * hd;
+                    const R Df = (at(qb, s + 1) - at(qb, s - 1)) * hd;
                     if (first)
                         acc[c] = k == 0 ? Df
-                                        : Df + R(0.5) * (MGRIT_SH(qf, s + 1, lim()) + MGRIT_SH(qf, s - 1, lim()));
+                                        : Df + R(0.5) * (at(qf, s + 1) + at(qf, s - 1));
                     else if (k == 0)
                         acc[c] = Df;   // D f(u)
-                    v[c] = R(0.5) * (MGRIT_SH(qa, s + 1, lim()) + MGRIT_SH(qa, s - 1, lim()));
+                    v[c] = R(0.5) * (at(qa, s + 1) + at(qa, s - 1));
                 }
             }
         }
@@ -566,11 +775,14 @@ struct Slab {
     }
 };
 
-// shared-memory bytes of one slab
+// shared-memory bytes of one slab of nx cells with cpt cells per thread
 template <typename R>
-inline size_t slab_smem_bytes(int nx)
+inline size_t slab_smem_bytes(int nx, int cpt)
 {
-    return sizeof(R) * (3 * (size_t)(nx + 2 * GHOST) + NWARP_MAX);
+    const bool pad = sizeof(R) == 4 && cpt >= 2;
+    const size_t s = (size_t)nx + 2 * GHOST;
+    const size_t e = pad ? (s - 1) + (s - 1) / (size_t)cpt + 1 : s;
+    return sizeof(R) * (3 * e + NWARP_MAX);
 }
 
 }  // namespace mgrit
