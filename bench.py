@@ -40,23 +40,22 @@ WORKLOAD = dict(nx=4096, nt=16384, m=4, levels=6, T=1.0, seed=0)
 SAMPLE = dict(nx=4096, nt=4096, m=4, levels=6, T=0.25, seed=0)   # CPU baseline sample
 
 # Algorithmic FLOPs per cell update of one SSPRK3 step of WENO5-JS with the
-# global LF splitting, counted from the paper's formulas (every +, -, x, /,
-# |.| and max counts 1): per reconstruction 73 (3 candidates x 6, 3
-# smoothness indicators x 12, 3 weights x 3, normalisation 5 + sum 5), per
-# stage and cell 2 reconstructions + 1 (flux sum) + 2 (flux difference / dx)
-# + 9 (|u|, max, f = u^2/2, f^+/-) = 158; 3 stages + 12 for the RK
-# combinations = 486 (Burgers).
-FLOPS_PER_CELL_UPDATE = 486
+# global LF splitting (Burgers): the operations the paper's formulas take, as
+# counted by the instrumented build of the oracle (oracle/count_flops.py:
+# every data-dependent +, -, x, /, |.| and comparison counts 1, constant
+# expressions fold): 185 additions, 289 multiplications, 75 divisions,
+# 3 |.| and 3 comparisons.  tests/test_flop_count.py keeps the figure equal
+# to the counting run.
+FLOPS_PER_CELL_UPDATE = 555
 # adjoint gradient workload: pre-shock and post-shock final times with the
 # levels the coarse CFL allows (level-2 CFL 0.51 at T=0.12, level-1 0.32 at T=0.3)
 ADJOINT_WORKLOAD = dict(nx=2048, nt=8192, m=4, seed=1, target_seed=1001, breaking_time=0.201,
                         cases=((0.12, 3), (0.3, 2)))
 
-# FP64 peak of the SIMT pipe, from the unit counts and clocks: 152 SMs x
-# 2.07 GHz x 4 FP64 FLOP/clk/SM (the nominal 1.25 TFLOP/s FP64 rate).
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
-# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Nominal SIMT rates from the unit counts and clocks (context only; the
+# roofline uses the rates measured in the run, see fma_peaks)
+FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12          # 2 DFMA / clk / SM
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 128 FFMA lanes / SM
 
 # DRAM bytes (read + write) per level-0 relaxation launch from an ncu
 # capture, keyed by a hash of the kernel sources it was taken on; reported
@@ -71,6 +70,21 @@ def measured_hbm_gbs():
             return float(json.load(f)["hbm_gbs"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def fma_peaks(mgrit):
+    """Measured multiply-add throughput of the FP64 and FP32 pipes on this GPU
+    (mgrit_fma_probe, ~0.1 s each, best of 3): the roofline denominators of
+    the arithmetic-bound sweeps.  FP32 takes the faster of scalar and packed
+    pairs."""
+    def best(kind, iters):
+        mgrit.fma_probe(kind, max(1, iters // 20))
+        return max(mgrit.fma_probe(kind, iters) for _ in range(3)) / 1e12
+    fp64 = best(mgrit.FMA_FP64, 3000)
+    fp32 = max(best(mgrit.FMA_FP32, 200000), best(mgrit.FMA_FP32X2, 100000))
+    return {"fp64_tflops": fp64, "fp32_tflops": fp32,
+            "source": "mgrit_fma_probe on this GPU in this run: 152 x 8 CTAs x 256 threads, "
+                      "8 independent multiply-add chains per thread, CUDA events, best of 3"}
 
 
 def kernel_hash():
@@ -90,6 +104,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch line")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient line")
+    p.add_argument("--no-c4", action="store_true", help="skip the nx=16384, nt=65536 FP32 line")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the paper's coarse-integrator / relaxation / cycle comparisons")
     return p.parse_args()
@@ -207,14 +222,24 @@ def cycle_updates(w, fcf=True):
     return steps * w["nx"]
 
 
-def workload_config(ws):
-    """The config object of both arms' JSON lines (the bench workload)."""
-    return {"workload": "Burgers WENO5-JS/LF-split/SSPRK3 FP64 MGRIT V-cycle: nx=4096, "
-                        "nt=16384, T=1, m=4, 6 levels, FCF, Fourier u0 seed 0",
-            "step": "one V-cycle (all levels) from the initial iterate",
-            "cell_updates_per_step": cycle_updates(WORKLOAD),
-            "l2": "inputs larger than L2: each cycle streams >500 MB of level rows",
-            "parallelism": "replicas" if ws > 1 else "single GPU"}
+def workload_config(ws, sample=None):
+    """The config object of the JSON line: the bench workload, or (reference
+    arm) the sample of it that the oracle times, with the full workload named."""
+    full = ("Burgers WENO5-JS/LF-split/SSPRK3 FP64 MGRIT V-cycle: nx=4096, nt=16384, T=1, m=4, "
+            "6 levels, FCF, Fourier u0 seed 0")
+    w = sample or WORKLOAD
+    cfg = {"workload": full if sample is None else
+           ("Burgers WENO5-JS/LF-split/SSPRK3 FP64 MGRIT V-cycle: nx=%d, nt=%d, T=%g, m=%d, "
+            "%d levels, FCF, Fourier u0 seed %d" % (w["nx"], w["nt"], w["T"], w["m"], w["levels"],
+                                                    w["seed"])),
+           "step": "one V-cycle (all levels) from the initial iterate",
+           "cell_updates_per_step": cycle_updates(w),
+           "l2": "inputs larger than L2: each cycle streams >500 MB of level rows",
+           "parallelism": "replicas" if ws > 1 else "single GPU"}
+    if sample is not None:
+        cfg["sample_of"] = full
+        cfg["l2"] = "host run (no L2 flush applies)"
+    return cfg
 
 
 def sample_desc(s):
@@ -241,7 +266,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(ws),
+        "config": workload_config(ws, SAMPLE),
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
                          "kind": "oracle",
                          "sample": "FP64 C oracle on the host cores: " + sample_desc(SAMPLE)},
@@ -301,6 +326,57 @@ def adjoint_gradient(mgrit, inputs, dev, stream):
             "rel_max_diff_vs_serial_adjoint": rel,
             "J": 0.5 * float((lamT ** 2).sum())})
         s.close()
+    return out
+
+
+C4 = dict(nx=16384, nt=65536, m=8, levels=3)
+
+
+def config4(mgrit, inputs, dev, timed_ms, rel_errs):
+    """Config 4: Burgers, nx=16384, nt=65536, m=8, FP32 WENO5/SSPRK3 sweeps with
+    FP64 tau correction, residual norms and coarsest solve; u0 = 0.5 + sin 2 pi x
+    (breaks at t = 0.159); smooth T=0.12 and shocked T=0.5.
+    (1) As stated (3 levels): outcome and cycle count (coarsest CFL 2.9 and 12).
+    (2) CFL-capped at T=0.12 (2 levels, coarse CFL 0.36): time to tolerance,
+        against FP32 serial stepping, and the max / L1 error of u(T) against FP64
+        serial stepping (the GPU FP64 stepper, equal to the oracle's to 1e-11 in
+        the parity tests).  At T=0.5 even 2 levels put the coarse CFL at 1.5, past
+        the explicit limit; its 2-level outcome is reported as well."""
+    import torch
+    nx, nt, m = C4["nx"], C4["nt"], C4["m"]
+    u0_np = inputs.sine_ic(nx)
+    u0 = torch.as_tensor(u0_np, device=dev)
+    speed = float(abs(u0_np).max())
+    out = {"workload": "Burgers WENO5-JS/LF-split/SSPRK3, FP32 sweeps (FP64 tau, norms, coarsest), "
+                       "nx=16384, nt=65536, m=8, FCF, u0 = 0.5 + sin(2 pi x)",
+           "runs": []}
+    for T in (0.12, 0.5):
+        for L in (C4["levels"], 2):
+            cfl = speed * (T / nt) * nx * m ** (L - 1)
+            capped = cfl <= 0.95
+            sv = mgrit.Solver(nx, nt, m, L, T=T, precision=32, max_iter=64 if capped else 16)
+            st, uT, _, stats = sv.solve(u0, want_uC=False)
+            run = {"T": T, "levels": L, "coarsest_cfl": cfl, "as_stated": L == C4["levels"],
+                   "status": mgrit.STATUS_NAMES[st], "cycles": stats.iters,
+                   "stagnated": bool(stats.stagnated), "seconds": stats.t_total_ms / 1e3,
+                   "res_hist": [stats.res_hist[k] for k in range(min(stats.iters + 1, 6))]}
+            if st == mgrit.OK and capped:
+                st2, uT, _, stats = sv.solve(u0, want_uC=False)     # warm (graphs captured)
+                run["seconds"] = stats.t_total_ms / 1e3
+                run["cell_updates_per_s"] = nx * nt / (stats.t_total_ms / 1e3)
+                sv.serial_step(u0, 8)
+                uTs32, ser32_ms = timed_ms(lambda: sv.serial_step(u0, nt))
+                s64 = mgrit.Solver(nx, nt, m, L, T=T)
+                s64.serial_step(u0, 8)
+                uT64, ser64_ms = timed_ms(lambda: s64.serial_step(u0, nt))
+                s64.close()
+                run.update({"serial_fp32_seconds": ser32_ms / 1e3,
+                            "serial_fp64_seconds": ser64_ms / 1e3,
+                            "speedup_vs_fp32_serial": ser32_ms / stats.t_total_ms,
+                            "error_vs_fp64_serial": rel_errs(uT, uT64),
+                            "serial_fp32_error_vs_fp64_serial": rel_errs(uTs32, uT64)})
+            sv.close()
+            out["runs"].append(run)
     return out
 
 
@@ -462,20 +538,28 @@ def run_mgrit(args):
     restrict_bytes = 40.0 * nC0 * W["nx"]
     restrict_gbs = restrict_bytes / (kern["restrict_l0"] / 1e3) / 1e9
     hbm_peak = measured_hbm_gbs()
+    peaks = fma_peaks(mgrit)
     achieved = FLOPS_PER_CELL_UPDATE * relax0_updates / (kern["relax_l0"] / 1e3) / 1e12
     traffic = TRAFFIC.get(kernel_hash())
 
     # ---- serial GPU stepping and time to tolerance -------------------------
     # serial: all nt fine steps of the workload on one thread-block cluster
+    def timed_ms(fn):
+        torch.cuda.synchronize()
+        ta = torch.cuda.Event(enable_timing=True)
+        tb = torch.cuda.Event(enable_timing=True)
+        ta.record(stream)
+        r = fn()
+        tb.record(stream)
+        torch.cuda.synchronize()
+        return r, ta.elapsed_time(tb)
+
+    def rel_errs(got, ref):
+        d = (got - ref).abs()
+        return {"max": float(d.max() / ref.abs().max()), "l1": float(d.sum() / ref.abs().sum())}
+
     s.serial_step(u0, 8)
-    torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    uT_serial = s.serial_step(u0, W["nt"])
-    b.record(stream)
-    torch.cuda.synchronize()
-    serial_ms = a.elapsed_time(b)
+    uT_serial, serial_ms = timed_ms(lambda: s.serial_step(u0, W["nt"]))
     st, _, _, stats = s.solve(u0, want_uC=False)
     outcome = {"status": mgrit.STATUS_NAMES[st], "cycles": stats.iters,
                "res_hist": [stats.res_hist[k] for k in range(min(stats.iters + 1, 8))],
@@ -486,42 +570,63 @@ def run_mgrit(args):
     while (Lc + 1 <= W["levels"] and
            speed * (W["T"] / W["nt"]) * W["nx"] * W["m"] ** Lc <= 0.95):
         Lc += 1
-    ttt = None
+    ttt = capped = None
     if Lc >= 2:
+        cfl_c = speed * (W["T"] / W["nt"]) * W["nx"] * W["m"] ** (Lc - 1)
         sc = mgrit.Solver(W["nx"], W["nt"], W["m"], Lc, T=W["T"], max_iter=120)
         sc.solve(u0, want_uC=False)                 # warm-up (allocation, graph capture)
         stc, uTc, _, statc = sc.solve(u0, want_uC=False)
         torch.cuda.synchronize()
-        err = float((uTc - uT_serial).abs().max() / uT_serial.abs().max())
-        ttt = {"levels": Lc, "coarsest_cfl": speed * (W["T"] / W["nt"]) * W["nx"] * W["m"] ** (Lc - 1),
+        ttt = {"levels": Lc, "coarsest_cfl": cfl_c,
                "status": mgrit.STATUS_NAMES[stc], "cycles": statc.iters,
                "seconds": statc.t_total_ms / 1e3, "serial_seconds": serial_ms / 1e3,
                "speedup_vs_serial": (serial_ms / 1e3) / (statc.t_total_ms / 1e3),
                "final_residual": statc.res_hist[statc.iters],
-               "rel_max_diff_vs_serial_uT": err}
+               "rel_max_diff_vs_serial_uT": rel_errs(uTc, uT_serial)["max"]}
+        # the headline's per-cycle throughput on this finite (CFL-capped)
+        # hierarchy, beside the as-stated one whose coarse levels go non-finite
+        pc_c = sc.cycle_cell_updates()
+        sc.run_cycles(u0, 1)
+        _, msc = timed_ms(lambda: sc.run_cycles(u0, args.steps))
+        capped = {"levels": Lc, "coarsest_cfl": cfl_c, "value": pc_c * args.steps / (msc / 1e3),
+                  "unit": "cell-updates/s", "ms_per_step": msc / args.steps,
+                  "cell_updates_per_step": pc_c}
         sc.close()
 
     # ---- the same workload with FP32 sweeps (precision = 32) ---------------
     s32 = mgrit.Solver(W["nx"], W["nt"], W["m"], W["levels"], T=W["T"], precision=32)
     for _ in range(3):
         s32.run_cycles(u0, 1)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(args.steps):
-        s32.run_cycles(u0, 1)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms32 = a.elapsed_time(b)
+    _, ms32 = timed_ms(lambda: [s32.run_cycles(u0, 1) for _ in range(args.steps)])
     s32.run_cycles(u0, 0)
     s32.launch_kernel(0, 0, 1)
-    torch.cuda.synchronize()
-    a.record(stream)
-    s32.launch_kernel(0, 0, reps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    relax32_ms = a.elapsed_time(b) / reps
+    _, relax32_reps = timed_ms(lambda: s32.launch_kernel(0, 0, reps))
+    relax32_ms = relax32_reps / reps
+    # time to tolerance in FP32 sweeps on the CFL-capped hierarchy, against
+    # FP32 serial stepping; errors of both against the FP64 serial solution
+    # (GPU FP64 stepping, equal to the oracle's to 1e-11 in the parity tests)
+    ttt32 = None
+    if Lc >= 2:
+        sc32 = mgrit.Solver(W["nx"], W["nt"], W["m"], Lc, T=W["T"], max_iter=120, precision=32)
+        sc32.solve(u0, want_uC=False)
+        st32, uT32, _, stat32 = sc32.solve(u0, want_uC=False)
+        sc32.serial_step(u0, 8)
+        uTs32, ser32_ms = timed_ms(lambda: sc32.serial_step(u0, W["nt"]))
+        ttt32 = {"levels": Lc, "status": mgrit.STATUS_NAMES[st32], "cycles": stat32.iters,
+                 "stagnated": bool(stat32.stagnated), "seconds": stat32.t_total_ms / 1e3,
+                 "serial_seconds": ser32_ms / 1e3,
+                 "speedup_vs_serial": ser32_ms / stat32.t_total_ms,
+                 "error_vs_fp64_serial": rel_errs(uT32, uT_serial),
+                 "serial_fp32_error_vs_fp64_serial": rel_errs(uTs32, uT_serial)}
+        sc32.close()
+
+    # ---- config 4: nx = 16384, nt = 65536, m = 8, FP32 sweeps ----------------
+    c4 = None if args.no_c4 else config4(mgrit, inputs, dev, timed_ms, rel_errs)
 
     # ---- A/B: one CTA per chunk on every level (chunk_clusters = 0) --------
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+
     def cycle_ms(sv, n):
         for _ in range(3):
             sv.run_cycles(u0, 1)
@@ -545,9 +650,11 @@ def run_mgrit(args):
     ach32 = FLOPS_PER_CELL_UPDATE * relax0_updates / (relax32_ms / 1e3) / 1e12
     fp32 = {"value": per_cycle * args.steps / (ms32 / 1e3), "unit": "cell-updates/s",
             "ms_per_step": ms32 / args.steps, "relax_l0_ms": relax32_ms,
-            "roofline": {"bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach32 / FP32_PEAK_TFLOPS,
-                         "peak_source": "derived FP32 SIMT rate: 152 SMs x 128 lanes x 2 x 2.07 GHz"}}
+            "roofline": {"bound": "alu", "achieved": ach32, "peak": peaks["fp32_tflops"],
+                         "unit": "TFLOP/s", "frac": ach32 / peaks["fp32_tflops"],
+                         "peak_source": "measured FP32 multiply-add rate (" + peaks["source"] + ")",
+                         "flops_per_cell_update": FLOPS_PER_CELL_UPDATE},
+            "time_to_tol_cfl_capped": ttt32}
     s32.close()
 
     # ---- 64 uneven instances: one batch vs one context at a time -----------
@@ -622,9 +729,10 @@ def run_mgrit(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(ws),
         "roofline": {"bound": "alu", "kernel": "level-0 relaxation (k_slab, MODE_RELAX)",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "derived FP64 SIMT rate: 152 SMs x 2.07 GHz x 4 FLOP/clk",
+                     "achieved": achieved, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["fp64_tflops"], "traffic": traffic,
+                     "peak_source": "measured FP64 multiply-add rate, burst (" + peaks["source"] + ")",
+                     "nominal_peak": FP64_NOMINAL_TFLOPS,
                      "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
                      "cell_updates_per_launch": relax0_updates},
         "cpu_baseline": cpu,
@@ -644,7 +752,9 @@ def run_mgrit(args):
                        "cell_updates_per_s": W["nx"] * W["nt"] / (serial_ms / 1e3),
                        "cluster_ctas": s.query(2)},
         "mgrit_outcome_as_stated": outcome,
+        "cfl_capped_cycle": capped,
         "time_to_tol_cfl_capped": ttt,
+        "config4": c4,
         "fp32_sweeps": fp32,
         "batched": batched,
         "adjoint": adjoint,

@@ -43,7 +43,7 @@ enum {
     MGRIT_ENOMEM = -3,     /* device or pinned-host allocation failed */
     MGRIT_EDIVERGED = -4,  /* residual not finite or > 1e8 x first residual */
     MGRIT_ENOTCONV = -5,   /* max_iter cycles without reaching tol */
-    MGRIT_ETIMEOUT = -6    /* reserved: a bounded device wait gave up */
+    MGRIT_ETIMEOUT = -6    /* a bounded device wait gave up (see mgrit_sync_status) */
 };
 
 /* spatial reconstruction + time integrator (Sec. 2.1.1, Sec. 2.2), or the
@@ -99,6 +99,14 @@ typedef struct {
                         on thread-block clusters (mgrit_query 100 + l);
                         0: one CTA per chunk wherever a slice fits one CTA.
                         FP64 slices beyond one CTA use clusters either way. */
+    int seq_stepper; /* kernel of the sequential chains (the coarsest solve and
+                        mgrit_serial_step): 0 (default) the fastest of those
+                        that fit, as timed when the workspaces are allocated;
+                        1: one CTA; 2: a thread-block cluster; 3: the grid
+                        stepper (split numerical flux).  A choice that does not
+                        fit this nx falls back to the default.  All of them
+                        perform the same floating-point operations per cell,
+                        so their results are bit-identical. */
 } mgrit_params;
 
 typedef struct {
@@ -218,14 +226,18 @@ int mgrit_fma_probe(int kind, int iters, int blocks_per_sm, double *flops_out, v
  *   norm_dev one device double that receives ||r||_2, with r as in
  *            mgrit_residual (caller-owned output)
  *   the other arguments as in mgrit_create / mgrit_params (dx = L/nx,
- *   dt = T/nt).
+ *   dt = T/nt), with two restrictions: scheme MGRIT_WENO5_SSPRK3 or
+ *   MGRIT_FO_FE (not MGRIT_LF_FE), and nx at most 8192 (the one-CTA FP64
+ *   slab; wider slices, which mgrit_residual steps on clusters, are refused).
  *
- * Returns MGRIT_EINVAL for bad arguments or when (nt/m + 1) * nx exceeds
- * MGRIT_STATIC_SCRATCH_DOUBLES (nothing is launched), MGRIT_ECUDA if a
- * launch fails.  Asynchronous on `stream`; the caller reads norm_dev after
+ * Returns MGRIT_EINVAL for bad arguments, for the cases above, or when
+ * (nt/m + 1) * nx exceeds MGRIT_STATIC_SCRATCH_DOUBLES (nothing is launched),
+ * MGRIT_ECUDA if a launch fails.  Asynchronous on `stream`; the caller reads norm_dev after
  * synchronising.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current): make that first
- * call before any stream capture.  Every call shares the one array, so calls
+ * address (cudaGetSymbolAddress, with that device current) and raises the
+ * kernel's shared-memory limit: make that first call before any stream
+ * capture.  Calls outside capture look the address up again, so the entry
+ * point keeps working after a device reset.  Every call shares the one array, so calls
  * that overlap on the GPU (other streams, other host threads) race; each
  * call overwrites every scratch value it reads before reading it, so no
  * state carries over between calls.
@@ -234,11 +246,35 @@ int mgrit_fma_probe(int kind, int iters, int blocks_per_sm, double *flops_out, v
 int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numflux, double T,
                           double L, const double *uC_dev, double *norm_dev, void *stream);
 
+/*
+ * Sequential stepping (the coarsest solve and mgrit_serial_step) runs, where
+ * it measured faster at allocation, on a grid of up to one CTA per SM that
+ * exchange boundary cells through global memory: once per Runge-Kutta stage
+ * each CTA waits for the values it reads (its neighbours' boundary cells and,
+ * with Burgers, every CTA's partial maximum of |f'|) (split numerical flux;
+ * mgrit_query 3).  Every wait is bounded (0.5 s): a wait that gives up ends
+ * the launch and sets a flag, which mgrit_solve reports as MGRIT_ETIMEOUT.
+ * This call synchronises `stream` and returns MGRIT_ETIMEOUT (clearing the
+ * flag) if a wait of an earlier asynchronous call on the context gave up,
+ * else MGRIT_OK.
+ */
+int mgrit_sync_status(mgrit_ctx *ctx, void *stream);
+
+/*
+ * Test hook for the bounded waits above: launches the grid stepper for one
+ * step with one CTA that never publishes its first stage, so the waits of the
+ * CTAs that read it run out (and then those of their readers); returns what
+ * mgrit_sync_status then returns (MGRIT_ETIMEOUT).  The context stays usable.  MGRIT_EINVAL if the context
+ * does not use the grid stepper.
+ */
+int mgrit_test_grid_timeout(mgrit_ctx *ctx, void *stream);
+
 /* Launch shape chosen for this context (for reports and tests):
  * what = 0: cells per thread of the slab kernel; 1: threads per CTA;
  * 2: CTAs per thread-block cluster used for sequential stepping (the
- * coarsest solve and mgrit_serial_step; 1 = a single CTA), known after the
- * first call that allocates (0 before); 100 + l (0 <= l <= levels-2): CTAs
+ * coarsest solve and mgrit_serial_step; 1 = a single CTA, 0 = the grid
+ * stepper), known after the first call that allocates (0 before);
+ * 3: CTAs of the grid stepper used for sequential stepping (0: not used); 100 + l (0 <= l <= levels-2): CTAs
  * per cluster of each relaxation / interpolation chunk of level l (1 = one
  * CTA per chunk; clusters are used where a level's chunks alone leave SMs
  * idle, and for FP64 slices beyond one CTA), 0 before the first allocating

@@ -294,13 +294,12 @@ struct AdjSlab {
             R w[CPT];
             F.fluxes(v);
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? v[c] + dt * F.A(c) : R(0);
+            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? RK<R>::euler(v[c], dt, F.A(c)) : R(0);
             F.store(w, st);
             F.fluxes(w);
-            const R q = R(0.25) * dt;
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                v[c] = (cell(c) < nx) ? R(0.75) * v[c] + R(0.25) * w[c] + q * F.A(c) : R(0);
+                v[c] = (cell(c) < nx) ? RK<R>::stage2(v[c], w[c], dt, F.A(c)) : R(0);
         }
         // stage 3: out = 1/3 u + 2/3 u2 + 2/3 dt A(u2)
         //   lam_u += 1/3 lam;  l2 = 2/3 lam + A'(u2)^T (dt l2_0), l2_0 = 2/3 lam

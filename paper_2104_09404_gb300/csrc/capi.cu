@@ -61,10 +61,12 @@ static bool choose_launch(int nx, int scheme, int flux, int f32, Launch *ln)
         const int cpt = CPT_VALUES[ci];
         const int need = (nx + cpt - 1) / cpt;
         if (need <= MAX_THREADS) {
-            const size_t smem = f32 ? slab_smem_bytes<float>(nx, cpt) : slab_smem_bytes<double>(nx, cpt);
+            const int threads = ((need + 31) / 32) * 32;
+            const size_t smem = f32 ? slab_smem_bytes<float>(nx, cpt, threads)
+                                    : slab_smem_bytes<double>(nx, cpt, threads);
             if (smem > 227 * 1024) return false;
             ln->cpt = cpt;
-            ln->threads = ((need + 31) / 32) * 32;
+            ln->threads = threads;
             ln->smem = smem;
             ln->slab = f32 ? table().slab32[scheme][flux][ci] : table().slab64[scheme][flux][ci];
             return ln->slab != nullptr;
@@ -92,6 +94,7 @@ extern "C" void mgrit_default_params(mgrit_params *p)
     p->precision = 64;
     p->coarse = MGRIT_COARSE_REDISC;
     p->chunk_clusters = 1;
+    p->seq_stepper = 0;
 }
 
 static int check_params(mgrit_ctx *ctx, const mgrit_params *p)
@@ -115,6 +118,8 @@ static int check_params(mgrit_ctx *ctx, const mgrit_params *p)
         return mgrit_fail(ctx, MGRIT_EINVAL, "coarse must be 0, 1 or 2");
     if (p->chunk_clusters != 0 && p->chunk_clusters != 1)
         return mgrit_fail(ctx, MGRIT_EINVAL, "chunk_clusters must be 0 or 1");
+    if (p->seq_stepper < 0 || p->seq_stepper > 3)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "seq_stepper must be 0, 1, 2 or 3");
     if (ctx && p->coarse != MGRIT_COARSE_REDISC && ctx->scheme != MGRIT_LF_FE)
         return mgrit_fail(ctx, MGRIT_EINVAL, "matched coarse integrators need the MGRIT_LF_FE scheme");
     if (ctx && ctx->scheme == MGRIT_LF_FE && p->precision != 64)
@@ -204,6 +209,14 @@ static void free_workspaces(mgrit_ctx *ctx)
     }
     cudaFree(ctx->u32c);
     cudaFree(ctx->ser32);
+    cudaFree(ctx->gbuf.part);
+    cudaFree(ctx->gbuf.halo);
+    cudaFree(ctx->gbuf.bar);
+    cudaFree(ctx->gbuf.err);
+    memset(&ctx->gbuf, 0, sizeof ctx->gbuf);
+    memset(&ctx->lg64, 0, sizeof ctx->lg64);
+    memset(&ctx->lg32, 0, sizeof ctx->lg32);
+    ctx->grid64 = ctx->grid32 = false;
     cudaFree(ctx->resid_rows);
     cudaFree(ctx->partials);
     cudaFree(ctx->d_norm);
@@ -232,7 +245,8 @@ extern "C" int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p)
                             ctx->p.cycle == p->cycle && ctx->p.guess == p->guess &&
                             ctx->p.numflux == p->numflux && ctx->p.precision == p->precision &&
                             ctx->p.coarse == p->coarse &&
-                            ctx->p.chunk_clusters == p->chunk_clusters;
+                            ctx->p.chunk_clusters == p->chunk_clusters &&
+                            ctx->p.seq_stepper == p->seq_stepper;
     const bool rechoose = ctx->alloc && ctx->p.chunk_clusters != p->chunk_clusters;
     if (ctx->alloc && (p->precision == 32) != (ctx->f32 != 0)) free_workspaces(ctx);
     ctx->p = *p;
@@ -362,6 +376,149 @@ static cudaError_t launch_seq(const ClusterLaunch &lc, const Launch &ln, cudaStr
     return launch_clusters(lc, 1, s, a);
 }
 
+// the grid stepper: barrier counter zeroed, then a cooperative launch (all G
+// CTAs co-resident, or the launch fails).  skip_cta >= 0 makes that CTA skip
+// the first barrier (the bounded-wait test hook).
+template <typename R>
+static cudaError_t launch_grid(const GridLaunch &lg, const GridBufs &gb, const SlabArgs<R> &a,
+                               cudaStream_t s, int skip_cta = -1)
+{
+    cudaError_t e = cudaMemsetAsync(gb.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    GridArgs<R> ga;
+    memset(&ga, 0, sizeof ga);
+    ga.a = a;
+    ga.gb = gb;
+    ga.skip_cta = skip_cta;
+    void *args[] = {&ga};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(lg.G);
+    cfg.blockDim = dim3(lg.threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, lg.fn, args);
+}
+
+// sequential stepping of a context in FP64 (f32 = 0) or FP32: the grid
+// stepper where it was chosen and the split flux is in use, else the cluster
+// or one-CTA stepper
+template <typename R>
+static cudaError_t launch_seq_ctx(const mgrit_ctx *ctx, const SlabArgs<R> &a, cudaStream_t s)
+{
+    const bool f32 = sizeof(R) == 4;
+    const GridLaunch &lg = f32 ? ctx->lg32 : ctx->lg64;
+    const ClusterLaunch &lc = f32 ? ctx->lc32 : ctx->lc64;
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    const int want = ctx->p.seq_stepper;
+    const bool grid_ok = lg.fn && ctx->p.numflux == MGRIT_LF_SPLIT;
+    SlabArgs<R> b = a;
+    if (want == 1 && ln.slab) return launch1(ln.slab, 1, ln, s, &b);
+    if (want == 2 && lc.fn) return launch_clusters(lc, 1, s, &b);
+    if (grid_ok && (want == 3 || (f32 ? ctx->grid32 : ctx->grid64))) return launch_grid(lg, ctx->gbuf, a, s);
+    return launch_seq(lc, ln, s, &b);
+}
+
+// true (and the flag cleared) if a grid-stepper wait gave up since the
+// last check; call after the stream's work has completed
+static bool grid_timed_out(mgrit_ctx *ctx)
+{
+    if (!ctx->gbuf.err) return false;
+    int err = 0;
+    if (cudaMemcpy(&err, ctx->gbuf.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    if (err) cudaMemset(ctx->gbuf.err, 0, sizeof(int));
+    return err != 0;
+}
+
+// Grid stepper shape for sequential stepping, chosen by timing: candidates
+// of G = SMs, SMs/2, SMs/4, ... CTAs (8 to 127 cells each, a lane pair per
+// interface, co-resident) against the cluster / one-CTA stepper, 16 steps each on a zero
+// state (the work does not depend on the data); the fastest is kept.  Split
+// numerical flux, WENO5 or first order, nx >= 512.
+template <typename R>
+static int choose_grid(mgrit_ctx *ctx, GridLaunch *lg, bool *faster, R *row)
+{
+    memset(lg, 0, sizeof *lg);
+    *faster = false;
+    const bool f32 = sizeof(R) == 4;
+    if (ctx->scheme == MGRIT_LF_FE || ctx->nx < 512 || !row) return MGRIT_OK;
+    const void *fn = f32 ? table().grid32[ctx->scheme][ctx->flux] : table().grid64[ctx->scheme][ctx->flux];
+    if (!fn) return MGRIT_OK;
+    const int nx = ctx->nx;
+    cudaStream_t s = ctx->cap;
+    CK(cudaMemsetAsync(row, 0, sizeof(R) * nx, s));
+    SlabArgs<R> a;
+    memset(&a, 0, sizeof a);
+    a.mode = MODE_SEQ;
+    a.nx = nx;
+    a.numflux = MGRIT_LF_SPLIT;
+    a.dxinv = (R)(nx / ctx->p.L);
+    a.dt = (R)ctx->dt_l[0];
+    a.src = row;
+    a.out = row;
+    const int steps = 16;
+    auto time_ms = [&](auto launch) -> float {
+        a.nsteps = 2;
+        if (launch() != cudaSuccess) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        a.nsteps = steps;
+        cudaEventRecord(ctx->ev0, s);
+        if (launch() != cudaSuccess) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        cudaEventRecord(ctx->ev1, s);
+        if (cudaEventSynchronize(ctx->ev1) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        float ms = -1.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        return ms;
+    };
+    const ClusterLaunch &lc = f32 ? ctx->lc32 : ctx->lc64;
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    float other = -1.f, best = -1.f;
+    if (lc.fn || ln.slab) other = time_ms([&] {
+        SlabArgs<R> b = a;
+        return launch_seq(lc, ln, s, &b);
+    });
+    int nb = 0;
+    for (int G = ctx->nsm < GRID_MAX ? ctx->nsm : GRID_MAX; G >= 8; G /= 2) {
+        const int n = (nx + G - 1) / G;
+        if (n < 8 || nx / G < 8) continue;
+        const int threads = ((2 * (n + 1) + 31) / 32) * 32;   // a lane pair per interface
+        if (threads > GRID_THREADS) break;   // fewer CTAs would only be larger
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess ||
+            (long long)nb * ctx->nsm < G) {
+            cudaGetLastError();
+            continue;
+        }
+        const GridLaunch cand{fn, G, threads};
+        const float ms = time_ms([&] { return launch_grid(cand, ctx->gbuf, a, s); });
+        if (ms > 0.f && (best < 0.f || ms < best)) {
+            best = ms;
+            *lg = cand;
+        }
+    }
+    *faster = lg->fn && (other < 0.f || best < other);
+    // a wait that gave up during the choice would leave the error flag set
+    int err = 0;
+    CK(cudaMemcpy(&err, ctx->gbuf.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        memset(lg, 0, sizeof *lg);
+        *faster = false;
+        CK(cudaMemset(ctx->gbuf.err, 0, sizeof(int)));
+    }
+    return MGRIT_OK;
+}
+
 int mgrit_ensure_alloc(mgrit_ctx *ctx)
 {
     if (ctx->alloc) return MGRIT_OK;
@@ -400,6 +557,25 @@ int mgrit_ensure_alloc(mgrit_ctx *ctx)
     CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     choose_cluster(ctx, 0, &ctx->lc64);
     if (ctx->f32) choose_cluster(ctx, 1, &ctx->lc32);
+    CK(cudaMalloc((void **)&ctx->gbuf.part, sizeof(double) * 2 * GRID_MAX));
+    CK(cudaMalloc((void **)&ctx->gbuf.halo, sizeof(double) * 2 * GRID_MAX * 6));
+    CK(cudaMalloc((void **)&ctx->gbuf.bar, sizeof(unsigned)));
+    CK(cudaMalloc((void **)&ctx->gbuf.err, sizeof(int)));
+    CK(cudaMemset(ctx->gbuf.err, 0, sizeof(int)));
+    // the grid stepper's choice times launches on rows the solve overwrites
+    // later: FP64 on the level-0 C-point row buffer (FP64 mode) or a fresh
+    // FP64 row, FP32 on the FP32 serial row
+    if (!ctx->f32) {
+        if ((st = choose_grid<double>(ctx, &ctx->lg64, &ctx->grid64, static_cast<double *>(ctx->newC[0]))))
+            return st;
+    } else {
+        double *tmp = nullptr;
+        CK(cudaMalloc((void **)&tmp, sizeof(double) * ctx->nx));
+        st = choose_grid<double>(ctx, &ctx->lg64, &ctx->grid64, tmp);
+        cudaFree(tmp);
+        if (st) return st;
+        if ((st = choose_grid<float>(ctx, &ctx->lg32, &ctx->grid32, ctx->ser32))) return st;
+    }
     if (!ctx->ln64.slab && !ctx->lc64.fn)
         return mgrit_fail(ctx, MGRIT_EINVAL, "no FP64 slab or cluster fits nx = %d for the coarsest solve",
                     ctx->nx);
@@ -536,7 +712,7 @@ static cudaError_t enqueue_coarse(mgrit_ctx *ctx, cudaStream_t s)
 {
     const int l = ctx->L - 1;
     SlabArgs<double> a = coarse_args(ctx);
-    cudaError_t e = launch_seq(ctx->lc64, ctx->ln64, s, &a);
+    cudaError_t e = launch_seq_ctx(ctx, a, s);
     if (e != cudaSuccess || !ctx->f32) return e;
     return launch_convert(ctx->u[l], 0, ctx->u32c, 1, (long long)(ctx->nt_l[l] + 1) * ctx->nx, s);
 }
@@ -626,7 +802,15 @@ static int ensure_graphs(mgrit_ctx *ctx)
 {
     int st;
     if (!ctx->gA && (st = capture(ctx, enqueue_part_a, &ctx->gA))) return st;
-    if (!ctx->gB && (st = capture(ctx, enqueue_part_b, &ctx->gB))) return st;
+    if (!ctx->gB && (st = capture(ctx, enqueue_part_b, &ctx->gB))) {
+        // a graph that the cooperative grid stepper cannot be captured into:
+        // the coarsest solve falls back to the cluster / one-CTA stepper
+        if (!ctx->lg64.fn) return st;
+        cudaGetLastError();
+        ctx->lg64.fn = nullptr;
+        ctx->grid64 = false;
+        if ((st = capture(ctx, enqueue_part_b, &ctx->gB))) return st;
+    }
     return MGRIT_OK;
 }
 
@@ -734,6 +918,9 @@ extern "C" int mgrit_solve(mgrit_ctx *ctx, const double *u0_dev, double *uC_out_
     if (uT_out_dev && (st = copy_out(ctx, uT_out_dev, ctx->nC_l[0], 1, s))) return st;
     CK(cudaStreamSynchronize(s));
     ctx->have_state = true;
+    // a grid-stepper wait that gave up (coarsest solve) makes the solve's
+    // values meaningless: report it
+    if (grid_timed_out(ctx)) status = MGRIT_ETIMEOUT;
     if (stats) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
@@ -743,6 +930,7 @@ extern "C" int mgrit_solve(mgrit_ctx *ctx, const double *u0_dev, double *uC_out_
         stats->cell_updates = updates;
         stats->stagnated = stagnated;
     }
+    if (status == MGRIT_ETIMEOUT) mgrit_fail(ctx, status, "a grid-stepper wait gave up");
     if (status == MGRIT_EDIVERGED) mgrit_fail(ctx, status, "diverged at cycle %d", k);
     if (status == MGRIT_ENOTCONV) mgrit_fail(ctx, status, "not converged after %d cycles", k);
     return status;
@@ -783,7 +971,7 @@ extern "C" int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *u
         a.src = u0_dev;
         a.out = uT_dev;
         a.nsteps = nsteps;
-        CK(launch_seq(ctx->lc64, ctx->ln64, s, &a));
+        CK(launch_seq_ctx(ctx, a, s));
         return MGRIT_OK;
     }
     // FP32 sweeps: step an FP32 copy of u0 and widen the result
@@ -792,9 +980,33 @@ extern "C" int mgrit_serial_step(mgrit_ctx *ctx, const double *u0_dev, double *u
     a.src = ctx->ser32;
     a.out = ctx->ser32;
     a.nsteps = nsteps;
-    CK(launch_seq(ctx->lc32, ctx->ln32, s, &a));
+    CK(launch_seq_ctx(ctx, a, s));
     CK(launch_convert(ctx->ser32, 1, uT_dev, 0, ctx->nx, s));
     return MGRIT_OK;
+}
+
+extern "C" int mgrit_sync_status(mgrit_ctx *ctx, void *stream)
+{
+    if (!ctx) return MGRIT_EINVAL;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (grid_timed_out(ctx))
+        return mgrit_fail(ctx, MGRIT_ETIMEOUT, "a grid-stepper wait gave up");
+    return MGRIT_OK;
+}
+
+extern "C" int mgrit_test_grid_timeout(mgrit_ctx *ctx, void *stream)
+{
+    if (!ctx) return MGRIT_EINVAL;
+    int st;
+    if ((st = mgrit_ensure_alloc(ctx))) return st;
+    if (!ctx->lg64.fn) return mgrit_fail(ctx, MGRIT_EINVAL, "this context steps without the grid stepper");
+    cudaStream_t s = (cudaStream_t)stream;
+    SlabArgs<double> a = base_args<double>(ctx, MODE_SEQ, 0);
+    a.src = static_cast<const double *>(ctx->newC[0]);
+    a.out = nullptr;
+    a.nsteps = 1;
+    CK(launch_grid(ctx->lg64, ctx->gbuf, a, s, 0));
+    return mgrit_sync_status(ctx, stream);
 }
 
 extern "C" int mgrit_residual(mgrit_ctx *ctx, const double *uC_dev, double *norm_out, void *stream)
@@ -873,7 +1085,19 @@ extern "C" int mgrit_query(const mgrit_ctx *ctx, int what)
     switch (what) {
     case 0: return ln.cpt;
     case 1: return ln.threads;
-    case 2: return ctx->alloc ? (lc.fn ? lc.K : 1) : 0;
+    case 2:     // CTAs of the cluster the sequential chains use (1: one CTA; 0: the grid stepper)
+    case 3: {   // CTAs of the grid stepper the sequential chains use (0: not used)
+        if (!ctx->alloc) return 0;
+        const GridLaunch &lg = f32 ? ctx->lg32 : ctx->lg64;
+        const int want = ctx->p.seq_stepper;
+        const bool grid = lg.fn && ctx->p.numflux == MGRIT_LF_SPLIT &&
+                          !(want == 1 && ln.slab) && !(want == 2 && lc.fn) &&
+                          (want == 3 || (f32 ? ctx->grid32 : ctx->grid64));
+        if (what == 3) return grid ? lg.G : 0;
+        if (grid) return 0;
+        if (want == 1 && ln.slab) return 1;
+        return lc.fn ? lc.K : 1;
+    }
     default:
         if (what >= 100 && what < 100 + ctx->L - 1) {   // level what-100 relaxation / interpolation
             if (!ctx->alloc) return 0;
@@ -1041,7 +1265,7 @@ struct SlabGroups {
             L.fn = sizeof(R) == 4 ? btable().slab32[flux][cpt_index(cpt)]
                                   : btable().slab64[flux][cpt_index(cpt)];
             L.threads = std::get<2>(kv.first);
-            L.smem = slab_smem_bytes<R>(grp.nx_max, cpt);
+            L.smem = slab_smem_bytes<R>(grp.nx_max, cpt, L.threads);
             L.nblocks = (int)grp.map.size();
             SlabArgs<R> *da;
             int st;

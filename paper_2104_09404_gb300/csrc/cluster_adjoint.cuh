@@ -269,13 +269,12 @@ struct ClusterAdj {
             R w[CPT];
             F.fluxes(v, (stage++) & 1);
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < F.n) ? v[c] + dt * F.A(c) : R(0);
+            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < F.n) ? RK<R>::euler(v[c], dt, F.A(c)) : R(0);
             F.store(w, st);
             F.fluxes(w, (stage++) & 1);
-            const R q = R(0.25) * dt;
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                v[c] = (cell(c) < F.n) ? R(0.75) * v[c] + R(0.25) * w[c] + q * F.A(c) : R(0);
+                v[c] = (cell(c) < F.n) ? RK<R>::stage2(v[c], w[c], dt, F.A(c)) : R(0);
         }
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {

@@ -81,6 +81,22 @@ struct ClusterSlab {
                              MGRIT_SH(q, s, lim()), MGRIT_SH(q, s - 1, lim()));
     }
 
+    // F_{i+1/2} of the split form at local slot s = i + GHOST: the windowed
+    // WENO5 expressions of slab.cuh (one window per interface), or first order
+    __device__ __forceinline__ R split_flux(const R *fp, const R *fm, int s) const
+    {
+        if (SCHEME == SCH_FO_FE) return MGRIT_SH(fp, s, lim()) + MGRIT_SH(fm, s + 1, lim());
+        const int L = lim();
+        WenoWin<R> P;
+        P.init(MGRIT_SH(fp, s - 2, L), MGRIT_SH(fp, s - 1, L), MGRIT_SH(fp, s, L), MGRIT_SH(fp, s + 1, L),
+               MGRIT_SH(fp, s + 2, L));
+        if (FLUX == FLX_ADVECTION) return split_flux_win_adv(P, MGRIT_SH(fp, s, L));
+        WenoWin<R> M;
+        M.init(MGRIT_SH(fm, s - 1, L), MGRIT_SH(fm, s, L), MGRIT_SH(fm, s + 1, L), MGRIT_SH(fm, s + 2, L),
+               MGRIT_SH(fm, s + 3, L));
+        return split_flux_win(P, M, MGRIT_SH(fp, s, L), MGRIT_SH(fm, s + 1, L));
+    }
+
     // global max of v over the cluster (publishes this CTA's partial in part[buf])
     __device__ __forceinline__ R cluster_max(R v, int buf)
     {
@@ -133,13 +149,23 @@ struct ClusterSlab {
                 alpha = cluster_max(v, buf);
             }
             R *fp = arr(buf, 0), *fm = arr(buf, 1);
+            // the one-CTA slab's split fluxes, formed the same way: WENO5 on
+            // q = f^{+/-}/2 (q^- = 0 for advection), first order on f^{+/-}
+            const R a4 = R(0.25) * alpha, h = R(0.5) * alpha;
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < n) {
-                    const R f = phys_flux<FLUX>(w[c]);
-                    const R p = R(0.5) * (f + alpha * w[c]);
-                    const R q = R(0.5) * (f - alpha * w[c]);
+                    const R x = w[c];
+                    R p, q;
+                    if (SCHEME == SCH_WENO5_SSPRK3) {
+                        p = FLUX == FLX_BURGERS ? Ar<R>::mul(Ar<R>::fma(R(0.125), x, a4), x) : R(0.5) * x;
+                        q = FLUX == FLX_BURGERS ? Ar<R>::mul(Ar<R>::fma(R(0.125), x, -a4), x) : R(0);
+                    } else {
+                        const R f2 = R(0.5) * phys_flux<FLUX>(x);
+                        p = fma(h, x, f2);
+                        q = fma(-h, x, f2);
+                    }
                     MGRIT_SH(fp, i + GHOST, lim()) = p;
                     MGRIT_SH(fm, i + GHOST, lim()) = q;
                 }
@@ -149,11 +175,10 @@ struct ClusterSlab {
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
-                if (i < n)
-                    MGRIT_SH(qf, i + 1, nmax + 2) = rec_minus(fp, i + GHOST) + rec_plus(fm, i + GHOST);
+                if (i < n) MGRIT_SH(qf, i + 1, nmax + 2) = split_flux(fp, fm, i + GHOST);
             }
             if (threadIdx.x == blockDim.x - 1)   // left boundary interface
-                qf[0] = rec_minus(fp, GHOST - 1) + rec_plus(fm, GHOST - 1);
+                qf[0] = split_flux(fp, fm, GHOST - 1);
         } else if (numflux == NF_ROE) {
             // local per interface: one cluster barrier per stage, as for advection
             R *wa = arr(buf, 0);
@@ -213,7 +238,7 @@ struct ClusterSlab {
     __device__ __forceinline__ R A(int c) const
     {
         const int i = cell(c);
-        return -(MGRIT_SH(qf, i + 1, nmax + 2) - MGRIT_SH(qf, i, nmax + 2)) * dxinv;
+        return RK<R>::A(Ar<R>::sub(MGRIT_SH(qf, i + 1, nmax + 2), MGRIT_SH(qf, i, nmax + 2)), dxinv);
     }
 
     // u <- Phi(u); stage buffers alternate with the global stage counter
@@ -223,23 +248,21 @@ struct ClusterSlab {
             fluxes(u, (stage++) & 1);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < n) u[c] = u[c] + dt * A(c);
+                if (cell(c) < n) u[c] = RK<R>::euler(u[c], dt, A(c));
             return;
         }
         R w[CPT];
         fluxes(u, (stage++) & 1);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < n) ? u[c] + dt * A(c) : R(0);
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < n) ? RK<R>::euler(u[c], dt, A(c)) : R(0);
         fluxes(w, (stage++) & 1);
-        const R q = R(0.25) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) w[c] = R(0.75) * u[c] + R(0.25) * w[c] + q * A(c);
+            if (cell(c) < n) w[c] = RK<R>::stage2(u[c], w[c], dt, A(c));
         fluxes(w, (stage++) & 1);
-        const R t = R(2.0 / 3.0) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * w[c] + t * A(c);
+            if (cell(c) < n) u[c] = RK<R>::stage3(u[c], w[c], dt, A(c));
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *row) const

@@ -7,6 +7,7 @@
 #include <cstdio>
 
 #include "../../include/mgrit.h"
+#include "grid_seq.cuh"
 
 namespace mgrit {
 
@@ -33,6 +34,13 @@ struct ClusterLaunch {
     int cpt;            // cells per thread (1 or 2)
     int threads;
     size_t smem;
+};
+
+// sequential stepping on a cooperative grid of G CTAs (k_seq_grid)
+struct GridLaunch {
+    const void *fn;     // null: not used (cluster or one-CTA stepper instead)
+    int G;              // CTAs
+    int threads;
 };
 
 struct AdjWork;   // adjoint workspaces (capi_adjoint.cu), allocated on first use
@@ -94,6 +102,11 @@ struct mgrit_ctx {
     double dt_l[mgrit::MAXLEV];
     mgrit::Launch ln64, ln32;
     mgrit::ClusterLaunch lc64, lc32;
+    // grid-wide sequential stepping, chosen by timing against the cluster
+    // stepper when the workspaces are allocated (fn null: cluster / one CTA)
+    mgrit::GridLaunch lg64, lg32;   // fastest grid shape (fn null: none fits)
+    bool grid64, grid32;            // the grid stepper timed faster than the others
+    mgrit::GridBufs gbuf;
     // relaxation / interpolation of level l on clusters (fn null: one CTA per
     // chunk), chosen when the workspaces are allocated
     mgrit::ClusterLaunch lr64[mgrit::MAXLEV], lr32[mgrit::MAXLEV];

@@ -1,6 +1,7 @@
 // Table of kernel instances, indexed by [scheme][flux][cells-per-thread].
 #pragma once
 #include "cluster_relax.cuh"
+#include "grid_seq.cuh"
 
 namespace mgrit {
 
@@ -22,6 +23,8 @@ struct KernelTable {
     const void *seqc32[2][2][2];
     const void *relc64[2][2][NCPT_RELAXC];   // k_slab_cluster, cells per thread 1, 2, 4
     const void *relc32[2][2][NCPT_RELAXC];
+    const void *grid64[2][2];   // k_seq_grid [scheme][flux] (WENO5 / first order, split flux)
+    const void *grid32[2][2];
 };
 
 template <typename R, int S, int F>
@@ -71,9 +74,11 @@ void fill_f64_relaxc_burgers(KernelTable &t);
 void fill_f64_relaxc_advection(KernelTable &t);
 void fill_f32_relaxc_burgers(KernelTable &t);
 void fill_f32_relaxc_advection(KernelTable &t);
+void fill_grid(KernelTable &t);
 
 inline void fill_all(KernelTable &t)
 {
+    fill_grid(t);
     fill_f64_weno_burgers(t);
     fill_f64_weno_advection(t);
     fill_f64_weno_cluster(t);

@@ -23,46 +23,90 @@ namespace {
 // Phi^m rows: (nt/m + 1) x nx doubles at most; then the norm partials.
 constexpr size_t ROWS_MAX = (size_t)MGRIT_STATIC_SCRATCH_DOUBLES;
 constexpr size_t PARTIALS_MAX = 2048;
+constexpr int MGRIT_NSCHEME_STATIC = 2;   // WENO5 + SSPRK3, first order + FE
 
 static __device__ __align__(256) double g_static_scratch[ROWS_MAX + PARTIALS_MAX];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
-double *g_scratch_addr[MAX_DEVICES];   // device address of g_static_scratch, per device
+// per device: the device address of g_static_scratch, and the kernel
+// instances whose shared-memory limit this file has raised
+struct DeviceSetup {
+    double *scratch;
+    const void *raised[MGRIT_NSCHEME_STATIC][2][NCPT64];
+};
+DeviceSetup g_dev[MAX_DEVICES];
 
-// Host code may not use &g_static_scratch (that is a host-side stand-in);
-// the device address is looked up once per device with it current.
-cudaError_t scratch_address(double **out)
+const KernelTable &kernels()
+{
+    static const KernelTable t = [] {
+        KernelTable k;
+        memset(&k, 0, sizeof k);
+        fill_all(k);
+        return k;
+    }();
+    return t;
+}
+
+// Device address of the scratch array for the current device.  Host code may
+// not use &g_static_scratch (that is a host-side stand-in); the address is
+// looked up with the device current.  Outside stream capture it is looked up
+// again on every call, so that a context re-created after a device reset
+// (which loads the module, and the array, anew) gets its new address; during
+// capture the cached address is used.  The per-device record of raised
+// kernel attributes is dropped when the address changes.
+cudaError_t scratch_address(cudaStream_t s, double **out, int *dev_out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    DeviceSetup &d = g_dev[dev];
+    if (cs == cudaStreamCaptureStatusNone || !d.scratch) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
+        if (static_cast<double *>(p) != d.scratch) {
+            memset(&d, 0, sizeof d);
+            d.scratch = static_cast<double *>(p);
+        }
     }
-    *out = g_scratch_addr[dev];
+    *out = d.scratch;
+    *dev_out = dev;
     return cudaSuccess;
 }
 
-const void *select_slab(int nx, int scheme, int flux, int *threads, int *cpt)
+// the FP64 one-CTA slab for (scheme, flux, nx): the smallest cells per
+// thread giving at most MAX_THREADS threads
+const void *select_slab(int nx, int scheme, int flux, int *threads, int *cpt, int *ci_out)
 {
-    KernelTable t;
-    memset(&t, 0, sizeof t);
-    fill_all(t);
     for (int ci = 0; ci < NCPT64; ++ci) {
         const int need = (nx + CPT_VALUES[ci] - 1) / CPT_VALUES[ci];
         if (need <= MAX_THREADS) {
             *threads = ((need + 31) / 32) * 32;
             *cpt = CPT_VALUES[ci];
-            return t.slab64[scheme][flux][ci];
+            *ci_out = ci;
+            return kernels().slab64[scheme][flux][ci];
         }
     }
     return nullptr;
+}
+
+// raise the kernel's dynamic shared-memory limit to the opt-in maximum once
+// per device (not to this launch's size: the kernel instance is shared with
+// solver contexts whose slices may be wider)
+cudaError_t raise_smem_once(int dev, int scheme, int flux, int ci, const void *slab)
+{
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    const void *&done = g_dev[dev].raised[scheme][flux][ci];
+    if (done == slab) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(slab, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess) done = slab;
+    return e;
 }
 
 }  // namespace
@@ -81,24 +125,21 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     if (!(T > 0) || !(L > 0) || !std::isfinite(T) || !std::isfinite(L)) return MGRIT_EINVAL;
     const int nC = nt / m;
     if ((size_t)(nC + 1) * (size_t)nx > ROWS_MAX) return MGRIT_EINVAL;   // beyond the scratch
-    int threads = 0, cpt = 0;
-    const void *slab = select_slab(nx, scheme, flux, &threads, &cpt);
+    int threads = 0, cpt = 0, ci = 0;
+    const void *slab = select_slab(nx, scheme, flux, &threads, &cpt, &ci);
     if (!slab) return MGRIT_EINVAL;
-    const size_t smem = slab_smem_bytes<double>(nx, cpt);
+    const size_t smem = slab_smem_bytes<double>(nx, cpt, threads);
     if (smem > 227 * 1024) return MGRIT_EINVAL;
     const int blocks = restrict_blocks(nC, nx);
     if ((size_t)blocks > PARTIALS_MAX) return MGRIT_EINVAL;
 
+    cudaStream_t s = (cudaStream_t)stream;
     double *scratch = nullptr;
-    if (scratch_address(&scratch) != cudaSuccess) return MGRIT_ECUDA;
+    int dev = 0;
+    if (scratch_address(s, &scratch, &dev) != cudaSuccess) return MGRIT_ECUDA;
     double *rows = scratch;
     double *partials = scratch + ROWS_MAX;
-    cudaStream_t s = (cudaStream_t)stream;
-    // the opt-in maximum, not this launch's size: the kernel instance is shared
-    // with solver contexts whose slices may be wider
-    if (cudaFuncSetAttribute(slab, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-        cudaSuccess)
-        return MGRIT_ECUDA;
+    if (raise_smem_once(dev, scheme, flux, ci, slab) != cudaSuccess) return MGRIT_ECUDA;
 
     // rows 1..nC <- Phi_0^m(uC row j-1); every row and partial read below is
     // written first by this call, so nothing needs clearing
@@ -117,8 +158,19 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     a.phirow = rows;
     a.nrows_uC = a.nrows_phirow = nC + 1;
     void *args[] = {&a};
-    if (cudaLaunchKernel(slab, dim3(nC), dim3(threads), args, smem, s) != cudaSuccess)
-        return MGRIT_ECUDA;
+    cudaError_t le = cudaLaunchKernel(slab, dim3(nC), dim3(threads), args, smem, s);
+    if (le == cudaErrorInvalidValue && smem > 48 * 1024) {
+        // the limit raised earlier no longer holds (a device reset that
+        // kept the array's address): raise it again and retry once
+        cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> lock(g_setup_mutex);
+            g_dev[dev].raised[scheme][flux][ci] = nullptr;
+        }
+        if (raise_smem_once(dev, scheme, flux, ci, slab) != cudaSuccess) return MGRIT_ECUDA;
+        le = cudaLaunchKernel(slab, dim3(nC), dim3(threads), args, smem, s);
+    }
+    if (le != cudaSuccess) return MGRIT_ECUDA;
 
     RestrictArgs r;
     memset(&r, 0, sizeof r);

@@ -354,13 +354,11 @@ struct WenoWin {
 //   F = 2 (q^+_i + q^-_{i+1}) + (N^+ D^- - N^- D^+) / (3 D^+ D^-)
 // with one division in FP64 (each D lies in [1e-23, 1e33] for |q| <= 1e3, so
 // the product stays far inside the FP64 range) and two in FP32
+// the combination of the two reconstructions' (N, D) and base values
 template <typename V>
-__device__ __forceinline__ V split_flux_win(const WenoWin<V> &P, const WenoWin<V> &M, V qp, V qm)
+__device__ __forceinline__ V split_flux_combine(V Np, V Dp, V Nm, V Dm, V qp, V qm)
 {
     using A = Ar<V>;
-    V Np, Dp, Nm, Dm;
-    P.left(Np, Dp);
-    M.right(Nm, Dm);
     const V base = A::add(qp, qm);
     if constexpr (std::is_same<V, double>::value) {
         const V num = A::fma(Np, Dm, A::neg(A::mul(Nm, Dp)));
@@ -370,6 +368,15 @@ __device__ __forceinline__ V split_flux_win(const WenoWin<V> &P, const WenoWin<V
         const V fr = A::sub(A::div(Np, A::mul(A::k(3.0), Dp)), A::div(Nm, A::mul(A::k(3.0), Dm)));
         return A::fma(A::k(2.0), base, fr);
     }
+}
+
+template <typename V>
+__device__ __forceinline__ V split_flux_win(const WenoWin<V> &P, const WenoWin<V> &M, V qp, V qm)
+{
+    V Np, Dp, Nm, Dm;
+    P.left(Np, Dp);
+    M.right(Nm, Dm);
+    return split_flux_combine(Np, Dp, Nm, Dm, qp, qm);
 }
 
 // advection (alpha = 1): f^- = (u - u)/2 is zero, so its reconstruction is
@@ -382,6 +389,39 @@ __device__ __forceinline__ V split_flux_win_adv(const WenoWin<V> &P, V qp)
     P.left(Np, Dp);
     return A::fma(A::k(2.0), qp, A::div(Np, A::mul(A::k(3.0), Dp)));
 }
+
+// Runge-Kutta stage updates of Eq. (SSPRK3) and forward Euler (Eq. SSPRK1)
+// from the flux difference dF = F_{i+1/2} - F_{i-1/2} of a cell, with
+// explicit rounding: the one-CTA slab, the cluster stepper and the grid
+// stepper perform the same operations, so a chain of steps gives the same
+// bits on each of them.
+//  - FP64: the Shu-Osher combinations as written, 3/4 u + 1/4 w + 1/4 dt A
+//    and 1/3 u + 2/3 w + 2/3 dt A (closest to the oracle's operation order);
+//  - FP32: the same combinations in increment form, u + 1/4 ((w - u) + dt A)
+//    and u + 2/3 ((w - u) + dt A), which round the state once per stage
+//    (w - u and the increment are small and nearly exact): over the 65536
+//    steps of the largest workload this halves the drift from FP64 stepping.
+template <typename R>
+struct RK {
+    using A_ = Ar<R>;
+    static constexpr bool INC = sizeof(R) == 4;
+    // A_i = -(F_{i+1/2} - F_{i-1/2}) / dx
+    static __device__ __forceinline__ R A(R dF, R dxinv) { return A_::mul(A_::neg(dxinv), dF); }
+    // u + dt A (forward Euler; the first SSPRK3 stage)
+    static __device__ __forceinline__ R euler(R u, R dt, R a) { return A_::fma(dt, a, u); }
+    // 3/4 u + 1/4 w + 1/4 dt A
+    static __device__ __forceinline__ R stage2(R u, R w, R dt, R a)
+    {
+        if (INC) return A_::fma(R(0.25), A_::fma(dt, a, A_::sub(w, u)), u);
+        return A_::fma(R(0.75), u, A_::fma(R(0.25), w, A_::mul(A_::mul(R(0.25), dt), a)));
+    }
+    // 1/3 u + 2/3 w + 2/3 dt A
+    static __device__ __forceinline__ R stage3(R u, R w, R dt, R a)
+    {
+        if (INC) return A_::fma(R(2.0 / 3.0), A_::fma(dt, a, A_::sub(w, u)), u);
+        return A_::fma(R(1.0 / 3.0), u, A_::fma(R(2.0 / 3.0), w, A_::mul(A_::mul(R(2.0 / 3.0), dt), a)));
+    }
+};
 
 template <typename R, int SCHEME, int FLUX, int CPT>
 struct Slab {
@@ -401,24 +441,47 @@ struct Slab {
     R psiDt;
     static constexpr int kScheme = SCHEME, kCpt = CPT;
 
-    // FP32 slabs pad the shared arrays with one slot after every CPT slots:
-    // thread t reads the window of interfaces t*CPT.., i.e. lanes CPT slots
-    // apart, and CPT + 1 slots apart spread over distinct banks.  FP64 slabs
-    // are bound by the FP64 pipe, not by shared memory, and keep the plain
-    // layout (the adjoint slab overlays it).
-    static constexpr bool PAD = sizeof(R) == 4 && CPT >= 2;
-    static __host__ __device__ __forceinline__ int phys(int s) { return PAD ? s + s / CPT : s; }
-    static __host__ __device__ __forceinline__ int extent(int nx) { return phys(nx + 2 * GHOST - 1) + 1; }
+    // Shared-array layout.  FP64 slabs keep cell i (i = -3 .. nx+2) at slot
+    // i + GHOST: they are bound by the FP64 pipe, not by shared memory, and
+    // the adjoint slab overlays that layout.  FP32 slabs with CPT >= 2 use a
+    // run-major layout: the window pass gives thread t the run of interfaces
+    // t*CPT .. t*CPT + CPT - 1, and cell i sits at slot k * P + r with
+    // r = (i + RO*CPT) / CPT (its run, after RO runs of left ghosts) and
+    // k = (i + RO*CPT) mod CPT.  Lanes reading element k of consecutive runs
+    // then touch consecutive slots, and a window step is a constant offset;
+    // P = 32/CPT (mod 32) keeps the interleaved writes of 32 consecutive
+    // cells on 32 distinct banks too.  The interface flux F_{i+1/2} is kept at
+    // cell i of qf (F_{-1/2} at cell -1).
+    static constexpr bool TL = sizeof(R) == 4 && CPT >= 2;
+    static constexpr int LOG = CPT >= 32 ? 5 : CPT >= 16 ? 4 : CPT >= 8 ? 3 : CPT >= 4 ? 2 : CPT >= 2 ? 1 : 0;
+    static constexpr int RO = CPT >= 4 ? 1 : 2;
+    // run stride of the FP32 layout for a CTA of T threads
+    static __host__ __device__ __forceinline__ int run_stride(int T)
+    {
+        const int r0 = (32 / CPT) % 32;
+        int P = T + RO + 2;
+        P += ((r0 - P % 32) % 32 + 32) % 32;
+        return P;
+    }
+    // elements of each of qa, qb, qf
+    static __host__ __device__ __forceinline__ int extent(int nx, int T)
+    {
+        return TL ? CPT * run_stride(T) : nx + 2 * GHOST;
+    }
 
-    int pstride;  // slots between a thread's consecutive interleaved cells
+    int P;        // run stride (FP32 layout)
+    int E;        // elements per array
+    int pstride;  // slot distance between a thread's consecutive interleaved cells
 
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
         : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))
     {
-        // blockDim.x is a multiple of 32, hence of CPT, so the padded slot of
-        // cell t + c*blockDim.x + o is phys(t + o) + c * pstride
-        pstride = PAD ? (int)blockDim.x + (int)blockDim.x / CPT : (int)blockDim.x;
-        const int E = extent(nx);
+        const int T = (int)blockDim.x;
+        P = TL ? run_stride(T) : 0;
+        E = extent(nx, T);
+        // blockDim.x is a multiple of 32, hence of CPT: cell t + c*T + o sits at
+        // sl(t + o) + c * pstride
+        pstride = TL ? T / CPT : T;
         qa = reinterpret_cast<R *>(smem);
         qb = qa + E;
         qf = qb + E;
@@ -428,18 +491,24 @@ struct Slab {
     static constexpr int RECON_UNROLL = sizeof(R) == 4 ? 1 : CPT;
 
     __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
-    __device__ __forceinline__ int lim() const { return extent(nx); }   // extent of qa, qb, qf
+    __device__ __forceinline__ int lim() const { return E; }   // extent of qa, qb, qf
 
-    // element of logical slot s (cell s - GHOST for qa/qb; interface s - 1 for qf)
-    __device__ __forceinline__ R &at(R *arr, int s) const { return MGRIT_SH(arr, phys(s), lim()); }
-    __device__ __forceinline__ R at(const R *arr, int s) const { return MGRIT_SH(arr, phys(s), lim()); }
+    // slot of cell i
+    __device__ __forceinline__ int sl(int i) const
+    {
+        if (!TL) return i + GHOST;
+        const int v = i + RO * CPT;
+        return (v & (CPT - 1)) * P + (v >> LOG);
+    }
+    __device__ __forceinline__ R &ce(R *arr, int i) const { return MGRIT_SH(arr, sl(i), lim()); }
+    __device__ __forceinline__ R ce(const R *arr, int i) const { return MGRIT_SH(arr, sl(i), lim()); }
 
-    // store cell i (and its periodic ghost copy) into slot i + GHOST
+    // store cell i (and its periodic ghost copy)
     __device__ __forceinline__ void put(R *arr, int i, R v) const
     {
-        at(arr, i + GHOST) = v;
-        if (i < GHOST) at(arr, i + GHOST + nx) = v;
-        if (i >= nx - GHOST) at(arr, i + GHOST - nx) = v;
+        ce(arr, i) = v;
+        if (i < GHOST) ce(arr, i + nx) = v;
+        if (i >= nx - GHOST) ce(arr, i - nx) = v;
     }
     // interfaces i0 .. i0 + run() - 1 (i0 = t * CPT) of this thread's contiguous run
     __device__ __forceinline__ int run() const
@@ -447,69 +516,82 @@ struct Slab {
         const int r = nx - (int)threadIdx.x * CPT;
         return r < 0 ? 0 : (r < CPT ? r : CPT);
     }
-    // physical index of slot cell(c) + o (affine in c, see pstride)
-    __device__ __forceinline__ int pc(int c, int o) const { return phys((int)threadIdx.x + o) + c * pstride; }
+    // slot of cell(c) + o (affine in c, see pstride)
+    __device__ __forceinline__ int pc(int c, int o) const { return sl((int)threadIdx.x + o) + c * pstride; }
     // put() for this thread's owned cell c
     __device__ __forceinline__ void put_c(R *arr, int c, R v) const
     {
         const int i = cell(c);
-        MGRIT_SH(arr, pc(c, GHOST), lim()) = v;
-        if (i < GHOST) at(arr, i + GHOST + nx) = v;
-        if (i >= nx - GHOST) at(arr, i + GHOST - nx) = v;
+        MGRIT_SH(arr, pc(c, 0), lim()) = v;
+        if (i < GHOST) ce(arr, i + nx) = v;
+        if (i >= nx - GHOST) ce(arr, i - nx) = v;
+    }
+    // slot of cell i0 + m of this thread's run (i0 = t * CPT), m a constant
+    // in -CPT*RO .. 2*CPT - 1 once the loops below are unrolled
+    __device__ __forceinline__ int rs(int m) const
+    {
+        if (!TL) return (int)threadIdx.x * CPT + m + GHOST;
+        const int mm = m + RO * CPT;   // >= 0
+        return (mm & (CPT - 1)) * P + (int)threadIdx.x + (mm >> LOG);
     }
 
-    // left-biased reconstruction at i+1/2 from slots around s = i + GHOST
-    __device__ __forceinline__ R rec_minus(const R *q, int s) const
+    // left-biased reconstruction at i+1/2 from the cells around i
+    __device__ __forceinline__ R rec_minus(const R *q, int i) const
     {
-        if (SCHEME == SCH_FO_FE) return at(q, s);
-        return weno5_left<R>(at(q, s - 2), at(q, s - 1), at(q, s), at(q, s + 1), at(q, s + 2));
+        if (SCHEME == SCH_FO_FE) return ce(q, i);
+        return weno5_left<R>(ce(q, i - 2), ce(q, i - 1), ce(q, i), ce(q, i + 1), ce(q, i + 2));
     }
     // right-biased reconstruction at i+1/2: the mirrored stencil
-    __device__ __forceinline__ R rec_plus(const R *q, int s) const
+    __device__ __forceinline__ R rec_plus(const R *q, int i) const
     {
-        if (SCHEME == SCH_FO_FE) return at(q, s + 1);
-        return weno5_left<R>(at(q, s + 3), at(q, s + 2), at(q, s + 1), at(q, s), at(q, s - 1));
+        if (SCHEME == SCH_FO_FE) return ce(q, i + 1);
+        return weno5_left<R>(ce(q, i + 3), ce(q, i + 2), ce(q, i + 1), ce(q, i), ce(q, i - 1));
     }
 
+    // F_{i+1/2} into cell i of qf (and F_{-1/2} = F_{nx-1/2} into cell -1)
     __device__ __forceinline__ void put_flux(int i, R F) const
     {
-        at(qf, i + 1) = F;
-        if (i == nx - 1) at(qf, 0) = F;
+        ce(qf, i) = F;
+        if (i == nx - 1) ce(qf, -1) = F;
     }
 
     // WENO5 split fluxes of the interfaces i0 .. i0 + CPT - 1 (i0 = t * CPT)
     // from qa = f^+/2 and qb = f^-/2, one sliding window per array (see
-    // WenoWin).  Reads slots i0 - 1 .. i0 + n + 2 (+ GHOST), all inside the
-    // arrays for every interface i < nx.
+    // WenoWin).  Reads cells i0 - 2 .. i0 + n + 2, all inside the arrays for
+    // every interface i < nx.  FP64: a rolled loop (the window shifts by
+    // register moves; unrolled, the slabs spill); FP32: unrolled, so that
+    // every slot is the thread's base plus a constant.
     __device__ __forceinline__ void split_fluxes_win() const
     {
         const int i0 = threadIdx.x * CPT;
         if (i0 >= nx) return;
         const int n = nx - i0 < CPT ? nx - i0 : CPT;
-        const int s = i0 + GHOST;
+        auto A_ = [&](int m) { return MGRIT_SH(qa, rs(m), lim()); };
+        auto B_ = [&](int m) { return MGRIT_SH(qb, rs(m), lim()); };
         WenoWin<R> P, M;
-        P.init(at(qa, s - 2), at(qa, s - 1), at(qa, s), at(qa, s + 1), at(qa, s + 2));
-        if (FLUX == FLX_BURGERS)
-            M.init(at(qb, s - 1), at(qb, s), at(qb, s + 1), at(qb, s + 2), at(qb, s + 3));
-        // rolled: the window shifts by register moves, and its live state
-        // stays independent of CPT (unrolled, the FP64 slabs spill)
-#pragma unroll 1
-        for (int k = 0; k < n; ++k) {
-            const R qp = at(qa, s + k);
-            put_flux(i0 + k, FLUX == FLX_BURGERS ? split_flux_win(P, M, qp, at(qb, s + k + 1))
-                                                 : split_flux_win_adv(P, qp));
+        P.init(A_(-2), A_(-1), A_(0), A_(1), A_(2));
+        if (FLUX == FLX_BURGERS) M.init(B_(-1), B_(0), B_(1), B_(2), B_(3));
+#pragma unroll(sizeof(R) == 4 ? CPT : 1)
+        for (int k = 0; k < CPT; ++k) {
+            if (k >= n) break;
+            const R qp = A_(k);
+            const R F = FLUX == FLX_BURGERS ? split_flux_win(P, M, qp, B_(k + 1)) : split_flux_win_adv(P, qp);
+            MGRIT_SH(qf, rs(k), lim()) = F;
             if (k + 1 < n) {
-                P.advance(at(qa, s + k + 3));
-                if (FLUX == FLX_BURGERS) M.advance(at(qb, s + k + 4));
+                P.advance(A_(k + 3));
+                if (FLUX == FLX_BURGERS) M.advance(B_(k + 4));
             }
         }
+        // F_{-1/2} = F_{nx-1/2}, from the thread whose run ends at nx - 1
+        if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
     }
 
     // FP32: the same windows on packed pairs.  Lane x of the pair walks
     // interfaces i0 .. i0 + CPT/2 - 1, lane y i0 + CPT/2 .. i0 + CPT - 1;
     // each lane performs the scalar window's operations, so the bits do not
-    // depend on the pairing.  Lane y's slots are clamped into the arrays
-    // where its interfaces run past nx (those results are dropped).
+    // depend on the pairing.  Where lane y's interfaces run past nx its cells
+    // still lie inside the arrays (the run stride leaves two runs to the
+    // right of the last thread's); those results are dropped.
     __device__ __forceinline__ void split_fluxes_win2() const
     {
         static_assert(sizeof(R) == 4 && CPT >= 2, "packed windows are FP32 with CPT >= 2");
@@ -517,30 +599,28 @@ struct Slab {
         const int i0 = threadIdx.x * CPT;
         if (i0 >= nx) return;
         const int n = nx - i0 < CPT ? nx - i0 : CPT;
-        const int sx = i0 + GHOST;
-        const bool yok = n > H;
-        const int sy = yok ? sx + H : sx;
-        const int top = nx + 2 * GHOST - 1;   // last slot
-        auto ld = [&](const R *q, int ox, int oy) {
-            const int y = sy + oy < top ? sy + oy : top;
-            return make_float2(at(q, sx + ox), at(q, y));
+        auto ld = [&](const R *q, int m) {
+            return make_float2(MGRIT_SH(q, rs(m), lim()), MGRIT_SH(q, rs(m + H), lim()));
         };
         WenoWin<float2> P, M;
-        P.init(ld(qa, -2, -2), ld(qa, -1, -1), ld(qa, 0, 0), ld(qa, 1, 1), ld(qa, 2, 2));
-        if (FLUX == FLX_BURGERS) M.init(ld(qb, -1, -1), ld(qb, 0, 0), ld(qb, 1, 1), ld(qb, 2, 2), ld(qb, 3, 3));
-        const int nxl = n < H ? n : H;   // interfaces of lane x
-#pragma unroll 1
-        for (int k = 0; k < nxl; ++k) {
-            const float2 qp = ld(qa, k, k);
-            const float2 F = FLUX == FLX_BURGERS ? split_flux_win(P, M, qp, ld(qb, k + 1, k + 1))
+        P.init(ld(qa, -2), ld(qa, -1), ld(qa, 0), ld(qa, 1), ld(qa, 2));
+        if (FLUX == FLX_BURGERS) M.init(ld(qb, -1), ld(qb, 0), ld(qb, 1), ld(qb, 2), ld(qb, 3));
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            if (k >= n) break;
+            const float2 qp = ld(qa, k);
+            const float2 F = FLUX == FLX_BURGERS ? split_flux_win(P, M, qp, ld(qb, k + 1))
                                                  : split_flux_win_adv(P, qp);
-            put_flux(i0 + k, F.x);
-            if (yok && H + k < n) put_flux(i0 + H + k, F.y);
-            if (k + 1 < nxl) {
-                P.advance(ld(qa, k + 3, k + 3));
-                if (FLUX == FLX_BURGERS) M.advance(ld(qb, k + 4, k + 4));
+            MGRIT_SH(qf, rs(k), lim()) = F.x;
+            if (H + k < n) MGRIT_SH(qf, rs(H + k), lim()) = F.y;
+            if (k + 1 < H) {
+                P.advance(ld(qa, k + 3));
+                if (FLUX == FLX_BURGERS) M.advance(ld(qb, k + 4));
             }
         }
+        // F_{-1/2} = F_{nx-1/2}, from the thread whose run ends at nx - 1 (its
+        // own store of that interface precedes this read in program order)
+        if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
     }
 
     // Interface fluxes F_{i+1/2} of the stage input w into qf (Sec. 2.1.2).
@@ -597,7 +677,7 @@ struct Slab {
                 const int i0 = threadIdx.x * CPT, n = run();
 #pragma unroll 1
                 for (int k = 0; k < n; ++k)
-                    put_flux(i0 + k, rec_minus(qa, i0 + k + GHOST) + rec_plus(qb, i0 + k + GHOST));
+                    put_flux(i0 + k, rec_minus(qa, i0 + k) + rec_plus(qb, i0 + k));
             }
         } else if (numflux == NF_ROE) {
             // local per interface: no global speed, no reduction
@@ -610,8 +690,7 @@ struct Slab {
             const int i0 = threadIdx.x * CPT, n = run();
 #pragma unroll 1
             for (int k = 0; k < n; ++k) {
-                const int s = i0 + k + GHOST;
-                put_flux(i0 + k, roe_flux<FLUX>(rec_minus(qa, s), rec_plus(qa, s)));
+                put_flux(i0 + k, roe_flux<FLUX>(rec_minus(qa, i0 + k), rec_plus(qa, i0 + k)));
             }
         } else {
 #pragma unroll
@@ -620,18 +699,18 @@ struct Slab {
                 if (i < nx) put_c(qa, c, w[c]);
             }
             __syncthreads();
-            // u^-_{i+1/2} parked in qb slot i, u^+_{i+1/2} in qf slot i+1 for this
+            // u^-_{i+1/2} parked in qb cell i, u^+_{i+1/2} in qf cell i for this
             // thread's run of interfaces; each thread reads back only its own
-            // slots, then overwrites qf slot i+1 with F
+            // cells, then overwrites qf cell i with F
             const int i0 = threadIdx.x * CPT, n = run();
             decltype(mag_key(R(0))) v = 0;   // max |u^-|, |u^+| (Burgers)
 #pragma unroll 1
             for (int k = 0; k < n; ++k) {
                 const int i = i0 + k;
-                const R um = rec_minus(qa, i + GHOST);
-                const R up = rec_plus(qa, i + GHOST);
-                at(qb, i) = um;
-                at(qf, i + 1) = up;
+                const R um = rec_minus(qa, i);
+                const R up = rec_plus(qa, i);
+                ce(qb, i) = um;
+                ce(qf, i) = up;
                 const auto km = mag_key(um), kp = mag_key(up);
                 const auto kk = km > kp ? km : kp;
                 v = kk > v ? kk : v;
@@ -641,7 +720,7 @@ struct Slab {
 #pragma unroll 1
             for (int k = 0; k < n; ++k) {
                 const int i = i0 + k;
-                const R um = at(qb, i), up = at(qf, i + 1);
+                const R um = ce(qb, i), up = ce(qf, i);
                 put_flux(i, R(0.5) * (phys_flux<FLUX>(up) + phys_flux<FLUX>(um)) - R(0.5) * alpha * (up - um));
             }
         }
@@ -652,7 +731,7 @@ struct Slab {
     // valid after fluxes().
     __device__ __forceinline__ R A(int c) const
     {
-        return -(MGRIT_SH(qf, pc(c, 1), lim()) - MGRIT_SH(qf, pc(c, 0), lim())) * dxinv;
+        return RK<R>::A(Ar<R>::sub(MGRIT_SH(qf, pc(c, 0), lim()), MGRIT_SH(qf, pc(c, -1), lim())), dxinv);
     }
 
     // Eq. (fineLF): u <- E u - dt D f(u), (E v)_i = (v_{i+1} + v_{i-1})/2,
@@ -689,14 +768,13 @@ struct Slab {
             for (int c = 0; c < CPT; ++c) {
                 const int i = cell(c);
                 if (i < nx) {
-                    const int s = i + GHOST;
-                    const R Df = (at(qb, s + 1) - at(qb, s - 1)) * hd;
+                    const R Df = (ce(qb, i + 1) - ce(qb, i - 1)) * hd;
                     if (first)
                         acc[c] = k == 0 ? Df
-                                        : Df + R(0.5) * (at(qf, s + 1) + at(qf, s - 1));
+                                        : Df + R(0.5) * (ce(qf, i + 1) + ce(qf, i - 1));
                     else if (k == 0)
                         acc[c] = Df;   // D f(u)
-                    v[c] = R(0.5) * (at(qa, s + 1) + at(qa, s - 1));
+                    v[c] = R(0.5) * (ce(qa, i + 1) + ce(qa, i - 1));
                 }
             }
         }
@@ -719,23 +797,21 @@ struct Slab {
             fluxes(u);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < nx) u[c] = u[c] + dt * A(c);
+                if (cell(c) < nx) u[c] = RK<R>::euler(u[c], dt, A(c));
             return;
         }
         R w[CPT];
         fluxes(u);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? u[c] + dt * A(c) : R(0);
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? RK<R>::euler(u[c], dt, A(c)) : R(0);
         fluxes(w);
-        const R q = R(0.25) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) w[c] = R(0.75) * u[c] + R(0.25) * w[c] + q * A(c);
+            if (cell(c) < nx) w[c] = RK<R>::stage2(u[c], w[c], dt, A(c));
         fluxes(w);
-        const R t = R(2.0 / 3.0) * dt;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) u[c] = R(1.0 / 3.0) * u[c] + R(2.0 / 3.0) * w[c] + t * A(c);
+            if (cell(c) < nx) u[c] = RK<R>::stage3(u[c], w[c], dt, A(c));
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *__restrict__ row) const
@@ -775,13 +851,18 @@ struct Slab {
     }
 };
 
-// shared-memory bytes of one slab of nx cells with cpt cells per thread
+// shared-memory bytes of one slab of nx cells on `threads` threads with cpt
+// cells per thread (the layout of Slab above)
 template <typename R>
-inline size_t slab_smem_bytes(int nx, int cpt)
+inline size_t slab_smem_bytes(int nx, int cpt, int threads)
 {
-    const bool pad = sizeof(R) == 4 && cpt >= 2;
-    const size_t s = (size_t)nx + 2 * GHOST;
-    const size_t e = pad ? (s - 1) + (s - 1) / (size_t)cpt + 1 : s;
+    size_t e = (size_t)nx + 2 * GHOST;
+    if (sizeof(R) == 4 && cpt >= 2) {
+        const int ro = cpt >= 4 ? 1 : 2, r0 = (32 / cpt) % 32;
+        int P = threads + ro + 2;
+        P += ((r0 - P % 32) % 32 + 32) % 32;
+        e = (size_t)cpt * P;
+    }
     return sizeof(R) * (3 * e + NWARP_MAX);
 }
 

@@ -21,6 +21,7 @@ LF_SPLIT, LF_STATE, ROE = 0, 1, 2
 RELAX_F, RELAX_FCF = 0, 1
 GUESS_EQ17, GUESS_INJECT = 0, 1
 CYCLE_V, CYCLE_F = 0, 1
+SEQ_AUTO, SEQ_ONE_CTA, SEQ_CLUSTER, SEQ_GRID = 0, 1, 2, 3
 COARSE_REDISC, COARSE_PSI0, COARSE_PSI1 = 0, 1, 2
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM",
                 EDIVERGED: "EDIVERGED", ENOTCONV: "ENOTCONV", ETIMEOUT: "ETIMEOUT"}
@@ -30,7 +31,8 @@ class mgrit_params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_double), ("L", ctypes.c_double), ("relax", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("guess", ctypes.c_int), ("numflux", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("coarse", ctypes.c_int), ("chunk_clusters", ctypes.c_int)]
+                ("coarse", ctypes.c_int), ("chunk_clusters", ctypes.c_int),
+                ("seq_stepper", ctypes.c_int)]
 
 
 class mgrit_stats(ctypes.Structure):
@@ -64,6 +66,8 @@ _SIGS = {
     "mgrit_fma_probe": (_I, [_I, _I, _I, ctypes.POINTER(_D), _P]),
     "mgrit_cycle_cell_updates": (_D, [_P]),
     "mgrit_query": (_I, [_P, _I]),
+    "mgrit_sync_status": (_I, [_P, _P]),
+    "mgrit_test_grid_timeout": (_I, [_P, _P]),
     "mgrit_step_vjp": (_I, [_P, _P, _P, _P, _P]),
     "mgrit_adjoint_serial": (_I, [_P, _P, _P, _P, _P]),
     "mgrit_adjoint": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(mgrit_stats)]),
@@ -206,10 +210,20 @@ class Solver:
 
     def query(self, what):
         """0: cells per thread, 1: threads per CTA, 2: cluster size of the
-        sequential stepper, 100 + l: cluster size of the level-l relaxation
-        and interpolation chunks (1: one CTA per chunk; 0 before the first
-        allocating call)."""
+        sequential stepper, 3: CTAs of the grid stepper (0: not used),
+        100 + l: cluster size of the level-l relaxation and interpolation
+        chunks (1: one CTA per chunk; 0 before the first allocating call)."""
         return load().mgrit_query(self._h, what)
+
+    def sync_status(self, stream=None):
+        """Synchronise; MGRIT_ETIMEOUT (raised) if a grid-stepper barrier wait
+        of an earlier asynchronous call gave up."""
+        self._check(load().mgrit_sync_status(self._h, _stream_handle(stream)))
+
+    def test_grid_timeout(self, stream=None):
+        """Status of one grid-stepper launch whose first barrier can never
+        complete (the bounded wait's test hook): MGRIT_ETIMEOUT expected."""
+        return load().mgrit_test_grid_timeout(self._h, _stream_handle(stream))
 
     # ---- discrete adjoint ----------------------------------------------
 

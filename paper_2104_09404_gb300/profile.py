@@ -14,6 +14,13 @@ runs the adjoint gradient workload instead (nx 2048, nt 8192, m 4, 3 levels,
 T 0.12, u0 Fourier seed 1, target seed 1001): a forward solve, then one
 adjoint cycle (k_adjoint launches: the forward-trajectory regeneration, then
 the level-0 adjoint relaxation).
+
+    python -m paper_2104_09404_gb300.profile --peaks
+
+measures the multiply-add throughput of the FP64 and FP32 pipes
+(mgrit_fma_probe: 152 x 8 CTAs of 256 threads, 8 independent chains per
+thread, ~0.1 s per launch, best of 3), the roofline denominators of the
+arithmetic-bound sweeps, and prints them in TFLOP/s.
 """
 import argparse
 import sys
@@ -33,11 +40,22 @@ def main(argv=None):
     p.add_argument("--level", type=int, default=0)
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--adjoint", action="store_true")
+    p.add_argument("--peaks", action="store_true", help="FP64 / FP32 multiply-add throughput")
     p.add_argument("--precision", type=int, default=64, choices=(64, 32),
                    help="32: the FP32-sweep instances of the kernels")
     a = p.parse_args(argv)
     import torch
     from . import inputs, mgrit
+    if a.peaks:
+        mgrit.load()
+        for kind, name, iters in ((mgrit.FMA_FP64, "FP64 DFMA", 3000),
+                                  (mgrit.FMA_FP32, "FP32 FFMA", 200000),
+                                  (mgrit.FMA_FP32X2, "FP32 FFMA2 (packed pairs)", 100000)):
+            mgrit.fma_probe(kind, iters // 20)
+            r = [mgrit.fma_probe(kind, iters) for _ in range(3)]
+            print("%-26s %8.3f TFLOP/s (best of 3; %s)" % (name, max(r) / 1e12,
+                                                         ", ".join("%.3f" % (x / 1e12) for x in r)))
+        return 0
     if a.adjoint:
         nx, nt = 2048, 8192
         s = mgrit.Solver(nx, nt, 4, 3, T=0.12)

@@ -50,7 +50,7 @@ def test_default_params(lib):
     lib.mgrit_default_params(ctypes.byref(p))
     assert (p.T, p.L, p.relax, p.cycle, p.guess, p.numflux) == (1.0, 1.0, 1, 0, 0, 0)
     assert p.tol == 1e-10 and p.max_iter == 64 and p.precision == 64 and p.coarse == 0
-    assert p.chunk_clusters == 1
+    assert p.chunk_clusters == 1 and p.seq_stepper == 0
 
 
 @pytest.mark.parametrize("args,frag", [
@@ -84,12 +84,13 @@ def test_create_set_params_destroy_without_gpu(lib):
     for field, bad in (("relax", 3), ("cycle", 2), ("guess", 2), ("numflux", 5), ("coarse", 3),
                        ("coarse", 1),
                        ("tol", -1.0), ("max_iter", 1000), ("precision", 16), ("T", 0.0),
-                       ("chunk_clusters", 2)):
+                       ("chunk_clusters", 2), ("seq_stepper", 4), ("seq_stepper", -1)):
         q = M.mgrit_params.from_buffer_copy(p)
         setattr(q, field, bad)
         assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field
     assert lib.mgrit_query(h, 0) == 1 and lib.mgrit_query(h, 1) == 128   # 100 cells, 1 per thread
     assert lib.mgrit_query(h, 2) == 0 and lib.mgrit_query(h, 9) == -1    # nothing allocated yet
+    assert lib.mgrit_query(h, 3) == 0                                     # grid stepper unknown yet
     # chunk cluster sizes of levels 0 and 1 (3 levels): unknown before allocation
     assert lib.mgrit_query(h, 100) == 0 and lib.mgrit_query(h, 101) == 0
     assert lib.mgrit_query(h, 102) == -1 and lib.mgrit_query(h, 99) == -1

@@ -97,7 +97,7 @@ def test_sequential_stepper_cluster_shape(M, nx, K):
     # the serial stepper and the coarsest solve spread one slab over a
     # cluster of K CTAs (at least 256 cells each); a silent fallback to one
     # CTA would show here
-    s = M.Solver(nx, 16, 2, 2, T=0.01)
+    s = M.Solver(nx, 16, 2, 2, T=0.01, seq_stepper=M.SEQ_CLUSTER)
     s.serial_step(dev(inputs.sine_ic(nx)), 2)
     torch.cuda.synchronize()
     assert s.query(2) == K

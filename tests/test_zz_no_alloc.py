@@ -41,23 +41,35 @@ def static_residual(M, uC, nt, m, T, scheme=0, flux=0, numflux=0):
     return st, float(out.item())
 
 
-@pytest.mark.parametrize("nx,nt,m,scheme,flux", [(256, 128, 4, 0, 0), (1000, 64, 8, 0, 1),
-                                                 (64, 96, 2, 1, 0)])
-def test_static_residual_matches_allocating_entry_point(M, nx, nt, m, scheme, flux):
+@pytest.mark.parametrize("nx,nt,m,scheme,flux,numflux", [
+    (256, 128, 4, 0, 0, 0), (1000, 64, 8, 0, 1, 0), (64, 96, 2, 1, 0, 0),
+    (300, 64, 4, 0, 0, 1),     # state-reconstruction Lax-Friedrichs flux
+    (200, 64, 4, 0, 0, 2),     # Roe flux with the entropy fix
+    (128, 64, 2, 1, 1, 2),
+])
+def test_static_residual_matches_allocating_entry_point(M, nx, nt, m, scheme, flux, numflux):
     T = 0.02
     u0 = inputs.fourier_ic(nx, seed=nx)
-    traj = O.serial(u0, T / nt, nt, scheme, flux, store_all=True)
-    s = M.Solver(nx, nt, m, 2, scheme, flux, T=T)
+    traj = O.serial(u0, T / nt, nt, scheme, flux, numflux, store_all=True)
+    s = M.Solver(nx, nt, m, 2, scheme, flux, T=T, numflux=numflux)
     rng = np.random.default_rng(1)
     for call in range(2):   # two calls in a row, different data
         uC = traj[::m].copy()
         uC[1:] += (10.0 ** (-3 - 2 * call)) * rng.standard_normal(uC[1:].shape)
         d = torch.as_tensor(uC, device="cuda")
-        st, got = static_residual(M, d, nt, m, T, scheme, flux)
+        st, got = static_residual(M, d, nt, m, T, scheme, flux, numflux)
         assert st == M.OK
         ref = s.residual(d)
         assert got == pytest.approx(ref, rel=1e-10)
-        assert got == pytest.approx(O.residual(uC, nt, m, T, scheme, flux), rel=1e-10)
+        assert got == pytest.approx(O.residual(uC, nt, m, T, scheme, flux, numflux), rel=1e-10)
+
+
+def test_static_residual_refuses_what_it_does_not_cover(M):
+    # the classical Lax-Friedrichs scheme and slices wider than one FP64 CTA
+    d = torch.zeros((5, 64), dtype=torch.float64, device="cuda")
+    assert static_residual(M, d, 16, 4, 0.1, scheme=2)[0] == M.EINVAL
+    w = torch.zeros((3, 8200), dtype=torch.float64, device="cuda")
+    assert static_residual(M, w, 8, 4, 0.1)[0] == M.EINVAL
 
 
 def test_static_residual_rejects_sizes_beyond_its_scratch(M):
