@@ -216,7 +216,7 @@ static void free_workspaces(mgrit_ctx *ctx)
     memset(&ctx->gbuf, 0, sizeof ctx->gbuf);
     memset(&ctx->lg64, 0, sizeof ctx->lg64);
     memset(&ctx->lg32, 0, sizeof ctx->lg32);
-    ctx->grid64 = ctx->grid32 = false;
+    ctx->seq64 = ctx->seq32 = 0;
     cudaFree(ctx->resid_rows);
     cudaFree(ctx->partials);
     cudaFree(ctx->d_norm);
@@ -234,6 +234,8 @@ static void free_workspaces(mgrit_ctx *ctx)
 }
 
 static int choose_levels(mgrit_ctx *ctx);
+template <typename R>
+static SlabArgs<R> relax_args(const mgrit_ctx *ctx, int l);
 
 extern "C" int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p)
 {
@@ -369,13 +371,6 @@ static cudaError_t launch_chunks(const ClusterLaunch &lc, const Launch &ln, int 
     return ln.slab ? launch1(ln.slab, chunks, ln, s, a) : cudaErrorInvalidConfiguration;
 }
 
-// sequential stepping in the precision of `lc`/`ln` (cluster if available)
-static cudaError_t launch_seq(const ClusterLaunch &lc, const Launch &ln, cudaStream_t s, void *a)
-{
-    if (!lc.fn) return ln.slab ? launch1(ln.slab, 1, ln, s, a) : cudaErrorInvalidConfiguration;
-    return launch_clusters(lc, 1, s, a);
-}
-
 // the grid stepper: barrier counter zeroed, then a cooperative launch (all G
 // CTAs co-resident, or the launch fails).  skip_cta >= 0 makes that CTA skip
 // the first barrier (the bounded-wait test hook).
@@ -404,6 +399,27 @@ static cudaError_t launch_grid(const GridLaunch &lg, const GridBufs &gb, const S
     return cudaLaunchKernelExC(&cfg, lg.fn, args);
 }
 
+// the sequential stepper a context uses in FP64 or FP32: 1 one CTA, 2 the
+// cluster, 3 the grid (mgrit_params.seq_stepper where that fits, else the
+// timed choice; the grid needs the split numerical flux)
+static int seq_kind(const mgrit_ctx *ctx, bool f32)
+{
+    const GridLaunch &lg = f32 ? ctx->lg32 : ctx->lg64;
+    const ClusterLaunch &lc = f32 ? ctx->lc32 : ctx->lc64;
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    const bool grid_ok = lg.fn && ctx->p.numflux == MGRIT_LF_SPLIT;
+    const int want = ctx->p.seq_stepper;
+    if (want == 1 && ln.slab) return 1;
+    if (want == 2 && lc.fn) return 2;
+    if (want == 3 && grid_ok) return 3;
+    int k = f32 ? ctx->seq32 : ctx->seq64;
+    if (k == 3 && !grid_ok) k = 0;
+    if (k == 1 && !ln.slab) k = 0;
+    if (k == 2 && !lc.fn) k = 0;
+    if (k == 0) k = lc.fn ? 2 : 1;
+    return k;
+}
+
 // sequential stepping of a context in FP64 (f32 = 0) or FP32: the grid
 // stepper where it was chosen and the split flux is in use, else the cluster
 // or one-CTA stepper
@@ -414,13 +430,11 @@ static cudaError_t launch_seq_ctx(const mgrit_ctx *ctx, const SlabArgs<R> &a, cu
     const GridLaunch &lg = f32 ? ctx->lg32 : ctx->lg64;
     const ClusterLaunch &lc = f32 ? ctx->lc32 : ctx->lc64;
     const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
-    const int want = ctx->p.seq_stepper;
-    const bool grid_ok = lg.fn && ctx->p.numflux == MGRIT_LF_SPLIT;
+    const int kind = seq_kind(ctx, f32);
     SlabArgs<R> b = a;
-    if (want == 1 && ln.slab) return launch1(ln.slab, 1, ln, s, &b);
-    if (want == 2 && lc.fn) return launch_clusters(lc, 1, s, &b);
-    if (grid_ok && (want == 3 || (f32 ? ctx->grid32 : ctx->grid64))) return launch_grid(lg, ctx->gbuf, a, s);
-    return launch_seq(lc, ln, s, &b);
+    if (kind == 3) return launch_grid(lg, ctx->gbuf, a, s);
+    if (kind == 1) return launch1(ln.slab, 1, ln, s, &b);
+    return launch_clusters(lc, 1, s, &b);
 }
 
 // true (and the flag cleared) if a grid-stepper wait gave up since the
@@ -434,20 +448,22 @@ static bool grid_timed_out(mgrit_ctx *ctx)
     return err != 0;
 }
 
-// Grid stepper shape for sequential stepping, chosen by timing: candidates
-// of G = SMs, SMs/2, SMs/4, ... CTAs (8 to 127 cells each, a lane pair per
-// interface, co-resident) against the cluster / one-CTA stepper, 16 steps each on a zero
-// state (the work does not depend on the data); the fastest is kept.  Split
-// numerical flux, WENO5 or first order, nx >= 512.
+// Kernel of the sequential chains, chosen by timing 16 steps of each shape
+// that fits on a zero state (the work does not depend on the data): one CTA,
+// the cluster, and the grid stepper with G = SMs, SMs/2, SMs/4, ... CTAs (8
+// to 127 cells each, a lane pair per interface, co-resident).  *kind gets
+// the fastest (1 one CTA, 2 cluster, 3 grid) and *lg the fastest grid shape
+// (null if none fits).  Grid: split numerical flux, WENO5 or first order,
+// nx >= 512.
 template <typename R>
-static int choose_grid(mgrit_ctx *ctx, GridLaunch *lg, bool *faster, R *row)
+static int choose_seq(mgrit_ctx *ctx, GridLaunch *lg, int *kind, R *row)
 {
     memset(lg, 0, sizeof *lg);
-    *faster = false;
     const bool f32 = sizeof(R) == 4;
-    if (ctx->scheme == MGRIT_LF_FE || ctx->nx < 512 || !row) return MGRIT_OK;
-    const void *fn = f32 ? table().grid32[ctx->scheme][ctx->flux] : table().grid64[ctx->scheme][ctx->flux];
-    if (!fn) return MGRIT_OK;
+    const ClusterLaunch &lc = f32 ? ctx->lc32 : ctx->lc64;
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    *kind = lc.fn ? 2 : 1;
+    if (!row) return MGRIT_OK;
     const int nx = ctx->nx;
     cudaStream_t s = ctx->cap;
     CK(cudaMemsetAsync(row, 0, sizeof(R) * nx, s));
@@ -482,13 +498,25 @@ static int choose_grid(mgrit_ctx *ctx, GridLaunch *lg, bool *faster, R *row)
         cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
         return ms;
     };
-    const ClusterLaunch &lc = f32 ? ctx->lc32 : ctx->lc64;
-    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
-    float other = -1.f, best = -1.f;
-    if (lc.fn || ln.slab) other = time_ms([&] {
+    float best = -1.f;
+    auto consider = [&](float ms, int k) {
+        if (ms > 0.f && (best < 0.f || ms < best)) {
+            best = ms;
+            *kind = k;
+        }
+    };
+    if (ln.slab) consider(time_ms([&] {
         SlabArgs<R> b = a;
-        return launch_seq(lc, ln, s, &b);
-    });
+        return launch1(ln.slab, 1, ln, s, &b);
+    }), 1);
+    if (lc.fn) consider(time_ms([&] {
+        SlabArgs<R> b = a;
+        return launch_clusters(lc, 1, s, &b);
+    }), 2);
+    const void *fn = f32 ? table().grid32[ctx->scheme == MGRIT_LF_FE ? 0 : ctx->scheme][ctx->flux]
+                         : table().grid64[ctx->scheme == MGRIT_LF_FE ? 0 : ctx->scheme][ctx->flux];
+    if (ctx->scheme == MGRIT_LF_FE || nx < 512 || !fn) return MGRIT_OK;
+    float gbest = -1.f;
     int nb = 0;
     for (int G = ctx->nsm < GRID_MAX ? ctx->nsm : GRID_MAX; G >= 8; G /= 2) {
         const int n = (nx + G - 1) / G;
@@ -502,20 +530,63 @@ static int choose_grid(mgrit_ctx *ctx, GridLaunch *lg, bool *faster, R *row)
         }
         const GridLaunch cand{fn, G, threads};
         const float ms = time_ms([&] { return launch_grid(cand, ctx->gbuf, a, s); });
-        if (ms > 0.f && (best < 0.f || ms < best)) {
-            best = ms;
+        if (ms > 0.f && (gbest < 0.f || ms < gbest)) {
+            gbest = ms;
             *lg = cand;
         }
     }
-    *faster = lg->fn && (other < 0.f || best < other);
+    consider(gbest, 3);
     // a wait that gave up during the choice would leave the error flag set
     int err = 0;
     CK(cudaMemcpy(&err, ctx->gbuf.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         memset(lg, 0, sizeof *lg);
-        *faster = false;
+        if (*kind == 3) *kind = lc.fn ? 2 : 1;
         CK(cudaMemset(ctx->gbuf.err, 0, sizeof(int)));
     }
+    return MGRIT_OK;
+}
+
+// FP32 WENO5 slabs: the cells per thread of the one-CTA slab, chosen by
+// timing the level-0 relaxation with 1x, 2x and 4x the smallest that fits
+// (fewer, fuller threads let two CTAs share an SM and hide each other's
+// barriers) on min(chunks, 2 x SMs) chunks of a zero state; the choice gives
+// the same bits as any other (every FP32 shape performs the same operations)
+static int tune_slab32(mgrit_ctx *ctx)
+{
+    if (!ctx->f32 || ctx->scheme != MGRIT_WENO5_SSPRK3 || !ctx->ln32.slab) return MGRIT_OK;
+    int ci0 = 0;
+    while (ci0 < NCPT && CPT_VALUES[ci0] != ctx->ln32.cpt) ++ci0;
+    SlabArgs<float> a = relax_args<float>(ctx, 0);
+    const int chunks = ctx->nC_l[0] + 1 < 2 * ctx->nsm ? ctx->nC_l[0] + 1 : 2 * ctx->nsm;
+    cudaStream_t s = ctx->cap;
+    CK(cudaMemsetAsync(const_cast<float *>(a.uC), 0, sizeof(float) * (size_t)ctx->nx * chunks, s));
+    Launch best = ctx->ln32;
+    float best_ms = -1.f;
+    for (int ci = ci0; ci < NCPT && ci <= ci0 + 2; ++ci) {
+        const int cpt = CPT_VALUES[ci];
+        const int need = (ctx->nx + cpt - 1) / cpt;
+        Launch ln;
+        ln.cpt = cpt;
+        ln.threads = ((need + 31) / 32) * 32;
+        ln.smem = slab_smem_bytes<float>(ctx->nx, cpt, ln.threads);
+        ln.slab = table().slab32[ctx->scheme][ctx->flux][ci];
+        if (!ln.slab || ln.smem > (size_t)SMEM_OPTIN) continue;
+        CK(cudaFuncSetAttribute(ln.slab, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
+        float ms = -1.f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first launch warms up
+            CK(cudaEventRecord(ctx->ev0, s));
+            CK(launch1(ln.slab, chunks, ln, s, &a));
+            CK(cudaEventRecord(ctx->ev1, s));
+            CK(cudaEventSynchronize(ctx->ev1));
+            CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        }
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = ln;
+        }
+    }
+    ctx->ln32 = best;
     return MGRIT_OK;
 }
 
@@ -562,19 +633,21 @@ int mgrit_ensure_alloc(mgrit_ctx *ctx)
     CK(cudaMalloc((void **)&ctx->gbuf.bar, sizeof(unsigned)));
     CK(cudaMalloc((void **)&ctx->gbuf.err, sizeof(int)));
     CK(cudaMemset(ctx->gbuf.err, 0, sizeof(int)));
-    // the grid stepper's choice times launches on rows the solve overwrites
-    // later: FP64 on the level-0 C-point row buffer (FP64 mode) or a fresh
-    // FP64 row, FP32 on the FP32 serial row
+    // the timed choices run on rows the solve overwrites later: the FP32 slab
+    // shape on the level-0 C-point source, the FP64 sequential stepper on the
+    // level-0 C-point row buffer (FP64 mode) or a fresh FP64 row, the FP32
+    // one on the FP32 serial row
+    if ((st = tune_slab32(ctx))) return st;
     if (!ctx->f32) {
-        if ((st = choose_grid<double>(ctx, &ctx->lg64, &ctx->grid64, static_cast<double *>(ctx->newC[0]))))
+        if ((st = choose_seq<double>(ctx, &ctx->lg64, &ctx->seq64, static_cast<double *>(ctx->newC[0]))))
             return st;
     } else {
         double *tmp = nullptr;
         CK(cudaMalloc((void **)&tmp, sizeof(double) * ctx->nx));
-        st = choose_grid<double>(ctx, &ctx->lg64, &ctx->grid64, tmp);
+        st = choose_seq<double>(ctx, &ctx->lg64, &ctx->seq64, tmp);
         cudaFree(tmp);
         if (st) return st;
-        if ((st = choose_grid<float>(ctx, &ctx->lg32, &ctx->grid32, ctx->ser32))) return st;
+        if ((st = choose_seq<float>(ctx, &ctx->lg32, &ctx->seq32, ctx->ser32))) return st;
     }
     if (!ctx->ln64.slab && !ctx->lc64.fn)
         return mgrit_fail(ctx, MGRIT_EINVAL, "no FP64 slab or cluster fits nx = %d for the coarsest solve",
@@ -808,7 +881,7 @@ static int ensure_graphs(mgrit_ctx *ctx)
         if (!ctx->lg64.fn) return st;
         cudaGetLastError();
         ctx->lg64.fn = nullptr;
-        ctx->grid64 = false;
+        if (ctx->seq64 == 3) ctx->seq64 = 0;
         if ((st = capture(ctx, enqueue_part_b, &ctx->gB))) return st;
     }
     return MGRIT_OK;
@@ -1088,15 +1161,9 @@ extern "C" int mgrit_query(const mgrit_ctx *ctx, int what)
     case 2:     // CTAs of the cluster the sequential chains use (1: one CTA; 0: the grid stepper)
     case 3: {   // CTAs of the grid stepper the sequential chains use (0: not used)
         if (!ctx->alloc) return 0;
-        const GridLaunch &lg = f32 ? ctx->lg32 : ctx->lg64;
-        const int want = ctx->p.seq_stepper;
-        const bool grid = lg.fn && ctx->p.numflux == MGRIT_LF_SPLIT &&
-                          !(want == 1 && ln.slab) && !(want == 2 && lc.fn) &&
-                          (want == 3 || (f32 ? ctx->grid32 : ctx->grid64));
-        if (what == 3) return grid ? lg.G : 0;
-        if (grid) return 0;
-        if (want == 1 && ln.slab) return 1;
-        return lc.fn ? lc.K : 1;
+        const int kind = seq_kind(ctx, f32);
+        if (what == 3) return kind == 3 ? (f32 ? ctx->lg32.G : ctx->lg64.G) : 0;
+        return kind == 3 ? 0 : kind == 1 ? 1 : lc.K;
     }
     default:
         if (what >= 100 && what < 100 + ctx->L - 1) {   // level what-100 relaxation / interpolation

@@ -105,7 +105,7 @@ struct mgrit_ctx {
     // grid-wide sequential stepping, chosen by timing against the cluster
     // stepper when the workspaces are allocated (fn null: cluster / one CTA)
     mgrit::GridLaunch lg64, lg32;   // fastest grid shape (fn null: none fits)
-    bool grid64, grid32;            // the grid stepper timed faster than the others
+    int seq64, seq32;               // the fastest sequential stepper timed (1 one CTA, 2 cluster, 3 grid)
     mgrit::GridBufs gbuf;
     // relaxation / interpolation of level l on clusters (fn null: one CTA per
     // chunk), chosen when the workspaces are allocated

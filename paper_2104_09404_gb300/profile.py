@@ -2,6 +2,9 @@
 
     python -m paper_2104_09404_gb300.profile --case c2 --kernel relax --level 0 --reps 1
 
+(--kernel serial: 64 steps of mgrit_serial_step instead, on the sequential
+stepper the context chose at allocation.)
+
 Cases: c2 = nx 4096, nt 16384, m 4, 6 levels, T 1 (the benchmark workload);
 small = nx 4096, nt 2048, m 4, 4 levels, T 0.125 (same kernel shape, 513
 CTAs).  The context is prepared with zero cycles (workspaces allocated,
@@ -30,7 +33,7 @@ CASES = {
     "small": dict(nx=4096, nt=2048, m=4, levels=4, T=0.125),
     "c1": dict(nx=128, nt=256, m=4, levels=2, T=0.5),
 }
-KERNELS = {"relax": 0, "restrict": 1, "coarsest": 2, "interp": 3}
+KERNELS = {"relax": 0, "restrict": 1, "coarsest": 2, "interp": 3, "serial": -1}
 
 
 def main(argv=None):
@@ -70,6 +73,14 @@ def main(argv=None):
     c = CASES[a.case]
     s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"], precision=a.precision)
     u0 = torch.as_tensor(inputs.fourier_ic(c["nx"], seed=0), device="cuda")
+    if a.kernel == "serial":
+        # 64 serial steps on the sequential stepper the context chose
+        # (allocation times the candidates first: their launches come before)
+        s.serial_step(u0, 64)
+        s.sync_status()
+        print("serial stepping x64 on case %s (grid CTAs %d, cluster CTAs %d)"
+              % (a.case, s.query(3), s.query(2)))
+        return 0
     s.run_cycles(u0, 0)
     s.launch_kernel(KERNELS[a.kernel], a.level, a.reps)
     torch.cuda.synchronize()
