@@ -3,14 +3,16 @@
 // stage fluxes in shared memory for every step of a C-interval.
 //
 // Cell ownership is interleaved: thread t owns cells t + c*blockDim.x,
-// c = 0..CPT-1 (cells >= nx are idle).  Consecutive lanes touch
-// consecutive cells, so shared-memory traffic is conflict-free and global
-// row loads/stores are coalesced.
+// c = 0..CPT-1 (cells >= nx are idle), so global row loads and stores are
+// coalesced.  The interface fluxes are computed in contiguous runs instead:
+// thread t takes the interfaces t*CPT .. t*CPT + CPT - 1 and slides a window
+// of first differences along them (WenoWin below).
 //
-// Shared memory: three arrays of nx + 6 values (the split fluxes f^+ and f^-
-// with 3 periodic ghost cells on each side -- the WENO5 half-stencil -- and
-// the interface fluxes) plus NWARP_MAX values for the block max reduction of
-// the global Lax-Friedrichs alpha.
+// Shared memory: three arrays (the half split fluxes q^+ and q^- with 3
+// periodic ghost cells on each side -- the WENO5 half-stencil -- and the
+// interface fluxes; FP32 slabs in the run-major layout of Slab) plus
+// NWARP_MAX values for the block max reduction of the global Lax-Friedrichs
+// alpha.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -104,9 +106,10 @@ __device__ __forceinline__ void weno5_left_nd(R a, R b, R c, R d, R e, R &num, R
     den = R(6) * (t0 + t1 + t2);
 }
 
-// FP32: the same fraction with every multiply-add explicit, in the order of
-// the packed-pair version below (weno5_left_x2), so that an FP32
-// reconstruction gives the same bits whether it runs alone or in a pair
+// FP32: the same fraction with every multiply-add explicit (used by the
+// state-form and Roe fluxes, whose reconstructions act on the state), so
+// that an FP32 reconstruction gives the same bits in every kernel that
+// evaluates it
 template <>
 __device__ __forceinline__ void weno5_left_nd<float>(float a, float b, float c, float d, float e,
                                                      float &num, float &den)
@@ -455,21 +458,14 @@ struct Slab {
     static constexpr bool TL = sizeof(R) == 4 && CPT >= 2;
     static constexpr int LOG = CPT >= 32 ? 5 : CPT >= 16 ? 4 : CPT >= 8 ? 3 : CPT >= 4 ? 2 : CPT >= 2 ? 1 : 0;
     static constexpr int RO = CPT >= 4 ? 1 : 2;
-    // run stride of the FP32 layout for a CTA of T threads
-    static __host__ __device__ __forceinline__ int run_stride(int T)
-    {
-        const int r0 = (32 / CPT) % 32;
-        int P = T + RO + 2;
-        P += ((r0 - P % 32) % 32 + 32) % 32;
-        return P;
-    }
+    // run stride of the FP32 layout: sized for the largest CTA (512 threads)
+    // and fixed per CTA shape, so that every window slot is the thread's base
+    // plus a compile-time constant
+    static constexpr int P0 = 512 + RO + 2;
+    static constexpr int P = P0 + ((((32 / CPT) % 32) - P0 % 32) % 32 + 32) % 32;
     // elements of each of qa, qb, qf
-    static __host__ __device__ __forceinline__ int extent(int nx, int T)
-    {
-        return TL ? CPT * run_stride(T) : nx + 2 * GHOST;
-    }
+    static __host__ __device__ __forceinline__ int extent(int nx) { return TL ? CPT * P : nx + 2 * GHOST; }
 
-    int P;        // run stride (FP32 layout)
     int E;        // elements per array
     int pstride;  // slot distance between a thread's consecutive interleaved cells
 
@@ -477,8 +473,7 @@ struct Slab {
         : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))
     {
         const int T = (int)blockDim.x;
-        P = TL ? run_stride(T) : 0;
-        E = extent(nx, T);
+        E = extent(nx);
         // blockDim.x is a multiple of 32, hence of CPT: cell t + c*T + o sits at
         // sl(t + o) + c * pstride
         pstride = TL ? T / CPT : T;
@@ -487,8 +482,6 @@ struct Slab {
         qf = qb + E;
         red = qf + E;
     }
-
-    static constexpr int RECON_UNROLL = sizeof(R) == 4 ? 1 : CPT;
 
     __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
     __device__ __forceinline__ int lim() const { return E; }   // extent of qa, qb, qf
@@ -518,12 +511,13 @@ struct Slab {
     }
     // slot of cell(c) + o (affine in c, see pstride)
     __device__ __forceinline__ int pc(int c, int o) const { return sl((int)threadIdx.x + o) + c * pstride; }
-    // put() for this thread's owned cell c
+    // put() for this thread's owned cell c (c a constant once unrolled; a
+    // CTA has at least 32 threads, so only c = 0 can hold cells 0..2)
     __device__ __forceinline__ void put_c(R *arr, int c, R v) const
     {
         const int i = cell(c);
         MGRIT_SH(arr, pc(c, 0), lim()) = v;
-        if (i < GHOST) ce(arr, i + nx) = v;
+        if (c == 0 && i < GHOST) ce(arr, i + nx) = v;
         if (i >= nx - GHOST) ce(arr, i - nx) = v;
     }
     // slot of cell i0 + m of this thread's run (i0 = t * CPT), m a constant
@@ -657,7 +651,7 @@ struct Slab {
                 }
                 __syncthreads();
                 // (packed FP32 windows beyond 8 cells per thread would spill)
-                if constexpr (sizeof(R) == 4 && CPT >= 2 && CPT <= 8)
+                if constexpr (sizeof(R) == 4 && CPT >= 2 && CPT <= 16)
                     split_fluxes_win2();
                 else
                     split_fluxes_win();
@@ -856,10 +850,11 @@ struct Slab {
 template <typename R>
 inline size_t slab_smem_bytes(int nx, int cpt, int threads)
 {
+    (void)threads;
     size_t e = (size_t)nx + 2 * GHOST;
-    if (sizeof(R) == 4 && cpt >= 2) {
+    if (sizeof(R) == 4 && cpt >= 2) {   // Slab<float, ..., cpt>::P
         const int ro = cpt >= 4 ? 1 : 2, r0 = (32 / cpt) % 32;
-        int P = threads + ro + 2;
+        int P = 512 + ro + 2;
         P += ((r0 - P % 32) % 32 + 32) % 32;
         e = (size_t)cpt * P;
     }

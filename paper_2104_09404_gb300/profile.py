@@ -3,7 +3,9 @@
     python -m paper_2104_09404_gb300.profile --case c2 --kernel relax --level 0 --reps 1
 
 (--kernel serial: 64 steps of mgrit_serial_step instead, on the sequential
-stepper the context chose at allocation.)
+stepper the context chose at allocation.)  The profiled launches run inside
+the NVTX range "profiled"; profile them with
+    ncu --nvtx --nvtx-include "profiled/" ...
 
 Cases: c2 = nx 4096, nt 16384, m 4, 6 levels, T 1 (the benchmark workload);
 small = nx 4096, nt 2048, m 4, 4 levels, T 0.125 (same kernel shape, 513
@@ -74,16 +76,27 @@ def main(argv=None):
     s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"], precision=a.precision)
     u0 = torch.as_tensor(inputs.fourier_ic(c["nx"], seed=0), device="cuda")
     if a.kernel == "serial":
-        # 64 serial steps on the sequential stepper the context chose
-        # (allocation times the candidates first: their launches come before)
+        # 64 serial steps on the sequential stepper the context chose, in the
+        # NVTX range "profiled" (allocation, which times the candidates,
+        # comes before it)
+        s.serial_step(u0, 1)
+        s.sync_status()
+        torch.cuda.nvtx.range_push("profiled")
         s.serial_step(u0, 64)
         s.sync_status()
+        torch.cuda.nvtx.range_pop()
         print("serial stepping x64 on case %s (grid CTAs %d, cluster CTAs %d)"
               % (a.case, s.query(3), s.query(2)))
         return 0
     s.run_cycles(u0, 0)
+    torch.cuda.synchronize()
+    # the launches to profile sit in the NVTX range "profiled" (the context's
+    # allocation times candidate kernel shapes first: ncu --nvtx
+    # --nvtx-include "profiled/" skips those)
+    torch.cuda.nvtx.range_push("profiled")
     s.launch_kernel(KERNELS[a.kernel], a.level, a.reps)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     print("launched %s level %d x%d on case %s" % (a.kernel, a.level, a.reps, a.case))
     return 0
 
