@@ -65,34 +65,45 @@ __device__ __forceinline__ void relax_chunk(SL &S, const SlabArgs<R> &a, const i
     // C_{j-1} (F- then C-relaxation of chunk j-1); F: C_j kept.  Then the
     // F-relaxation of chunk j from the new C_j.  Chunks are independent
     // (block-diagonal A_FF, Eq. AFF): no grid-wide synchronisation.
+    //
+    // The steps run as one loop with a single call of S.step (each call site
+    // compiles the whole time-stepper):
+    //   r = 0 .. nF-1        C-relaxation prefix from C_{j-1} (FCF, j > 0),
+    //                        then newC_j is stored;
+    //   r = nF (if cstep)    the coarse step Phi_{l+1}(newC_j) of the FAS
+    //                        term, then u is re-read from newC_j;
+    //   the next m steps     the F-relaxation of chunk j; the m-th gives
+    //                        Phi_l(u^{m(j+1)-1}) for the residual.
     const int nx = a.nx, m = a.m;
+    const int nF = (j > 0 && a.fcf) ? m : 0;
+    const bool coarse = a.cstep && j < a.nC;
+    const int total = nF + (j < a.nC ? (coarse ? 1 : 0) + m : 0);
     R u[CPT];
-    if (j == 0 || !a.fcf) {
-        S.load(u, rowp(a.uC, j, (int)a.strideC, a.nrows_uC));
-    } else {
-        S.load(u, rowp(a.uC, j - 1, (int)a.strideC, a.nrows_uC));
-        for (int r = 1; r <= m; ++r) {
-            S.step(u, a.dt);
-            if (a.g) S.add(u, rowp(a.g, (long long)m * (j - 1) + r, nx, a.nrows_g));
+    S.load(u, rowp(a.uC, nF ? j - 1 : j, (int)a.strideC, a.nrows_uC));
+    if (!nF && a.newC) S.store(u, rowp(a.newC, j, nx, a.nrows_newC));
+#pragma unroll 1
+    for (int r = 0; r < total; ++r) {
+        const bool is_coarse = coarse && r == nF;
+        if (SCHEME == SCH_LF_FE) S.psiM = is_coarse ? a.psiMc : a.psiM;
+        S.step(u, is_coarse ? a.dtc : a.dt);
+        if (r < nF) {                                   // C-relaxation prefix
+            if (a.g) S.add(u, rowp(a.g, (long long)m * (j - 1) + r + 1, nx, a.nrows_g));
+            if (r + 1 == nF && a.newC) S.store(u, rowp(a.newC, j, nx, a.nrows_newC));
+        } else if (is_coarse) {                         // coarse step of the FAS term
+            // u is then re-read from the row this thread just stored (its
+            // own cells), which saves CPT registers
+            S.store(u, rowp(a.cstep, j, nx, a.nrows_cstep));
+            S.load(u, rowp(a.newC, j, nx, a.nrows_newC));
+        } else {                                        // F-relaxation step q of chunk j
+            const int q = r - nF - (coarse ? 1 : 0) + 1;
+            if (q < m) {
+                if (a.g) S.add(u, rowp(a.g, (long long)m * j + q, nx, a.nrows_g));
+            } else {
+                S.store(u, rowp(a.phirow, j + 1, nx, a.nrows_phirow));
+            }
         }
     }
-    if (a.newC) S.store(u, rowp(a.newC, j, nx, a.nrows_newC));
-    if (j == a.nC) return;
-    if (a.cstep) {
-        // coarse step of the FAS term; u is then re-read from the row this
-        // thread just stored (its own cells), which saves CPT registers
-        if (SCHEME == SCH_LF_FE) S.psiM = a.psiMc;
-        S.step(u, a.dtc);
-        if (SCHEME == SCH_LF_FE) S.psiM = a.psiM;
-        S.store(u, rowp(a.cstep, j, nx, a.nrows_cstep));
-        S.load(u, rowp(a.newC, j, nx, a.nrows_newC));
-    }
-    for (int r = 1; r < m; ++r) {
-        S.step(u, a.dt);
-        if (a.g) S.add(u, rowp(a.g, (long long)m * j + r, nx, a.nrows_g));
-    }
-    S.step(u, a.dt);
-    S.store(u, rowp(a.phirow, j + 1, nx, a.nrows_phirow));
+    if (SCHEME == SCH_LF_FE) S.psiM = a.psiM;
 }
 
 template <typename SL, typename R>

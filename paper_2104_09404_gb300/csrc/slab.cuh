@@ -794,18 +794,31 @@ struct Slab {
                 if (cell(c) < nx) u[c] = RK<R>::euler(u[c], dt, A(c));
             return;
         }
+        // the three stages as one rolled loop, so that the flux pass is
+        // compiled once per call site of step() (the unrolled window code is
+        // large, and several copies of it miss in the instruction cache)
         R w[CPT];
-        fluxes(u);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? RK<R>::euler(u[c], dt, A(c)) : R(0);
-        fluxes(w);
+        for (int c = 0; c < CPT; ++c) w[c] = u[c];
+#pragma unroll 1
+        for (int st = 0; st < 3; ++st) {
+            fluxes(w);
+            if (st == 0) {
 #pragma unroll
-        for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) w[c] = RK<R>::stage2(u[c], w[c], dt, A(c));
-        fluxes(w);
+                for (int c = 0; c < CPT; ++c)
+                    if (cell(c) < nx) w[c] = RK<R>::euler(u[c], dt, A(c));
+            } else if (st == 1) {
 #pragma unroll
-        for (int c = 0; c < CPT; ++c)
-            if (cell(c) < nx) u[c] = RK<R>::stage3(u[c], w[c], dt, A(c));
+                for (int c = 0; c < CPT; ++c)
+                    if (cell(c) < nx) w[c] = RK<R>::stage2(u[c], w[c], dt, A(c));
+            } else {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (cell(c) < nx) w[c] = RK<R>::stage3(u[c], w[c], dt, A(c));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) u[c] = w[c];
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *__restrict__ row) const
