@@ -547,30 +547,35 @@ static int choose_seq(mgrit_ctx *ctx, GridLaunch *lg, int *kind, R *row)
     return MGRIT_OK;
 }
 
-// FP32 WENO5 slabs: the cells per thread of the one-CTA slab, chosen by
-// timing the level-0 relaxation with 1x, 2x and 4x the smallest that fits
-// (fewer, fuller threads let two CTAs share an SM and hide each other's
-// barriers) on min(chunks, 2 x SMs) chunks of a zero state; the choice gives
-// the same bits as any other (every FP32 shape performs the same operations)
-static int tune_slab32(mgrit_ctx *ctx)
+// WENO5 slabs: the cells per thread of the one-CTA slab, chosen by timing
+// the level-0 relaxation with 1x, 2x and 4x the smallest that fits (FP64:
+// up to 16 cells per thread) on min(chunks, 2 x SMs) chunks of a zero state.
+// Fewer, fuller threads let two CTAs share an SM and hide each other's
+// barriers.  Every shape performs the same operations per cell, so the
+// choice gives the same bits.
+template <typename R>
+static int tune_slab(mgrit_ctx *ctx)
 {
-    if (!ctx->f32 || ctx->scheme != MGRIT_WENO5_SSPRK3 || !ctx->ln32.slab) return MGRIT_OK;
+    const bool f32 = sizeof(R) == 4;
+    Launch &cur = f32 ? ctx->ln32 : ctx->ln64;
+    if (ctx->scheme != MGRIT_WENO5_SSPRK3 || !cur.slab) return MGRIT_OK;
+    const int ncpt = f32 ? NCPT : NCPT64;
     int ci0 = 0;
-    while (ci0 < NCPT && CPT_VALUES[ci0] != ctx->ln32.cpt) ++ci0;
-    SlabArgs<float> a = relax_args<float>(ctx, 0);
+    while (ci0 < ncpt && CPT_VALUES[ci0] != cur.cpt) ++ci0;
+    SlabArgs<R> a = relax_args<R>(ctx, 0);
     const int chunks = ctx->nC_l[0] + 1 < 2 * ctx->nsm ? ctx->nC_l[0] + 1 : 2 * ctx->nsm;
     cudaStream_t s = ctx->cap;
-    CK(cudaMemsetAsync(const_cast<float *>(a.uC), 0, sizeof(float) * (size_t)ctx->nx * chunks, s));
-    Launch best = ctx->ln32;
+    CK(cudaMemsetAsync(const_cast<R *>(a.uC), 0, sizeof(R) * (size_t)ctx->nx * chunks, s));
+    Launch best = cur;
     float best_ms = -1.f;
-    for (int ci = ci0; ci < NCPT && ci <= ci0 + 2; ++ci) {
+    for (int ci = ci0; ci < ncpt && ci <= ci0 + 2; ++ci) {
         const int cpt = CPT_VALUES[ci];
         const int need = (ctx->nx + cpt - 1) / cpt;
         Launch ln;
         ln.cpt = cpt;
         ln.threads = ((need + 31) / 32) * 32;
-        ln.smem = slab_smem_bytes<float>(ctx->nx, cpt, ln.threads);
-        ln.slab = table().slab32[ctx->scheme][ctx->flux][ci];
+        ln.smem = slab_smem_bytes<R>(ctx->nx, cpt, ln.threads);
+        ln.slab = f32 ? table().slab32[ctx->scheme][ctx->flux][ci] : table().slab64[ctx->scheme][ctx->flux][ci];
         if (!ln.slab || ln.smem > (size_t)SMEM_OPTIN) continue;
         CK(cudaFuncSetAttribute(ln.slab, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
         float ms = -1.f;
@@ -586,7 +591,7 @@ static int tune_slab32(mgrit_ctx *ctx)
             best = ln;
         }
     }
-    ctx->ln32 = best;
+    cur = best;
     return MGRIT_OK;
 }
 
@@ -633,11 +638,11 @@ int mgrit_ensure_alloc(mgrit_ctx *ctx)
     CK(cudaMalloc((void **)&ctx->gbuf.bar, sizeof(unsigned)));
     CK(cudaMalloc((void **)&ctx->gbuf.err, sizeof(int)));
     CK(cudaMemset(ctx->gbuf.err, 0, sizeof(int)));
-    // the timed choices run on rows the solve overwrites later: the FP32 slab
-    // shape on the level-0 C-point source, the FP64 sequential stepper on the
-    // level-0 C-point row buffer (FP64 mode) or a fresh FP64 row, the FP32
-    // one on the FP32 serial row
-    if ((st = tune_slab32(ctx))) return st;
+    // the timed choices run on rows the solve overwrites later: the slab
+    // shape (in the sweep precision) on the level-0 C-point source, the FP64
+    // sequential stepper on the level-0 C-point row buffer (FP64 mode) or a
+    // fresh FP64 row, the FP32 one on the FP32 serial row
+    if (ctx->f32 ? (st = tune_slab<float>(ctx)) : (st = tune_slab<double>(ctx))) return st;
     if (!ctx->f32) {
         if ((st = choose_seq<double>(ctx, &ctx->lg64, &ctx->seq64, static_cast<double *>(ctx->newC[0]))))
             return st;

@@ -26,6 +26,14 @@ measures the multiply-add throughput of the FP64 and FP32 pipes
 (mgrit_fma_probe: 152 x 8 CTAs of 256 threads, 8 independent chains per
 thread, ~0.1 s per launch, best of 3), the roofline denominators of the
 arithmetic-bound sweeps, and prints them in TFLOP/s.
+
+    python -m paper_2104_09404_gb300.profile --steppers
+
+times serial stepping (Burgers WENO5/SSPRK3, CFL 0.25, Fourier u0 seed 0) on
+each sequential stepper (one CTA, cluster, grid, and the one the context
+picks at allocation), FP64 and FP32, at nx = 1024, 2048, 4096 and 16384,
+with CUDA events around one mgrit_serial_step call, and prints microseconds
+per step with the cluster size and grid size used.
 """
 import argparse
 import sys
@@ -46,6 +54,8 @@ def main(argv=None):
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--adjoint", action="store_true")
     p.add_argument("--peaks", action="store_true", help="FP64 / FP32 multiply-add throughput")
+    p.add_argument("--steppers", action="store_true",
+                   help="microseconds per serial step on each sequential stepper")
     p.add_argument("--precision", type=int, default=64, choices=(64, 32),
                    help="32: the FP32-sweep instances of the kernels")
     a = p.parse_args(argv)
@@ -61,6 +71,8 @@ def main(argv=None):
             print("%-26s %8.3f TFLOP/s (best of 3; %s)" % (name, max(r) / 1e12,
                                                          ", ".join("%.3f" % (x / 1e12) for x in r)))
         return 0
+    if a.steppers:
+        return time_steppers(torch, inputs, mgrit)
     if a.adjoint:
         nx, nt = 2048, 8192
         s = mgrit.Solver(nx, nt, 4, 3, T=0.12)
@@ -98,6 +110,38 @@ def main(argv=None):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print("launched %s level %d x%d on case %s" % (a.kernel, a.level, a.reps, a.case))
+    return 0
+
+
+def time_steppers(torch, inputs, mgrit):
+    mgrit.load()
+    names = ((mgrit.SEQ_AUTO, "auto"), (mgrit.SEQ_ONE_CTA, "one CTA"),
+             (mgrit.SEQ_CLUSTER, "cluster"), (mgrit.SEQ_GRID, "grid"))
+    print("precision  nx      " + "".join("%-22s" % n for _, n in names))
+    for prec in (64, 32):
+        for nx, steps in ((1024, 2048), (2048, 2048), (4096, 2048), (16384, 1024)):
+            row = []
+            for k, _ in names:
+                if k == mgrit.SEQ_ONE_CTA and prec == 64 and nx > 8192:
+                    row.append("-")         # beyond the one-CTA FP64 slab
+                    continue
+                s = mgrit.Solver(nx, steps, 2, 2, T=0.25 * steps / nx, precision=prec,
+                                 seq_stepper=k)
+                u0 = torch.as_tensor(inputs.fourier_ic(nx, seed=0), device="cuda")
+                s.serial_step(u0, 4)
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record()
+                s.serial_step(u0, steps)
+                t1.record()
+                torch.cuda.synchronize()
+                s.sync_status()
+                us = 1e3 * t0.elapsed_time(t1) / steps
+                k2, g = s.query(2), s.query(3)
+                row.append("%.2f (%s)" % (us, "G=%d" % g if g else "K=%d" % k2))
+                s.close()
+            print("FP%-8d %-7d " % (prec, nx) + "".join("%-22s" % x for x in row), flush=True)
     return 0
 
 
