@@ -232,15 +232,14 @@ int mgrit_fma_probe(int kind, int iters, int blocks_per_sm, double *flops_out, v
  *
  * Returns MGRIT_EINVAL for bad arguments, for the cases above, or when
  * (nt/m + 1) * nx exceeds MGRIT_STATIC_SCRATCH_DOUBLES (nothing is launched),
- * MGRIT_ECUDA if a launch fails.  Asynchronous on `stream`; the caller reads norm_dev after
- * synchronising.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current) and raises the
- * kernel's shared-memory limit: make that first call before any stream
- * capture.  Calls outside capture look the address up again, so the entry
- * point keeps working after a device reset.  Every call shares the one array, so calls
- * that overlap on the GPU (other streams, other host threads) race; each
- * call overwrites every scratch value it reads before reading it, so no
- * state carries over between calls.
+ * MGRIT_ECUDA if a launch fails.  Asynchronous on `stream`; the caller
+ * reads norm_dev after synchronising.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress, with the caller's device current), so the
+ * entry point keeps working after a device reset; the first call on each
+ * device also raises the kernel's shared-memory limit.  Every call shares
+ * the one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race; each call overwrites every scratch value it reads before
+ * reading it, so no state carries over between calls.
  */
 #define MGRIT_STATIC_SCRATCH_DOUBLES (1 << 21)
 int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux, int numflux, double T,

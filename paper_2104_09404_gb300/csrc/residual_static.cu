@@ -50,30 +50,24 @@ const KernelTable &kernels()
 
 // Device address of the scratch array for the current device.  Host code may
 // not use &g_static_scratch (that is a host-side stand-in); the address is
-// looked up with the device current.  Outside stream capture it is looked up
-// again on every call, so that a context re-created after a device reset
-// (which loads the module, and the array, anew) gets its new address; during
-// capture the cached address is used.  The per-device record of raised
-// kernel attributes is dropped when the address changes.
-cudaError_t scratch_address(cudaStream_t s, double **out, int *dev_out)
+// looked up with the device current, on every call, so that a context
+// re-created after a device reset (which loads the module, and the array,
+// anew) gets its new address.  The per-device record of raised kernel
+// attributes is dropped when the address changes.
+cudaError_t scratch_address(double **out, int *dev_out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    e = cudaStreamIsCapturing(s, &cs);
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup &d = g_dev[dev];
-    if (cs == cudaStreamCaptureStatusNone || !d.scratch) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        if (static_cast<double *>(p) != d.scratch) {
-            memset(&d, 0, sizeof d);
-            d.scratch = static_cast<double *>(p);
-        }
+    if (static_cast<double *>(p) != d.scratch) {
+        memset(&d, 0, sizeof d);
+        d.scratch = static_cast<double *>(p);
     }
     *out = d.scratch;
     *dev_out = dev;
@@ -136,7 +130,7 @@ extern "C" int mgrit_residual_static(int nx, int nt, int m, int scheme, int flux
     cudaStream_t s = (cudaStream_t)stream;
     double *scratch = nullptr;
     int dev = 0;
-    if (scratch_address(s, &scratch, &dev) != cudaSuccess) return MGRIT_ECUDA;
+    if (scratch_address(&scratch, &dev) != cudaSuccess) return MGRIT_ECUDA;
     double *rows = scratch;
     double *partials = scratch + ROWS_MAX;
     if (raise_smem_once(dev, scheme, flux, ci, slab) != cudaSuccess) return MGRIT_ECUDA;
