@@ -94,7 +94,7 @@ inline size_t adj_smem_bytes(int nx)
 
 template <typename R, int SCHEME, int FLUX, int CPT>
 struct AdjSlab {
-    Slab<R, SCHEME, FLUX, CPT> F;   // forward stage recomputation
+    Slab<R, SCHEME, FLUX, CPT, true> F;   // forward stage recomputation (flat layout)
     R *cg, *mu, *sred;
     int *ired;
     int nx;

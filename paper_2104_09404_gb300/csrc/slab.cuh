@@ -426,7 +426,27 @@ struct RK {
     }
 };
 
-template <typename R, int SCHEME, int FLUX, int CPT>
+// Run stride of the run-major layout of Slab below for a CTA of `threads`
+// threads: the runs 0 .. threads + RO + 1 (RO runs of left ghosts, the
+// threads' runs, the right ghosts), rounded up so that the interleaved writes
+// of 32 consecutive cells hit distinct banks: P = 32/CPT (mod 32) for FP32
+// (one word per bank), P = 16/CPT (mod 16) for FP64 (a double spans two
+// banks, and a warp's doubles are served in two halves).  FP32 sizes it for
+// the largest CTA (512 threads), so that it is a compile-time constant of
+// the CTA shape; FP64 sizes it for the launch, whose slab is twice as large.
+template <typename R>
+__host__ __device__ constexpr int slab_run_stride(int cpt, int threads)
+{
+    const int ro = cpt >= 4 ? 1 : 2;
+    const int p0 = (sizeof(R) == 4 ? 512 : threads) + ro + 2;
+    const int bank = sizeof(R) == 4 ? 32 : 16;
+    const int r0 = cpt <= bank ? (bank / cpt) % bank : 0;
+    return p0 + ((r0 - p0 % bank) % bank + bank) % bank;
+}
+
+// FLAT: keep every cell at slot i + GHOST whatever CPT (the adjoint slab,
+// which overlays its own arrays on that layout)
+template <typename R, int SCHEME, int FLUX, int CPT, bool FLAT = false>
 struct Slab {
     R *qa;        // slots of cells -3..nx+2: f^+ / 2 (WENO5 split form), f^+ (first
                   // order), or the stage state (state form, Roe)
@@ -444,36 +464,39 @@ struct Slab {
     R psiDt;
     static constexpr int kScheme = SCHEME, kCpt = CPT;
 
-    // Shared-array layout.  FP64 slabs keep cell i (i = -3 .. nx+2) at slot
-    // i + GHOST: they are bound by the FP64 pipe, not by shared memory, and
-    // the adjoint slab overlays that layout.  FP32 slabs with CPT >= 2 use a
-    // run-major layout: the window pass gives thread t the run of interfaces
-    // t*CPT .. t*CPT + CPT - 1, and cell i sits at slot k * P + r with
-    // r = (i + RO*CPT) / CPT (its run, after RO runs of left ghosts) and
-    // k = (i + RO*CPT) mod CPT.  Lanes reading element k of consecutive runs
-    // then touch consecutive slots, and a window step is a constant offset;
-    // P = 32/CPT (mod 32) keeps the interleaved writes of 32 consecutive
-    // cells on 32 distinct banks too.  The interface flux F_{i+1/2} is kept at
-    // cell i of qf (F_{-1/2} at cell -1).
-    static constexpr bool TL = sizeof(R) == 4 && CPT >= 2;
+    // Shared-array layout.  Slabs with CPT >= 2 use a run-major layout: the
+    // window pass gives thread t the run of interfaces t*CPT .. t*CPT + CPT - 1,
+    // and cell i sits at slot k * P + r with r = (i + RO*CPT) / CPT (its run,
+    // after RO runs of left ghosts) and k = (i + RO*CPT) mod CPT.  Lanes
+    // reading element k of consecutive runs then touch consecutive slots, a
+    // window step is a constant offset, and the run stride P
+    // (slab_run_stride) keeps the interleaved writes of 32 consecutive cells
+    // free of bank conflicts too.  CPT = 1 slabs (and FLAT ones) keep cell i
+    // (i = -3 .. nx+2) at slot i + GHOST.  The interface flux F_{i+1/2} is
+    // kept at cell i of qf (F_{-1/2} at cell -1).
+    static constexpr bool TL = !FLAT && CPT >= 2;
     static constexpr int LOG = CPT >= 32 ? 5 : CPT >= 16 ? 4 : CPT >= 8 ? 3 : CPT >= 4 ? 2 : CPT >= 2 ? 1 : 0;
     static constexpr int RO = CPT >= 4 ? 1 : 2;
-    // run stride of the FP32 layout: sized for the largest CTA (512 threads)
-    // and fixed per CTA shape, so that every window slot is the thread's base
-    // plus a compile-time constant
-    static constexpr int P0 = 512 + RO + 2;
-    static constexpr int P = P0 + ((((32 / CPT) % 32) - P0 % 32) % 32 + 32) % 32;
+    // FP32: the run stride as a compile-time constant
+    static constexpr int P32 = slab_run_stride<float>(CPT, 512);
     // elements of each of qa, qb, qf
-    static __host__ __device__ __forceinline__ int extent(int nx) { return TL ? CPT * P : nx + 2 * GHOST; }
+    static __host__ __device__ __forceinline__ int extent(int nx, int threads)
+    {
+        return TL ? CPT * slab_run_stride<R>(CPT, threads) : nx + 2 * GHOST;
+    }
 
     int E;        // elements per array
     int pstride;  // slot distance between a thread's consecutive interleaved cells
+    int prun;     // run stride (FP64; FP32 uses P32)
+
+    __device__ __forceinline__ int P() const { return sizeof(R) == 4 ? P32 : prun; }
 
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
         : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))
     {
         const int T = (int)blockDim.x;
-        E = extent(nx);
+        E = extent(nx, T);
+        prun = slab_run_stride<R>(CPT, T);
         // blockDim.x is a multiple of 32, hence of CPT: cell t + c*T + o sits at
         // sl(t + o) + c * pstride
         pstride = TL ? T / CPT : T;
@@ -491,7 +514,7 @@ struct Slab {
     {
         if (!TL) return i + GHOST;
         const int v = i + RO * CPT;
-        return (v & (CPT - 1)) * P + (v >> LOG);
+        return (v & (CPT - 1)) * P() + (v >> LOG);
     }
     __device__ __forceinline__ R &ce(R *arr, int i) const { return MGRIT_SH(arr, sl(i), lim()); }
     __device__ __forceinline__ R ce(const R *arr, int i) const { return MGRIT_SH(arr, sl(i), lim()); }
@@ -526,7 +549,7 @@ struct Slab {
     {
         if (!TL) return (int)threadIdx.x * CPT + m + GHOST;
         const int mm = m + RO * CPT;   // >= 0
-        return (mm & (CPT - 1)) * P + (int)threadIdx.x + (mm >> LOG);
+        return (mm & (CPT - 1)) * P() + (int)threadIdx.x + (mm >> LOG);
     }
 
     // left-biased reconstruction at i+1/2 from the cells around i
@@ -863,14 +886,7 @@ struct Slab {
 template <typename R>
 inline size_t slab_smem_bytes(int nx, int cpt, int threads)
 {
-    (void)threads;
-    size_t e = (size_t)nx + 2 * GHOST;
-    if (sizeof(R) == 4 && cpt >= 2) {   // Slab<float, ..., cpt>::P
-        const int ro = cpt >= 4 ? 1 : 2, r0 = (32 / cpt) % 32;
-        int P = 512 + ro + 2;
-        P += ((r0 - P % 32) % 32 + 32) % 32;
-        e = (size_t)cpt * P;
-    }
+    const size_t e = cpt >= 2 ? (size_t)cpt * slab_run_stride<R>(cpt, threads) : (size_t)nx + 2 * GHOST;
     return sizeof(R) * (3 * e + NWARP_MAX);
 }
 
