@@ -292,14 +292,15 @@ struct AdjSlab {
         // u2 = 3/4 u + 1/4 u1 + 1/4 dt A(u1) (kept in v)
         {
             R w[CPT];
+            const typename RK<R>::Coef K = F.coef(dt);
             F.fluxes(v);
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? RK<R>::euler(v[c], dt, F.A(c)) : R(0);
+            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < nx) ? RK<R>::euler(v[c], K, F.df(c)) : R(0);
             F.store(w, st);
             F.fluxes(w);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                v[c] = (cell(c) < nx) ? RK<R>::stage2(v[c], w[c], dt, F.A(c)) : R(0);
+                v[c] = (cell(c) < nx) ? RK<R>::stage2(v[c], w[c], K, F.df(c)) : R(0);
         }
         // stage 3: out = 1/3 u + 2/3 u2 + 2/3 dt A(u2)
         //   lam_u += 1/3 lam;  l2 = 2/3 lam + A'(u2)^T (dt l2_0), l2_0 = 2/3 lam

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(512) k_slab_batch(const SlabArgs<R> *__restric
     const SlabArgs<R> a = args[it.args];
     extern __shared__ __align__(16) unsigned char smem[];
     Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
+    S.pair_div = a.mode != MODE_SEQ;
     if (a.mode == MODE_RELAX)
         relax_chunk(S, a, it.chunk);
     else if (a.mode == MODE_INTERP)

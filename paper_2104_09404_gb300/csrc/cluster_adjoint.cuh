@@ -267,14 +267,15 @@ struct ClusterAdj {
         }
         {
             R w[CPT];
+            const typename RK<R>::Coef K = F.coef(dt);
             F.fluxes(v, (stage++) & 1);
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < F.n) ? RK<R>::euler(v[c], dt, F.A(c)) : R(0);
+            for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < F.n) ? RK<R>::euler(v[c], K, F.df(c)) : R(0);
             F.store(w, st);
             F.fluxes(w, (stage++) & 1);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                v[c] = (cell(c) < F.n) ? RK<R>::stage2(v[c], w[c], dt, F.A(c)) : R(0);
+                v[c] = (cell(c) < F.n) ? RK<R>::stage2(v[c], w[c], K, F.df(c)) : R(0);
         }
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {

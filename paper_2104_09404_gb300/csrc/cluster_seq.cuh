@@ -235,34 +235,40 @@ struct ClusterSlab {
         __syncthreads();
     }
 
-    __device__ __forceinline__ R A(int c) const
+    // dG of owned slot c (see RK) and the stage coefficients of a step
+    __device__ __forceinline__ R df(int c) const
     {
         const int i = cell(c);
-        return RK<R>::A(Ar<R>::sub(MGRIT_SH(qf, i + 1, nmax + 2), MGRIT_SH(qf, i, nmax + 2)), dxinv);
+        return Ar<R>::sub(MGRIT_SH(qf, i + 1, nmax + 2), MGRIT_SH(qf, i, nmax + 2));
+    }
+    __device__ __forceinline__ typename RK<R>::Coef coef(R dt) const
+    {
+        return RK<R>::coef(dt, dxinv, flux_scale<R>(SCHEME == SCH_WENO5_SSPRK3 && numflux == NF_SPLIT));
     }
 
     // u <- Phi(u); stage buffers alternate with the global stage counter
     __device__ __forceinline__ void step(R (&u)[CPT], R dt, int &stage)
     {
+        const typename RK<R>::Coef K = coef(dt);
         if (SCHEME == SCH_FO_FE) {
             fluxes(u, (stage++) & 1);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < n) u[c] = RK<R>::euler(u[c], dt, A(c));
+                if (cell(c) < n) u[c] = RK<R>::euler(u[c], K, df(c));
             return;
         }
         R w[CPT];
         fluxes(u, (stage++) & 1);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < n) ? RK<R>::euler(u[c], dt, A(c)) : R(0);
+        for (int c = 0; c < CPT; ++c) w[c] = (cell(c) < n) ? RK<R>::euler(u[c], K, df(c)) : R(0);
         fluxes(w, (stage++) & 1);
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) w[c] = RK<R>::stage2(u[c], w[c], dt, A(c));
+            if (cell(c) < n) w[c] = RK<R>::stage2(u[c], w[c], K, df(c));
         fluxes(w, (stage++) & 1);
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-            if (cell(c) < n) u[c] = RK<R>::stage3(u[c], w[c], dt, A(c));
+            if (cell(c) < n) u[c] = RK<R>::stage3(u[c], w[c], K, df(c));
     }
 
     __device__ __forceinline__ void load(R (&u)[CPT], const R *row) const

@@ -213,20 +213,23 @@ __global__ void __launch_bounds__(GRID_THREADS) k_seq_grid(GridArgs<R> ga)
         return true;
     };
 
-    auto A = [&]() -> R { return RK<R>::A(AR::sub(qf[t + 1], qf[t]), a.dxinv); };
+    // dG of the own cell and the stage coefficients (see RK): the WENO5
+    // split form stores G = 3F
+    auto df = [&]() -> R { return AR::sub(qf[t + 1], qf[t]); };
+    const typename RK<R>::Coef K = RK<R>::coef(a.dt, a.dxinv, flux_scale<R>(SCHEME == SCH_WENO5_SSPRK3));
 
     bool alive = true;
     for (int i = 1; i <= a.nsteps && alive; ++i) {
         if (SCHEME == SCH_FO_FE) {
             if (!(alive = fluxes(u))) break;
-            if (own) u = RK<R>::euler(u, a.dt, A());
+            if (own) u = RK<R>::euler(u, K, df());
         } else {
             if (!(alive = fluxes(u))) break;
-            R w = own ? RK<R>::euler(u, a.dt, A()) : R(0);
+            R w = own ? RK<R>::euler(u, K, df()) : R(0);
             if (!(alive = fluxes(w))) break;
-            if (own) w = RK<R>::stage2(u, w, a.dt, A());
+            if (own) w = RK<R>::stage2(u, w, K, df());
             if (!(alive = fluxes(w))) break;
-            if (own) u = RK<R>::stage3(u, w, a.dt, A());
+            if (own) u = RK<R>::stage3(u, w, K, df());
         }
         if (own && a.g) u = R((double)u + a.g[(long long)i * nx + lo + t]);
         if (own && a.rows) a.rows[(long long)i * nx + lo + t] = u;

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(512) k_slab(SlabArgs<R> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Slab<R, SCHEME, FLUX, CPT> S(smem, a.nx, a.dxinv, a.numflux);
+    S.pair_div = a.mode != MODE_SEQ;
     if (SCHEME == SCH_LF_FE) {
         S.psiM = a.psiM;
         S.psiOrder = a.psiOrder;

@@ -353,11 +353,12 @@ struct WenoWin {
 };
 
 // interface flux F = W^-(f^+) + W^+(f^-) from the two windows and the base
-// values qp = q^+_i, qm = q^-_{i+1} (Burgers):
-//   F = 2 (q^+_i + q^-_{i+1}) + (N^+ D^- - N^- D^+) / (3 D^+ D^-)
-// with one division in FP64 (each D lies in [1e-23, 1e33] for |q| <= 1e3, so
-// the product stays far inside the FP64 range) and two in FP32
-// the combination of the two reconstructions' (N, D) and base values
+// values qp = q^+_i, qm = q^-_{i+1} (Burgers), returned as G = 3F:
+//   G = 6 (q^+_i + q^-_{i+1}) + (N^+ D^- - N^- D^+) / (D^+ D^-)
+// (the factor 1/3 of the reconstructions is applied with dt/dx in the stage
+// update, see RK), with one division in FP64 (each D lies in [1e-23, 1e33]
+// for |q| <= 1e3, so the product stays far inside the FP64 range) and two in
+// FP32
 template <typename V>
 __device__ __forceinline__ V split_flux_combine(V Np, V Dp, V Nm, V Dm, V qp, V qm)
 {
@@ -365,11 +366,46 @@ __device__ __forceinline__ V split_flux_combine(V Np, V Dp, V Nm, V Dm, V qp, V 
     const V base = A::add(qp, qm);
     if constexpr (std::is_same<V, double>::value) {
         const V num = A::fma(Np, Dm, A::neg(A::mul(Nm, Dp)));
-        const V den = A::mul(A::k(3.0), A::mul(Dp, Dm));
-        return A::fma(A::k(2.0), base, A::div(num, den));
+        return A::fma(A::k(6.0), base, A::div(num, A::mul(Dp, Dm)));
     } else {
-        const V fr = A::sub(A::div(Np, A::mul(A::k(3.0), Dp)), A::div(Nm, A::mul(A::k(3.0), Dm)));
-        return A::fma(A::k(2.0), base, fr);
+        return A::fma(A::k(6.0), base, A::sub(A::div(Np, Dp), A::div(Nm, Dm)));
+    }
+}
+
+// FP64: the numerator and denominator of split_flux_combine's fraction, and
+// its base term, for an interface whose division is shared with its pair
+// partner (split_flux_pair)
+struct SplitParts {
+    double num, den, base;
+};
+__device__ __forceinline__ SplitParts split_flux_parts(double Np, double Dp, double Nm, double Dm, double qp,
+                                                       double qm)
+{
+    using A = Ar<double>;
+    SplitParts r;
+    r.base = A::add(qp, qm);
+    r.num = A::fma(Np, Dm, A::neg(A::mul(Nm, Dp)));
+    r.den = A::mul(Dp, Dm);
+    return r;
+}
+// G of two interfaces from one reciprocal: with d = den0 den1 and i = 1/d
+// (correctly rounded), num0/den0 = num0 (den1 i) and num1/den1 =
+// num1 (den0 i), each quotient within three roundings.  Each D lies in
+// [1e-23, 1e33] for |q| <= 1e3, so d lies in [1e-92, 1e132]; where d falls
+// outside [2^-996, 2^997] (tested on its exponent bits, on the integer pipe)
+// the two plain divisions are taken instead.
+__device__ __forceinline__ void split_flux_pair(const SplitParts &a, const SplitParts &b, double &Ga, double &Gb)
+{
+    using A = Ar<double>;
+    const double d = A::mul(a.den, b.den);
+    const unsigned e = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;   // biased exponent (sign: d > 0)
+    if (e - 27u <= 1993u) {
+        const double inv = __drcp_rn(d);
+        Ga = A::fma(6.0, a.base, A::mul(a.num, A::mul(b.den, inv)));
+        Gb = A::fma(6.0, b.base, A::mul(b.num, A::mul(a.den, inv)));
+    } else {
+        Ga = A::fma(6.0, a.base, A::div(a.num, a.den));
+        Gb = A::fma(6.0, b.base, A::div(b.num, b.den));
     }
 }
 
@@ -383,21 +419,23 @@ __device__ __forceinline__ V split_flux_win(const WenoWin<V> &P, const WenoWin<V
 }
 
 // advection (alpha = 1): f^- = (u - u)/2 is zero, so its reconstruction is
-// exactly zero and F = W^-(f^+) = 2 q^+_i + N^+ / (3 D^+)
+// exactly zero and G = 3 W^-(f^+) = 6 q^+_i + N^+ / D^+
 template <typename V>
 __device__ __forceinline__ V split_flux_win_adv(const WenoWin<V> &P, V qp)
 {
     using A = Ar<V>;
     V Np, Dp;
     P.left(Np, Dp);
-    return A::fma(A::k(2.0), qp, A::div(Np, A::mul(A::k(3.0), Dp)));
+    return A::fma(A::k(6.0), qp, A::div(Np, Dp));
 }
 
 // Runge-Kutta stage updates of Eq. (SSPRK3) and forward Euler (Eq. SSPRK1)
-// from the flux difference dF = F_{i+1/2} - F_{i-1/2} of a cell, with
-// explicit rounding: the one-CTA slab, the cluster stepper and the grid
-// stepper perform the same operations, so a chain of steps gives the same
-// bits on each of them.
+// from the difference dG = G_{i+1/2} - G_{i-1/2} of a cell's interface
+// values G = F / s (s = 1/3 for the WENO5 split form, whose G is 3F; s = 1
+// otherwise), so that dt A_i = k1 dG with k1 = -(dt/dx) s (Eq. spaceDisc).
+// The coefficients are formed once per step (coef), and every stepper (the
+// one-CTA slab, the cluster stepper, the grid stepper) performs the same
+// operations, so a chain of steps gives the same bits on each of them.
 //  - FP64: the Shu-Osher combinations as written, 3/4 u + 1/4 w + 1/4 dt A
 //    and 1/3 u + 2/3 w + 2/3 dt A (closest to the oracle's operation order);
 //  - FP32: the same combinations in increment form, u + 1/4 ((w - u) + dt A)
@@ -408,23 +446,41 @@ template <typename R>
 struct RK {
     using A_ = Ar<R>;
     static constexpr bool INC = sizeof(R) == 4;
-    // A_i = -(F_{i+1/2} - F_{i-1/2}) / dx
-    static __device__ __forceinline__ R A(R dF, R dxinv) { return A_::mul(A_::neg(dxinv), dF); }
-    // u + dt A (forward Euler; the first SSPRK3 stage)
-    static __device__ __forceinline__ R euler(R u, R dt, R a) { return A_::fma(dt, a, u); }
-    // 3/4 u + 1/4 w + 1/4 dt A
-    static __device__ __forceinline__ R stage2(R u, R w, R dt, R a)
+    struct Coef {
+        R k1;   // -(dt/dx) s: dt A = k1 dG
+        R k2;   // k1 / 4 (FP64 stage 2)
+        R k3;   // 2/3 k1 (FP64 stage 3)
+    };
+    static __device__ __forceinline__ Coef coef(R dt, R dxinv, R s)
     {
-        if (INC) return A_::fma(R(0.25), A_::fma(dt, a, A_::sub(w, u)), u);
-        return A_::fma(R(0.75), u, A_::fma(R(0.25), w, A_::mul(A_::mul(R(0.25), dt), a)));
+        Coef c;
+        c.k1 = A_::mul(A_::mul(A_::neg(dt), dxinv), s);
+        c.k2 = A_::mul(R(0.25), c.k1);
+        c.k3 = A_::mul(R(2.0 / 3.0), c.k1);
+        return c;
+    }
+    // u + dt A (forward Euler; the first SSPRK3 stage)
+    static __device__ __forceinline__ R euler(R u, const Coef &c, R dG) { return A_::fma(c.k1, dG, u); }
+    // 3/4 u + 1/4 w + 1/4 dt A
+    static __device__ __forceinline__ R stage2(R u, R w, const Coef &c, R dG)
+    {
+        if (INC) return A_::fma(R(0.25), A_::fma(c.k1, dG, A_::sub(w, u)), u);
+        return A_::fma(R(0.75), u, A_::fma(R(0.25), w, A_::mul(c.k2, dG)));
     }
     // 1/3 u + 2/3 w + 2/3 dt A
-    static __device__ __forceinline__ R stage3(R u, R w, R dt, R a)
+    static __device__ __forceinline__ R stage3(R u, R w, const Coef &c, R dG)
     {
-        if (INC) return A_::fma(R(2.0 / 3.0), A_::fma(dt, a, A_::sub(w, u)), u);
-        return A_::fma(R(1.0 / 3.0), u, A_::fma(R(2.0 / 3.0), w, A_::mul(A_::mul(R(2.0 / 3.0), dt), a)));
+        if (INC) return A_::fma(R(2.0 / 3.0), A_::fma(c.k1, dG, A_::sub(w, u)), u);
+        return A_::fma(R(1.0 / 3.0), u, A_::fma(R(2.0 / 3.0), w, A_::mul(c.k3, dG)));
     }
 };
+
+// s of RK: the WENO5 split form stores G = 3F (split_flux_combine)
+template <typename R>
+__device__ __forceinline__ R flux_scale(bool weno_split)
+{
+    return weno_split ? R(1.0 / 3.0) : R(1);
+}
 
 // Run stride of the run-major layout of Slab below for a CTA of `threads`
 // threads: the runs 0 .. threads + RO + 1 (RO runs of left ghosts, the
@@ -462,6 +518,11 @@ struct Slab {
     // (psiOrder 0, Eq. coarseLFord0) or first order (1, Eq. coarseLFord1)
     int psiM, psiOrder;
     R psiDt;
+    // FP64 WENO5 split form: interfaces in pairs share one reciprocal
+    // (split_flux_pair).  Set by the relaxation and interpolation sweeps; the
+    // sequential chains keep one division per interface, the operations of
+    // the cluster and grid steppers.
+    bool pair_div;
     static constexpr int kScheme = SCHEME, kCpt = CPT;
 
     // Shared-array layout.  Slabs with CPT >= 2 use a run-major layout: the
@@ -492,7 +553,7 @@ struct Slab {
     __device__ __forceinline__ int P() const { return sizeof(R) == 4 ? P32 : prun; }
 
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
-        : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0))
+        : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0)), pair_div(false)
     {
         const int T = (int)blockDim.x;
         E = extent(nx, T);
@@ -574,10 +635,11 @@ struct Slab {
 
     // WENO5 split fluxes of the interfaces i0 .. i0 + CPT - 1 (i0 = t * CPT)
     // from qa = f^+/2 and qb = f^-/2, one sliding window per array (see
-    // WenoWin).  Reads cells i0 - 2 .. i0 + n + 2, all inside the arrays for
-    // every interface i < nx.  FP64: a rolled loop (the window shifts by
-    // register moves; unrolled, the slabs spill); FP32: unrolled, so that
-    // every slot is the thread's base plus a constant.
+    // WenoWin), stored as G = 3F.  Reads cells i0 - 2 .. i0 + n + 2, all inside
+    // the arrays for every interface i < nx.  FP64: a rolled loop (the window
+    // shifts by register moves; unrolled, the slabs spill), two interfaces per
+    // iteration when pair_div is set; FP32: unrolled, so that every slot is
+    // the thread's base plus a constant.
     __device__ __forceinline__ void split_fluxes_win() const
     {
         const int i0 = threadIdx.x * CPT;
@@ -588,6 +650,39 @@ struct Slab {
         WenoWin<R> P, M;
         P.init(A_(-2), A_(-1), A_(0), A_(1), A_(2));
         if (FLUX == FLX_BURGERS) M.init(B_(-1), B_(0), B_(1), B_(2), B_(3));
+        if constexpr (sizeof(R) == 8 && FLUX == FLX_BURGERS && CPT >= 2) {
+            if (pair_div) {
+                // interfaces (k, k+1), k even: i0 is even, so the pairs are
+                // the global pairs (2j, 2j+1) whatever CPT; a last interface
+                // without its partner (n odd) takes the plain division
+#pragma unroll 1
+                for (int k = 0; k < n; k += 2) {
+                    R Np, Dp, Nm, Dm;
+                    P.left(Np, Dp);
+                    M.right(Nm, Dm);
+                    const SplitParts x = split_flux_parts(Np, Dp, Nm, Dm, A_(k), B_(k + 1));
+                    if (k + 1 >= n) {
+                        MGRIT_SH(qf, rs(k), lim()) = Ar<R>::fma(6.0, x.base, Ar<R>::div(x.num, x.den));
+                        break;
+                    }
+                    P.advance(A_(k + 3));
+                    M.advance(B_(k + 4));
+                    P.left(Np, Dp);
+                    M.right(Nm, Dm);
+                    const SplitParts y = split_flux_parts(Np, Dp, Nm, Dm, A_(k + 1), B_(k + 2));
+                    R G0, G1;
+                    split_flux_pair(x, y, G0, G1);
+                    MGRIT_SH(qf, rs(k), lim()) = G0;
+                    MGRIT_SH(qf, rs(k + 1), lim()) = G1;
+                    if (k + 2 < n) {
+                        P.advance(A_(k + 4));
+                        M.advance(B_(k + 5));
+                    }
+                }
+                if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
+                return;
+            }
+        }
 #pragma unroll(sizeof(R) == 4 ? CPT : 1)
         for (int k = 0; k < CPT; ++k) {
             if (k >= n) break;
@@ -599,7 +694,7 @@ struct Slab {
                 if (FLUX == FLX_BURGERS) M.advance(B_(k + 4));
             }
         }
-        // F_{-1/2} = F_{nx-1/2}, from the thread whose run ends at nx - 1
+        // G_{-1/2} = G_{nx-1/2}, from the thread whose run ends at nx - 1
         if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
     }
 
@@ -744,11 +839,16 @@ struct Slab {
         __syncthreads();
     }
 
-    // A_i(w) = -(F_{i+1/2} - F_{i-1/2}) / dx for owned slot c (Eq. spaceDisc);
-    // valid after fluxes().
-    __device__ __forceinline__ R A(int c) const
+    // dG_i = G_{i+1/2} - G_{i-1/2} for owned slot c, valid after fluxes():
+    // dt A_i(w) = k1 dG_i (Eq. spaceDisc; RK)
+    __device__ __forceinline__ R df(int c) const
     {
-        return RK<R>::A(Ar<R>::sub(MGRIT_SH(qf, pc(c, 0), lim()), MGRIT_SH(qf, pc(c, -1), lim())), dxinv);
+        return Ar<R>::sub(MGRIT_SH(qf, pc(c, 0), lim()), MGRIT_SH(qf, pc(c, -1), lim()));
+    }
+    // the stage coefficients of a step of size dt
+    __device__ __forceinline__ typename RK<R>::Coef coef(R dt) const
+    {
+        return RK<R>::coef(dt, dxinv, flux_scale<R>(SCHEME == SCH_WENO5_SSPRK3 && numflux == NF_SPLIT));
     }
 
     // Eq. (fineLF): u <- E u - dt D f(u), (E v)_i = (v_{i+1} + v_{i-1})/2,
@@ -810,11 +910,12 @@ struct Slab {
             lf_step(u, dt);
             return;
         }
+        const typename RK<R>::Coef K = coef(dt);
         if (SCHEME == SCH_FO_FE) {
             fluxes(u);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
-                if (cell(c) < nx) u[c] = RK<R>::euler(u[c], dt, A(c));
+                if (cell(c) < nx) u[c] = RK<R>::euler(u[c], K, df(c));
             return;
         }
         // the three stages as one rolled loop, so that the flux pass is
@@ -829,15 +930,15 @@ struct Slab {
             if (st == 0) {
 #pragma unroll
                 for (int c = 0; c < CPT; ++c)
-                    if (cell(c) < nx) w[c] = RK<R>::euler(u[c], dt, A(c));
+                    if (cell(c) < nx) w[c] = RK<R>::euler(u[c], K, df(c));
             } else if (st == 1) {
 #pragma unroll
                 for (int c = 0; c < CPT; ++c)
-                    if (cell(c) < nx) w[c] = RK<R>::stage2(u[c], w[c], dt, A(c));
+                    if (cell(c) < nx) w[c] = RK<R>::stage2(u[c], w[c], K, df(c));
             } else {
 #pragma unroll
                 for (int c = 0; c < CPT; ++c)
-                    if (cell(c) < nx) w[c] = RK<R>::stage3(u[c], w[c], dt, A(c));
+                    if (cell(c) < nx) w[c] = RK<R>::stage3(u[c], w[c], K, df(c));
             }
         }
 #pragma unroll
