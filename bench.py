@@ -27,6 +27,7 @@ import ctypes
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -38,6 +39,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(nx=4096, nt=16384, m=4, levels=6, T=1.0, seed=0)
 SAMPLE = dict(nx=4096, nt=4096, m=4, levels=6, T=0.25, seed=0)   # CPU baseline sample
+SAMPLE1 = dict(nx=4096, nt=1024, m=4, levels=5, T=0.0625, seed=0)  # single-thread sample
 
 # Algorithmic FLOPs per cell update of one SSPRK3 step of WENO5-JS with the
 # global LF splitting (Burgers): the operations the paper's formulas take, as
@@ -209,6 +211,38 @@ def oracle_cycle_rate(sample, cycles=1):
     return upd / dt, dt, O.num_threads()
 
 
+def oracle_single_thread(sample):
+    """The oracle on one host thread (OMP_NUM_THREADS=1, in a child process
+    so that the parent's thread pool is untouched) over one V-cycle of
+    `sample`: (cell updates/s, seconds)."""
+    code = ("import json, time, oracle as O\n"
+            "from paper_2104_09404_gb300 import inputs\n"
+            "s = json.loads(%r)\n"
+            "O.build()\n"
+            "u0 = inputs.fourier_ic(s['nx'], seed=s['seed'])\n"
+            "t0 = time.perf_counter()\n"
+            "O.vcycles(u0, s['nt'], s['m'], s['levels'], s['T'], 1)\n"
+            "print(json.dumps([time.perf_counter() - t0, O.num_threads()]))\n" % json.dumps(sample))
+    env = dict(os.environ, OMP_NUM_THREADS="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT,
+                       timeout=600)
+    if r.returncode != 0:
+        return None
+    secs, threads = json.loads(r.stdout.strip().splitlines()[-1])
+    return cycle_updates(sample) / secs, secs, threads
+
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=30).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cycle_updates(w, fcf=True):
     # cells x Phi applications of one V-cycle (same count as mgrit_cycle_cell_updates)
     m, L = w["m"], w["levels"]
@@ -332,7 +366,7 @@ def adjoint_gradient(mgrit, inputs, dev, stream):
 C4 = dict(nx=16384, nt=65536, m=8, levels=3)
 
 
-def config4(mgrit, inputs, dev, timed_ms, rel_errs):
+def config4(mgrit, inputs, dev, timed_ms, rel_errs, peaks):
     """Config 4: Burgers, nx=16384, nt=65536, m=8, FP32 WENO5/SSPRK3 sweeps with
     FP64 tau correction, residual norms and coarsest solve; u0 = 0.5 + sin 2 pi x
     (breaks at t = 0.159); smooth T=0.12 and shocked T=0.5.
@@ -375,6 +409,18 @@ def config4(mgrit, inputs, dev, timed_ms, rel_errs):
                             "speedup_vs_fp32_serial": ser32_ms / stats.t_total_ms,
                             "error_vs_fp64_serial": rel_errs(uT, uT64),
                             "serial_fp32_error_vs_fp64_serial": rel_errs(uTs32, uT64)})
+                # the FP32 level-0 relaxation of this workload, launched alone
+                # (FCF: 2m + 1 steps on each of the nt/m + 1 chunks)
+                sv.run_cycles(u0, 0)
+                sv.launch_kernel(0, 0, 1)
+                _, rk = timed_ms(lambda: sv.launch_kernel(0, 0, 3))
+                nC = nt // m
+                upd = nx * (2 * nC * m + nC)
+                ach = FLOPS_PER_CELL_UPDATE * upd / (rk / 3 / 1e3) / 1e12
+                run["relax_l0_roofline"] = {"bound": "alu", "kernel": "level-0 relaxation (k_slab, FP32)",
+                                            "ms": rk / 3, "cell_updates_per_launch": upd,
+                                            "achieved": ach, "peak": peaks["fp32_tflops"],
+                                            "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"]}
             sv.close()
             out["runs"].append(run)
     return out
@@ -621,7 +667,7 @@ def run_mgrit(args):
         sc32.close()
 
     # ---- config 4: nx = 16384, nt = 65536, m = 8, FP32 sweeps ----------------
-    c4 = None if args.no_c4 else config4(mgrit, inputs, dev, timed_ms, rel_errs)
+    c4 = None if args.no_c4 else config4(mgrit, inputs, dev, timed_ms, rel_errs, peaks)
 
     # ---- A/B: one CTA per chunk on every level (chunk_clusters = 0) --------
     a = torch.cuda.Event(enable_timing=True)
@@ -715,7 +761,14 @@ def run_mgrit(args):
     if not args.no_cpu_baseline and ws == 1:
         rate, secs, cores = oracle_cycle_rate(SAMPLE)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-               "sample": sample_desc(SAMPLE), "seconds": secs}
+               "sample": sample_desc(SAMPLE), "seconds": secs, "cpu_model": host_cpu_model()}
+        one = oracle_single_thread(SAMPLE1)
+        if one is not None:
+            cpu["single_thread"] = {"value": one[0], "unit": "cell-updates/s", "threads": one[2],
+                                    "seconds": one[1],
+                                    "sample": "one V-cycle: nx=%d, nt=%d, T=%g, m=%d, %d levels, seed %d"
+                                              % (SAMPLE1["nx"], SAMPLE1["nt"], SAMPLE1["T"],
+                                                 SAMPLE1["m"], SAMPLE1["levels"], SAMPLE1["seed"])}
 
     L = W["levels"]
     # graph A (relax, restrict, norm), graph B (relax + restrict per level
