@@ -332,3 +332,50 @@ def test_full_width_multicycle_solve_matches_oracle(M):
     np.testing.assert_allclose(hist[:k], ref["res_hist"][:k], rtol=1e-8, atol=floor)
     assert relerr(uC, ref["uC"]) <= RTOL
     assert relerr(uT, ref["uT"]) <= RTOL
+
+
+def _pair_denominator_products(u):
+    # coverage check only: the products den_2j * den_2j+1 of the interface
+    # denominators D+ D- (Sec. 2.1.1 indicators in closed form) that the FP64
+    # sweeps pair up, from the stage input u
+    a = np.abs(u).max()
+    qp, qm = u * (u / 8 + a / 4), u * (u / 8 - a / 4)
+
+    def dn(v0, v1, v2, v3, v4):
+        e0, e1, e2, e3 = v1 - v0, v2 - v1, v3 - v2, v4 - v3
+        z = [1e-6 + 13 / 3 * d ** 2 for d in (e1 - e0, e2 - e1, e3 - e2)]
+        y = (3 * e1 - e0, e1 + e2, e3 - 3 * e2)
+        s0, s1, s2 = [(zz + yy ** 2) ** 2 for zz, yy in zip(z, y)]
+        return s1 * s2 + 6 * s0 * s2 + 3 * s0 * s1
+
+    r = np.roll
+    with np.errstate(over="ignore"):
+        den = (dn(r(qp, 2), r(qp, 1), qp, r(qp, -1), r(qp, -2)) *
+               dn(r(qm, -3), r(qm, -2), r(qm, -1), qm, r(qm, 1)))
+        n = len(u) // 2
+        return den[0:2 * n:2] * den[1:2 * n:2]
+
+
+@pytest.mark.parametrize("nx", [1000, 4096])
+def test_sweeps_where_paired_reciprocals_leave_their_range(M, nx):
+    # amplitudes from 1 to 1e7 across the slice: where |u| reaches ~1e6 the
+    # product of two interface denominators leaves [2^-996, 2^997] and the
+    # FP64 sweeps divide per interface; elsewhere the pair shares one
+    # reciprocal.  The first FCF relaxation from C-points all equal to u0
+    # gives Phi^m(u0) at every C-point (cycle 0 of Algorithm 1), which the
+    # oracle computes by m serial steps.
+    x = (np.arange(nx) + 0.5) / nx
+    u0 = inputs.fourier_ic(nx, seed=3) * 10.0 ** (3.5 + 3.5 * np.sin(2 * np.pi * x))
+    d = _pair_denominator_products(u0)
+    inside = (d > 2.0 ** -996) & (d < 2.0 ** 997)
+    assert inside.sum() > nx // 8 and (~inside).sum() > nx // 8   # both branches are taken
+    nt, m = 64, 4
+    T = 0.25 * nt / (nx * np.abs(u0).max())
+    s = M.Solver(nx, nt, m, 2, T=T, max_iter=0)
+    st, _, uC, _ = s.solve(dev(u0))
+    assert st in (M.ENOTCONV, M.OK)
+    got = uC.cpu().numpy()[1]
+    ref = O.serial(u0, T / nt, m)
+    for region in (np.abs(u0) > 1e5, np.abs(u0) < 1e2):
+        assert region.any()
+        assert np.abs(got[region] - ref[region]).max() <= RTOL * np.abs(ref[region]).max()
