@@ -96,9 +96,15 @@ typedef struct {
                         MGRIT_LF_FE scheme (MGRIT_EINVAL otherwise) */
     int chunk_clusters; /* 1 (default): the relaxation / interpolation chunks of
                         a level whose chunks alone would leave SMs idle run
-                        on thread-block clusters (mgrit_query 100 + l);
-                        0: one CTA per chunk wherever a slice fits one CTA.
-                        FP64 slices beyond one CTA use clusters either way. */
+                        on thread-block clusters (mgrit_query 100 + l); and
+                        with the WENO5 split form and nx > 8192, the chunks of
+                        the other levels run on clusters of 2 or 4 CTAs of
+                        the one-CTA slab's layout where that was timed faster
+                        when the workspaces were allocated (mgrit_query
+                        200 + l); 2 or 4: as 1, with those clusters taken
+                        without timing, of 2 or 4 CTAs; 0: one CTA per chunk
+                        wherever a slice fits one CTA.  FP64 slices beyond
+                        one CTA use clusters either way. */
     int seq_stepper; /* kernel of the sequential chains (the coarsest solve and
                         mgrit_serial_step): 0 (default) the fastest of those
                         that fit, as timed when the workspaces are allocated;
@@ -277,7 +283,8 @@ int mgrit_test_grid_timeout(mgrit_ctx *ctx, void *stream);
  * per cluster of each relaxation / interpolation chunk of level l (1 = one
  * CTA per chunk; clusters are used where a level's chunks alone leave SMs
  * idle, and for FP64 slices beyond one CTA), 0 before the first allocating
- * call.  -1 for an unknown `what`. */
+ * call; 200 + l: 1 if those clusters hold run-major slabs (chunk_clusters),
+ * else 0.  -1 for an unknown `what`. */
 int mgrit_query(const mgrit_ctx *ctx, int what);
 
 /* Cells x Phi applications of one cycle (V or F, for throughput figures). */

@@ -118,8 +118,8 @@ static int check_params(mgrit_ctx *ctx, const mgrit_params *p)
         return mgrit_fail(ctx, MGRIT_EINVAL, "precision must be 64 or 32");
     if (p->coarse < MGRIT_COARSE_REDISC || p->coarse > MGRIT_COARSE_PSI1)
         return mgrit_fail(ctx, MGRIT_EINVAL, "coarse must be 0, 1 or 2");
-    if (p->chunk_clusters != 0 && p->chunk_clusters != 1)
-        return mgrit_fail(ctx, MGRIT_EINVAL, "chunk_clusters must be 0 or 1");
+    if (p->chunk_clusters != 0 && p->chunk_clusters != 1 && p->chunk_clusters != 2 && p->chunk_clusters != 4)
+        return mgrit_fail(ctx, MGRIT_EINVAL, "chunk_clusters must be 0, 1, 2 or 4");
     if (p->seq_stepper < 0 || p->seq_stepper > 3)
         return mgrit_fail(ctx, MGRIT_EINVAL, "seq_stepper must be 0, 1, 2 or 3");
     if (ctx && p->coarse != MGRIT_COARSE_REDISC && ctx->scheme != MGRIT_LF_FE)
@@ -251,7 +251,8 @@ extern "C" int mgrit_set_params(mgrit_ctx *ctx, const mgrit_params *p)
                             ctx->p.coarse == p->coarse &&
                             ctx->p.chunk_clusters == p->chunk_clusters &&
                             ctx->p.seq_stepper == p->seq_stepper;
-    const bool rechoose = ctx->alloc && ctx->p.chunk_clusters != p->chunk_clusters;
+    const bool rechoose = ctx->alloc && (ctx->p.chunk_clusters != p->chunk_clusters ||
+                                         ctx->p.numflux != p->numflux);
     if (ctx->alloc && (p->precision == 32) != (ctx->f32 != 0)) free_workspaces(ctx);
     ctx->p = *p;
     set_level_steps(ctx);
@@ -341,14 +342,34 @@ static void choose_level_cluster(const mgrit_ctx *ctx, int f32, int l, ClusterLa
     *lc = fill.fn ? fill : ln.slab ? ClusterLaunch{} : any;
 }
 
+// a level's chunks on clusters of run-major slabs instead of the shape above:
+// where the timed choice took them (WENO5 split form), one-CTA chunks are
+// allowed either way (chunk_clusters) or do not fit, and the level's chunks
+// fill the SMs
+static void apply_tl(const mgrit_ctx *ctx, int f32, int l, ClusterLaunch *lc)
+{
+    const int slot = ctx->p.chunk_clusters == 2 ? 1 : ctx->p.chunk_clusters == 4 ? 2 : 0;
+    const ClusterLaunch &tl = f32 ? ctx->tl32[slot] : ctx->tl64[slot];
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    if (!tl.fn || ctx->scheme != MGRIT_WENO5_SSPRK3 || ctx->p.numflux != NF_SPLIT) return;
+    if (ln.slab && !ctx->p.chunk_clusters) return;
+    if ((long long)(ctx->nC_l[l] + 1) * tl.K < ctx->nsm && lc->fn) return;
+    *lc = tl;
+}
+
 // the chunk launch shapes of every level below the coarsest, in the
 // allocated precision and in FP64 (mgrit_residual's operator)
 static int choose_levels(mgrit_ctx *ctx)
 {
     for (int l = 0; l < ctx->L - 1; ++l) {
         choose_level_cluster(ctx, 0, l, &ctx->lr64[l]);
-        if (ctx->f32) choose_level_cluster(ctx, 1, l, &ctx->lr32[l]);
-        else memset(&ctx->lr32[l], 0, sizeof ctx->lr32[l]);
+        apply_tl(ctx, 0, l, &ctx->lr64[l]);
+        if (ctx->f32) {
+            choose_level_cluster(ctx, 1, l, &ctx->lr32[l]);
+            apply_tl(ctx, 1, l, &ctx->lr32[l]);
+        } else {
+            memset(&ctx->lr32[l], 0, sizeof ctx->lr32[l]);
+        }
         const bool ok = ctx->f32 ? (ctx->ln32.slab || ctx->lr32[l].fn) : (ctx->ln64.slab || ctx->lr64[l].fn);
         if (!ok)
             return mgrit_fail(ctx, MGRIT_EINVAL, "no slab or cluster shape fits nx = %d at level %d",
@@ -597,6 +618,73 @@ static int tune_slab(mgrit_ctx *ctx)
     return MGRIT_OK;
 }
 
+// Clusters of run-major slabs for the chunks of the WENO5 split form when nx
+// > 8192 (one FP32 CTA would hold 32 cells per thread and spill; an FP64
+// slice does not fit one CTA): K = 2 or 4 CTAs of 8 or 16 cells per thread,
+// timed on the level-0 relaxation of min(chunks, 8 x SMs) chunks of a zero
+// state against the level's current shape (the one-CTA slab or the cluster
+// stepper's chunks); the fastest is kept.  The choice applies to the levels
+// whose chunks fill the SMs (apply_tl).
+// Slots 1 and 2 keep the first shape that fits with K = 2 and 4, for
+// chunk_clusters = 2 and 4 (no timing).
+template <typename R>
+static int tune_tl(mgrit_ctx *ctx)
+{
+    const bool f32 = sizeof(R) == 4;
+    ClusterLaunch *tls = f32 ? ctx->tl32 : ctx->tl64;
+    ClusterLaunch &tl = tls[0];
+    memset(tls, 0, 3 * sizeof(ClusterLaunch));
+    if (ctx->scheme != MGRIT_WENO5_SSPRK3 || ctx->nx <= 8192) return MGRIT_OK;
+    const Launch &ln = f32 ? ctx->ln32 : ctx->ln64;
+    const ClusterLaunch cur = f32 ? ctx->lr32[0] : ctx->lr64[0];
+    SlabArgs<R> a = relax_args<R>(ctx, 0);
+    // enough chunks for several waves of every candidate (2 x SMs chunks
+    // timed K = 2 ahead of a K = 4 that is faster on the whole level)
+    const int chunks = ctx->nC_l[0] + 1 < 8 * ctx->nsm ? ctx->nC_l[0] + 1 : 8 * ctx->nsm;
+    cudaStream_t s = ctx->cap;
+    CK(cudaMemsetAsync(const_cast<R *>(a.uC), 0, sizeof(R) * (size_t)ctx->nx * chunks, s));
+    auto time_shape = [&](const ClusterLaunch &lc, float *ms) -> int {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(launch_chunks(lc, ln, chunks, s, &a));   // warm-up
+        CK(cudaEventRecord(e0, s));
+        CK(launch_chunks(lc, ln, chunks, s, &a));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return MGRIT_OK;
+    };
+    // the timing needs the split form and a shape to compare with
+    const bool timed = ctx->p.numflux == NF_SPLIT && ctx->p.chunk_clusters == 1 && (cur.fn || ln.slab);
+    float best_ms = -1.f;
+    int st;
+    if (timed && (st = time_shape(cur, &best_ms))) return st;
+    for (int K = 2; K <= 4; K *= 2) {
+        const int nmax = (ctx->nx + K - 1) / K;
+        for (int ci = 1; ci >= 0; --ci) {
+            const int cpt = ci ? 16 : 8;
+            const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+            if (threads > MAX_THREADS) continue;
+            const void *fn = f32 ? table().tlc32[ctx->flux][ci] : table().tlc64[ctx->flux][ci];
+            const size_t smem = slab_cluster_smem_bytes<R>(nmax, cpt, threads);
+            if (!fn || smem > (size_t)SMEM_OPTIN || !cluster_fits(fn, K, threads, smem)) continue;
+            const ClusterLaunch c{fn, K, cpt, threads, smem};
+            if (!tls[K / 2].fn) tls[K / 2] = c;
+            if (!timed) continue;
+            float ms = -1.f;
+            if ((st = time_shape(c, &ms))) return st;
+            if (best_ms < 0.f || ms < best_ms) {
+                best_ms = ms;
+                tl = c;
+            }
+        }
+    }
+    return MGRIT_OK;
+}
+
 int mgrit_ensure_alloc(mgrit_ctx *ctx)
 {
     if (ctx->alloc) return MGRIT_OK;
@@ -660,6 +748,12 @@ int mgrit_ensure_alloc(mgrit_ctx *ctx)
         return mgrit_fail(ctx, MGRIT_EINVAL, "no FP64 slab or cluster fits nx = %d for the coarsest solve",
                     ctx->nx);
     int st2;
+    memset(ctx->tl64, 0, sizeof ctx->tl64);
+    memset(ctx->tl32, 0, sizeof ctx->tl32);
+    if ((st2 = choose_levels(ctx))) return st2;
+    // clusters of run-major slabs (nx > 8192), timed against the shapes
+    // just chosen, on the same level-0 C-point source as tune_slab
+    if (ctx->f32 ? (st2 = tune_tl<float>(ctx)) : (st2 = tune_tl<double>(ctx))) return st2;
     if ((st2 = choose_levels(ctx))) return st2;
     ctx->alloc = true;
     return MGRIT_OK;
@@ -1177,6 +1271,12 @@ extern "C" int mgrit_query(const mgrit_ctx *ctx, int what)
             if (!ctx->alloc) return 0;
             const ClusterLaunch &lr = f32 ? ctx->lr32[what - 100] : ctx->lr64[what - 100];
             return lr.fn ? lr.K : 1;
+        }
+        if (what >= 200 && what < 200 + ctx->L - 1) {   // level what-200 on run-major cluster slabs?
+            if (!ctx->alloc) return 0;
+            const ClusterLaunch &lr = f32 ? ctx->lr32[what - 200] : ctx->lr64[what - 200];
+            const ClusterLaunch *tl = f32 ? ctx->tl32 : ctx->tl64;
+            return lr.fn && (lr.fn == tl[0].fn || lr.fn == tl[1].fn || lr.fn == tl[2].fn) ? 1 : 0;
         }
         return -1;
     }

@@ -50,4 +50,24 @@ __global__ void __launch_bounds__(512) k_slab_cluster(SlabArgs<R> a)
     C.cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
 }
 
+// The same chunks on clusters of run-major slabs (Slab with CLUSTER; WENO5
+// split form): each CTA holds a contiguous block of the slice in the one-CTA
+// slab's layout and arithmetic, with alpha and the ghost cells exchanged
+// through distributed shared memory, one cluster barrier per stage.  Slices
+// too wide for one CTA's registers (FP32 beyond 8192 cells, FP64 beyond 8192)
+// then run at 16 cells per thread with the sliding windows.
+template <typename R, int SCHEME, int FLUX, int CPT>
+__global__ void __launch_bounds__(512) k_slab_tlc(SlabArgs<R> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Slab<R, SCHEME, FLUX, CPT, false, true> S(smem, a.nx, a.dxinv, a.numflux);
+    S.pair_div = true;
+    const int j = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    if (a.mode == MODE_RELAX)
+        relax_chunk(S, a, j);
+    else
+        interp_chunk(S, a, j);
+    cg::this_cluster().sync();   // no CTA leaves while a neighbour may still read its shared memory
+}
+
 }  // namespace mgrit

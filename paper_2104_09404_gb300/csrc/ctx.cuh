@@ -110,6 +110,12 @@ struct mgrit_ctx {
     // relaxation / interpolation of level l on clusters (fn null: one CTA per
     // chunk), chosen when the workspaces are allocated
     mgrit::ClusterLaunch lr64[mgrit::MAXLEV], lr32[mgrit::MAXLEV];
+    // WENO5 split form, nx > 8192: clusters of run-major slabs (k_slab_tlc)
+    // for the levels whose chunks fill the SMs.  [0]: the shape timed faster
+    // than the one-CTA slab or the cluster stepper's chunks (fn null: those
+    // were faster); [1], [2]: the first shape that fits with K = 2 and 4
+    // (chunk_clusters = 2 and 4)
+    mgrit::ClusterLaunch tl64[3], tl32[3];
     bool cluster64;      // FP64 slices only fit on clusters (nx > 8192)
     int nsm;             // SMs of the device
     int f32;             // precision the workspaces were allocated for (1: FP32 sweeps)

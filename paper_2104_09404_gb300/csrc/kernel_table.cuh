@@ -25,7 +25,16 @@ struct KernelTable {
     const void *relc32[2][2][NCPT_RELAXC];
     const void *grid64[2][2];   // k_seq_grid [scheme][flux] (WENO5 / first order, split flux)
     const void *grid32[2][2];
+    const void *tlc64[2][2];    // k_slab_tlc [flux][0: 8, 1: 16 cells per thread] (WENO5 split form)
+    const void *tlc32[2][2];
 };
+
+template <typename R, int F>
+void fill_tlc(const void *(&t)[2][2])
+{
+    t[F][0] = (const void *)&k_slab_tlc<R, SCH_WENO5_SSPRK3, F, 8>;
+    t[F][1] = (const void *)&k_slab_tlc<R, SCH_WENO5_SSPRK3, F, 16>;
+}
 
 template <typename R, int S, int F>
 void fill_sf(const void *(&t)[NSCHEME][2][NCPT])
@@ -75,10 +84,18 @@ void fill_f64_relaxc_advection(KernelTable &t);
 void fill_f32_relaxc_burgers(KernelTable &t);
 void fill_f32_relaxc_advection(KernelTable &t);
 void fill_grid(KernelTable &t);
+void fill_tlc_f64_burgers(KernelTable &t);
+void fill_tlc_f64_advection(KernelTable &t);
+void fill_tlc_f32_burgers(KernelTable &t);
+void fill_tlc_f32_advection(KernelTable &t);
 
 inline void fill_all(KernelTable &t)
 {
     fill_grid(t);
+    fill_tlc_f64_burgers(t);
+    fill_tlc_f64_advection(t);
+    fill_tlc_f32_burgers(t);
+    fill_tlc_f32_advection(t);
     fill_f64_weno_burgers(t);
     fill_f64_weno_advection(t);
     fill_f64_weno_cluster(t);

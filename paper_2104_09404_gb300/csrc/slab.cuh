@@ -14,6 +14,7 @@
 // NWARP_MAX values for the block max reduction of the global Lax-Friedrichs
 // alpha.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +24,8 @@
 #endif
 
 namespace mgrit {
+
+namespace cg = cooperative_groups;
 
 enum { SCH_WENO5_SSPRK3 = 0, SCH_FO_FE = 1, SCH_LF_FE = 2 };
 enum { FLX_BURGERS = 0, FLX_ADVECTION = 1 };
@@ -501,15 +504,26 @@ __host__ __device__ constexpr int slab_run_stride(int cpt, int threads)
 }
 
 // FLAT: keep every cell at slot i + GHOST whatever CPT (the adjoint slab,
-// which overlays its own arrays on that layout)
-template <typename R, int SCHEME, int FLUX, int CPT, bool FLAT = false>
+// which overlays its own arrays on that layout).
+// CLUSTER: one of the K CTAs of a thread-block cluster that share one slice
+// (WENO5 split form only): CTA r holds the contiguous cells [lo, lo + nx) of
+// it in the same run-major layout, and fluxes_cluster() exchanges the
+// Lax-Friedrichs alpha and the 3 + 3 ghost cells through distributed shared
+// memory instead of the periodic copies.
+template <typename R, int SCHEME, int FLUX, int CPT, bool FLAT = false, bool CLUSTER = false>
 struct Slab {
     R *qa;        // slots of cells -3..nx+2: f^+ / 2 (WENO5 split form), f^+ (first
                   // order), or the stage state (state form, Roe)
     R *qb;        // the same slots: f^- / 2 or f^-
     R *qf;        // slots 0..nx: interface fluxes, qf[i+1] = F_{i+1/2}, qf[0] = F_{-1/2}
     R *red;       // NWARP_MAX
-    int nx;
+    R *ck;        // [2] CLUSTER: this CTA's alpha key, by stage parity
+    R *gw;        // [2][6] CLUSTER: stage inputs of the ghost cells -3..-1, nx..nx+2,
+                  // written by the neighbours, by stage parity
+    int nx;       // cells of this slab (CLUSTER: of this CTA's block)
+    int lo;       // first cell of the block in the slice (0 unless CLUSTER)
+    int rank, K;  // CLUSTER: block rank and cluster size
+    int par;      // CLUSTER: stage parity
     int numflux;
     R dxinv;
     // SCH_LF_FE only: the integrator of the current level.  psiM = 0: the fine
@@ -536,6 +550,7 @@ struct Slab {
     // (i = -3 .. nx+2) at slot i + GHOST.  The interface flux F_{i+1/2} is
     // kept at cell i of qf (F_{-1/2} at cell -1).
     static constexpr bool TL = !FLAT && CPT >= 2;
+    static_assert(!CLUSTER || (TL && SCHEME == SCH_WENO5_SSPRK3), "cluster slabs: run-major WENO5 only");
     static constexpr int LOG = CPT >= 32 ? 5 : CPT >= 16 ? 4 : CPT >= 8 ? 3 : CPT >= 4 ? 2 : CPT >= 2 ? 1 : 0;
     static constexpr int RO = CPT >= 4 ? 1 : 2;
     // FP32: the run stride as a compile-time constant
@@ -553,9 +568,17 @@ struct Slab {
     __device__ __forceinline__ int P() const { return sizeof(R) == 4 ? P32 : prun; }
 
     __device__ __forceinline__ Slab(unsigned char *smem, int nx_, R dxinv_, int numflux_)
-        : nx(nx_), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0), psiDt(R(0)), pair_div(false)
+        : nx(nx_), lo(0), rank(0), K(1), par(0), numflux(numflux_), dxinv(dxinv_), psiM(0), psiOrder(0),
+          psiDt(R(0)), pair_div(false)
     {
         const int T = (int)blockDim.x;
+        if constexpr (CLUSTER) {
+            cg::cluster_group cl = cg::this_cluster();
+            K = (int)cl.num_blocks();
+            rank = (int)cl.block_rank();
+            lo = (int)((long long)rank * nx_ / K);
+            nx = (int)((long long)(rank + 1) * nx_ / K) - lo;
+        }
         E = extent(nx, T);
         prun = slab_run_stride<R>(CPT, T);
         // blockDim.x is a multiple of 32, hence of CPT: cell t + c*T + o sits at
@@ -565,6 +588,8 @@ struct Slab {
         qb = qa + E;
         qf = qb + E;
         red = qf + E;
+        ck = red + NWARP_MAX;
+        gw = ck + 2;
     }
 
     __device__ __forceinline__ int cell(int c) const { return threadIdx.x + c * blockDim.x; }
@@ -601,6 +626,7 @@ struct Slab {
     {
         const int i = cell(c);
         MGRIT_SH(arr, pc(c, 0), lim()) = v;
+        if constexpr (CLUSTER) return;   // ghosts come from the neighbours
         if (c == 0 && i < GHOST) ce(arr, i + nx) = v;
         if (i >= nx - GHOST) ce(arr, i - nx) = v;
     }
@@ -679,7 +705,7 @@ struct Slab {
                         M.advance(B_(k + 5));
                     }
                 }
-                if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
+                if (!CLUSTER && i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
                 return;
             }
         }
@@ -694,8 +720,9 @@ struct Slab {
                 if (FLUX == FLX_BURGERS) M.advance(B_(k + 4));
             }
         }
-        // G_{-1/2} = G_{nx-1/2}, from the thread whose run ends at nx - 1
-        if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
+        // G_{-1/2} = G_{nx-1/2}, from the thread whose run ends at nx - 1 (a
+        // cluster slab forms it from its ghosts instead)
+        if (!CLUSTER && i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
     }
 
     // FP32: the same windows on packed pairs.  Lane x of the pair walks
@@ -731,14 +758,103 @@ struct Slab {
             }
         }
         // F_{-1/2} = F_{nx-1/2}, from the thread whose run ends at nx - 1 (its
-        // own store of that interface precedes this read in program order)
-        if (i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
+        // own store of that interface precedes this read in program order; a
+        // cluster slab forms it from its ghosts instead)
+        if (!CLUSTER && i0 + n == nx) ce(qf, -1) = MGRIT_SH(qf, rs(n - 1), lim());
     }
 
     // Interface fluxes F_{i+1/2} of the stage input w into qf (Sec. 2.1.2).
     // Ends with a barrier after which qf is complete.
+    // CLUSTER: the split-form interface values of this CTA's block.  Per stage
+    // one cluster barrier: before it, each CTA publishes its alpha key and
+    // writes the stage inputs of its three first and three last cells into
+    // the ghost slots of its neighbours (double-buffered by stage parity: a
+    // CTA writes buffer p of stage s + 2 only after the barrier of stage
+    // s + 1, which no CTA passes before every CTA has read stage s's values);
+    // after it, alpha is the maximum of the K keys, and each CTA forms q of
+    // its own and its ghost cells.  G_{-1/2} is formed from the left ghosts
+    // by one thread, with the windows of the other interfaces' operations.
+    __device__ __forceinline__ void fluxes_cluster(const R (&w)[CPT])
+    {
+        using KT = decltype(mag_key(R(0)));
+        cg::cluster_group cl = cg::this_cluster();
+        __syncthreads();   // previous readers of qa/qb/qf/red are done
+        const int p = par;
+        par ^= 1;
+        KT v = 0;
+        if (FLUX == FLX_BURGERS) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c)
+                if (cell(c) < nx) {
+                    const KT k = mag_key(w[c]);
+                    v = k > v ? k : v;
+                }
+            v = block_max_key(v, red);
+            if (threadIdx.x == 0) reinterpret_cast<KT *>(ck)[p] = v;
+        }
+        {
+            const unsigned right = (unsigned)((rank + 1) % K), left = (unsigned)((rank + K - 1) % K);
+            R *gr = cl.map_shared_rank(gw, right), *gl = cl.map_shared_rank(gw, left);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int i = cell(c);
+                if (i < nx && i >= nx - GHOST) gr[6 * p + i - (nx - GHOST)] = w[c];   // its cells -3..-1
+                if (c == 0 && i < GHOST) gl[6 * p + GHOST + i] = w[c];             // its cells n..n+2
+            }
+        }
+        cl.sync();
+        R alpha = R(1);
+        if (FLUX == FLX_BURGERS) {
+            KT m = 0;
+            for (int r = 0; r < K; ++r) {
+                const KT k = reinterpret_cast<const KT *>(cl.map_shared_rank(ck, (unsigned)r))[p];
+                m = k > m ? k : m;
+            }
+            alpha = key_value(m);
+        }
+        const R a4 = R(0.25) * alpha;
+        auto qp = [&](R x) { return FLUX == FLX_BURGERS ? Ar<R>::mul(Ar<R>::fma(R(0.125), x, a4), x) : R(0.5) * x; };
+        auto qm = [&](R x) { return Ar<R>::mul(Ar<R>::fma(R(0.125), x, -a4), x); };
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (cell(c) < nx) {
+                MGRIT_SH(qa, pc(c, 0), lim()) = qp(w[c]);
+                if (FLUX == FLX_BURGERS) MGRIT_SH(qb, pc(c, 0), lim()) = qm(w[c]);
+            }
+        if (threadIdx.x < 2 * GHOST) {
+            const int t = (int)threadIdx.x;
+            const int i = t < GHOST ? t - GHOST : nx + t - GHOST;
+            const R x = gw[6 * p + t];
+            ce(qa, i) = qp(x);
+            if (FLUX == FLX_BURGERS) ce(qb, i) = qm(x);
+        }
+        __syncthreads();
+        if constexpr (sizeof(R) == 4 && CPT <= 16)
+            split_fluxes_win2();
+        else
+            split_fluxes_win();
+        if (threadIdx.x == blockDim.x - 1) {   // G_{-1/2} from cells -3..2
+            WenoWin<R> P;
+            P.init(ce(qa, -3), ce(qa, -2), ce(qa, -1), ce(qa, 0), ce(qa, 1));
+            R G;
+            if (FLUX == FLX_BURGERS) {
+                WenoWin<R> M;
+                M.init(ce(qb, -2), ce(qb, -1), ce(qb, 0), ce(qb, 1), ce(qb, 2));
+                G = split_flux_win(P, M, ce(qa, -1), ce(qb, 0));
+            } else {
+                G = split_flux_win_adv(P, ce(qa, -1));
+            }
+            ce(qf, -1) = G;
+        }
+        __syncthreads();
+    }
+
     __device__ __forceinline__ void fluxes(const R (&w)[CPT])
     {
+        if constexpr (CLUSTER) {
+            fluxes_cluster(w);
+            return;
+        }
         __syncthreads();   // previous readers of qa/qb/qf/red are done
         if (numflux == NF_SPLIT) {
             R alpha = R(1);
@@ -953,7 +1069,7 @@ struct Slab {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);
-            u[c] = (i < nx) ? row[i] : R(0);
+            u[c] = (i < nx) ? row[lo + i] : R(0);
         }
     }
     __device__ __forceinline__ void store(const R (&u)[CPT], R *__restrict__ row) const
@@ -964,7 +1080,7 @@ struct Slab {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);
-            if (i < nx) row[i] = u[c];
+            if (i < nx) row[lo + i] = u[c];
         }
     }
     // u += g row; g is kept in FP64 (the FAS tau term), so an FP32 sweep adds
@@ -977,7 +1093,7 @@ struct Slab {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const int i = cell(c);
-            if (i < nx) u[c] = R((double)u[c] + row[i]);
+            if (i < nx) u[c] = R((double)u[c] + row[lo + i]);
         }
     }
 };
@@ -989,6 +1105,13 @@ inline size_t slab_smem_bytes(int nx, int cpt, int threads)
 {
     const size_t e = cpt >= 2 ? (size_t)cpt * slab_run_stride<R>(cpt, threads) : (size_t)nx + 2 * GHOST;
     return sizeof(R) * (3 * e + NWARP_MAX);
+}
+// the same for one CTA of a cluster slab (its block of at most nmax cells;
+// the layout does not depend on nmax), with the alpha keys and ghost inputs
+template <typename R>
+inline size_t slab_cluster_smem_bytes(int nmax, int cpt, int threads)
+{
+    return slab_smem_bytes<R>(nmax, cpt, threads) + sizeof(R) * (2 + 12);
 }
 
 }  // namespace mgrit

@@ -84,7 +84,7 @@ def test_create_set_params_destroy_without_gpu(lib):
     for field, bad in (("relax", 3), ("cycle", 2), ("guess", 2), ("numflux", 5), ("coarse", 3),
                        ("coarse", 1),
                        ("tol", -1.0), ("max_iter", 1000), ("precision", 16), ("T", 0.0),
-                       ("chunk_clusters", 2), ("seq_stepper", 4), ("seq_stepper", -1)):
+                       ("chunk_clusters", 3), ("seq_stepper", 4), ("seq_stepper", -1)):
         q = M.mgrit_params.from_buffer_copy(p)
         setattr(q, field, bad)
         assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field

@@ -3,9 +3,12 @@
 A level whose chunks alone would leave SMs idle runs each chunk on a cluster
 of K CTAs (contiguous cell blocks, ghosts and the LF alpha exchanged through
 distributed shared memory), and FP64 slices beyond one CTA (nx > 8192) always
-do.  The chunk logic is the one-CTA kernel's, so the bar is the same: the FP64
-oracle's outcome and cycle count, residual histories to rounding, and C-points
-within 1e-11 relative.
+do.  Beyond 8192 cells the WENO5 split form can also run its chunks on
+clusters of 2 or 4 run-major slabs (the one-CTA slab's layout and arithmetic
+per block, chunk_clusters = 2 or 4 to force them).  The chunk logic is the
+one-CTA kernel's, so the bar is the same: the FP64 oracle's outcome and cycle
+count, residual histories to rounding, and C-points within 1e-11 relative; and
+FP32 run-major cluster slabs give the bits of the one-CTA FP32 slab.
 """
 import numpy as np
 import pytest
@@ -84,7 +87,9 @@ def test_cluster_chunk_mgrit_parity(M, name, nx, nt, m, L, cfl, kw, seed):
     params = dict(T=T, tol=1e-10, max_iter=30, numflux=kw.get("numflux", 0),
                   relax=kw.get("relax", O.RELAX_FCF), guess=kw.get("guess", O.GUESS_EQ17),
                   cycle=kw.get("cycle", O.CYCLE_V))
-    s = M.Solver(nx, nt, m, L, scheme, flux, **params)
+    # beyond 8192 cells chunk_clusters = 0 keeps the cluster stepper's chunks
+    # of the rule (the run-major cluster slabs have their own tests below)
+    s = M.Solver(nx, nt, m, L, scheme, flux, chunk_clusters=0 if nx > 8192 else 1, **params)
     st, uT, uC, stats = s.solve(dev(u0))
     torch.cuda.synchronize()
     # every level below the coarsest took the shape the rule gives, and at
@@ -171,3 +176,78 @@ def test_one_cta_chunks_on_request_and_parameter_changes(M):
     stf, _, uCf, statsf = s.solve(dev(u0))
     assert stf == M.OK and statsf.iters == reff["iters"]
     assert relerr(uCf.cpu().numpy(), reff["uC"]) <= RTOL
+
+
+TL_CASES = [
+    # name, nx, nt, m, L, coarsest CFL, kw, seed, K
+    ("fp64-16384-k2", 16384, 512, 4, 2, 0.4, {}, 41, 2),
+    ("fp64-12000-k4", 12000, 512, 4, 2, 0.4, {}, 42, 4),
+    ("fp64-16384-advection-k4", 16384, 512, 4, 2, 0.5, dict(flux=O.FLUX_ADVECTION), 43, 4),
+    ("fp64-10000-fcycle-k2", 10000, 1024, 2, 4, 0.4, dict(cycle=O.CYCLE_F), 44, 2),
+]
+
+
+@pytest.mark.parametrize("name,nx,nt,m,L,cfl,kw,seed,K", TL_CASES, ids=[c[0] for c in TL_CASES])
+def test_run_major_cluster_slabs_mgrit_parity(M, name, nx, nt, m, L, cfl, kw, seed, K):
+    u0 = inputs.fourier_ic(nx, seed=seed)
+    flux = kw.get("flux", O.FLUX_BURGERS)
+    cycle = kw.get("cycle", O.CYCLE_V)
+    T = cfl_time(u0, nx, nt, m, L, flux, cfl)
+    s = M.Solver(nx, nt, m, L, 0, flux, T=T, tol=1e-10, max_iter=30, cycle=cycle, chunk_clusters=K)
+    st, uT, uC, stats = s.solve(dev(u0))
+    torch.cuda.synchronize()
+    # levels whose chunks fill the SMs on K run-major slabs; the others keep
+    # the cluster stepper's chunks of the rule
+    for l in range(L - 1):
+        tl = (nt // m ** (l + 1) + 1) * K >= nsm()
+        assert s.query(200 + l) == (1 if tl else 0), l
+        if tl:
+            assert s.query(100 + l) == K
+    assert s.query(200) == 1
+    ref = O.mgrit(u0, nt, m, L, T, flux=flux, tol=1e-10, max_iter=30, cycle=cycle)
+    assert ref["status"] == O.OK
+    if np.any(np.abs(np.asarray(ref["res_hist"]) - 1e-10) <= 1e-13):
+        pytest.skip("oracle residual within 1e-3 of tol: iteration count not decidable")
+    assert st == M.OK and stats.iters == ref["iters"]
+    hist = np.array(stats.res_hist[: stats.iters + 1])
+    floor = 1e-14 * np.abs(ref["uC"]).max() * np.sqrt(ref["uC"].size)
+    np.testing.assert_allclose(hist, ref["res_hist"], rtol=1e-8, atol=floor)
+    assert relerr(uC.cpu().numpy(), ref["uC"]) <= RTOL
+    assert relerr(uT.cpu().numpy(), ref["uT"]) <= RTOL
+
+
+@pytest.mark.parametrize("nx,flux", [(16384, O.FLUX_BURGERS), (12000, O.FLUX_BURGERS),
+                                     (16384, O.FLUX_ADVECTION)])
+def test_fp32_run_major_cluster_slabs_give_the_one_cta_bits(M, nx, flux):
+    # FP32 sweeps: one CTA of 32 cells per thread (chunk_clusters = 0) against
+    # clusters of 2 and 4 run-major slabs of 16 cells per thread; every FP32
+    # shape performs the same operations per interface and cell
+    nt, m, L = 1024, 4, 2
+    u0 = inputs.fourier_ic(nx, seed=nx + 7)
+    T = cfl_time(u0, nx, nt, m, L, flux, 0.4)
+    out = {}
+    for K in (0, 2, 4):
+        s = M.Solver(nx, nt, m, L, 0, flux, T=T, precision=32, chunk_clusters=K)
+        s.run_cycles(dev(u0), 2)
+        torch.cuda.synchronize()
+        assert s.query(200) == (1 if K else 0) and s.query(100) == (K if K else 1)
+        out[K] = s.cpoints()
+        s.close()
+    assert torch.equal(out[0], out[2]) and torch.equal(out[0], out[4])
+    ref, _ = O.vcycles(u0, nt, m, L, T, 2, flux=flux)
+    assert relerr(out[2].cpu().numpy(), ref) <= 1e-4
+
+
+def test_run_major_cluster_residual_parity(M):
+    # mgrit_residual's F-relaxation on K = 2 run-major slabs (129 chunks)
+    nx, nt, m = 16384, 512, 4
+    u0 = inputs.fourier_ic(nx, seed=45)
+    T = 0.3 * nt / (nx * np.abs(u0).max())
+    traj = O.serial(u0, T / nt, nt, store_all=True)
+    uC = traj[::m].copy()
+    s = M.Solver(nx, nt, m, 2, T=T, chunk_clusters=2)
+    assert s.residual(dev(uC)) < 1e-13 * np.sqrt(uC.size) * np.abs(uC).max()
+    assert s.query(200) == 1
+    rng = np.random.default_rng(2)
+    uC[1:] += 1e-4 * rng.standard_normal(uC[1:].shape)
+    assert s.residual(dev(uC)) == pytest.approx(O.residual(uC, nt, m, T), rel=1e-10)
