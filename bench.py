@@ -49,6 +49,9 @@ SAMPLE1 = dict(nx=4096, nt=1024, m=4, levels=5, T=0.0625, seed=0)  # single-thre
 # 3 |.| and 3 comparisons.  tests/test_flop_count.py keeps the figure equal
 # to the counting run.
 FLOPS_PER_CELL_UPDATE = 555
+# the same for linear advection (alpha = 1 and f^- = 0: 185 additions, 271
+# multiplications, 75 divisions)
+FLOPS_PER_CELL_UPDATE_ADVECTION = 531
 # adjoint gradient workload: pre-shock and post-shock final times with the
 # levels the coarse CFL allows (level-2 CFL 0.51 at T=0.12, level-1 0.32 at T=0.3)
 ADJOINT_WORKLOAD = dict(nx=2048, nt=8192, m=4, seed=1, target_seed=1001, breaking_time=0.201,
@@ -726,6 +729,20 @@ def run_mgrit(args):
         b.record(stream)
         torch.cuda.synchronize()
         msb = a.elapsed_time(b)
+        # the batched level-0 relaxation launched alone, against the measured
+        # FP32 rate; FLOPs per cell update by flux (the instrumented oracle
+        # counts 531 for advection, whose f^- reconstruction vanishes)
+        bt.launch_relax(1)
+        torch.cuda.synchronize()
+        a.record(stream)
+        bt.launch_relax(3)
+        b.record(stream)
+        torch.cuda.synchronize()
+        relaxb_ms = a.elapsed_time(b) / 3
+        relaxb_flop = sum(d["nx"] * (d["nt"] // d["m"]) * (2 * d["m"] + 1) *
+                          (FLOPS_PER_CELL_UPDATE if d["flux"] == 0 else FLOPS_PER_CELL_UPDATE_ADVECTION)
+                          for d in insts)
+        relaxb_ach = relaxb_flop / (relaxb_ms / 1e3) / 1e12
         bt.close()
         singles = [mgrit.Solver(d["nx"], d["nt"], d["m"], d["levels"], 0, d["flux"], T=d["T"],
                                 precision=32) for d in insts]
@@ -747,6 +764,10 @@ def run_mgrit(args):
                    "ms_per_cycle": msb / args.steps,
                    "one_context_at_a_time_ms_per_cycle": mss / args.steps,
                    "speedup_vs_one_at_a_time": mss / msb, "autotune_seconds": tune_s,
+                   "relax_l0_roofline": {"bound": "alu", "kernel": "batched level-0 relaxation (FP32)",
+                                         "ms": relaxb_ms, "flop_per_launch": relaxb_flop,
+                                         "achieved": relaxb_ach, "peak": peaks["fp32_tflops"],
+                                         "unit": "TFLOP/s", "frac": relaxb_ach / peaks["fp32_tflops"]},
                    "autotuned_instances_per_choice": tuned}
 
     adjoint = None if args.no_adjoint else adjoint_gradient(mgrit, inputs, dev, stream)

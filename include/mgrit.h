@@ -410,6 +410,15 @@ int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev, int reps, 
 /* Cells x Phi applications of one cycle (V or F) of all instances. */
 double mgrit_batch_cycle_cell_updates(const mgrit_batch *b);
 
+/* Profiling hook (as mgrit_launch_kernel): the batched level-0 relaxation of
+ * every instance (Sec. 3.2: the FCF or F sweep of every chunk, in the
+ * launches a cycle uses), `reps` times on `stream` from the instances'
+ * current level-0 C-points, overwriting the level-0 relaxation outputs as a
+ * cycle's first phase does.  Requires a prior mgrit_batch_run_cycles or
+ * mgrit_batch_solve.  Synchronises `stream` (its launch tables are freed
+ * afterwards).  MGRIT_EINVAL for reps < 1. */
+int mgrit_batch_launch_relax(mgrit_batch *b, int reps, void *stream);
+
 /* what = 0: cells per thread, 1: threads per CTA, 2: levels of instance i,
  * 3: slabs per CTA (always 1), 4: CTAs per cluster of its coarsest solve
  * (1 = one CTA); -1 for an unknown `what` or instance. */

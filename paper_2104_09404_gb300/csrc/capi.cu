@@ -2081,6 +2081,27 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
     return batch_build(b);
 }
 
+// Profiling hook: the batched level-0 relaxation phase, `reps` times, from
+// launch tables of its own (dropped once the launches have finished).
+extern "C" int mgrit_batch_launch_relax(mgrit_batch *b, int reps, void *stream)
+{
+    if (!b || reps < 1) return MGRIT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<BLaunch> ls;
+    const size_t keep = b->tables.size();
+    int st = b->p.precision == 32 ? emit_relax<float>(b, 0, ls) : emit_relax<double>(b, 0, ls);
+    for (int r = 0; r < reps && !st; ++r)
+        for (const BLaunch &L : ls)
+            if (enqueue_blaunch(b, L, s) != cudaSuccess) {
+                st = bfail(b, MGRIT_ECUDA, "launch: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+    if (cudaStreamSynchronize(s) != cudaSuccess && !st)
+        st = bfail(b, MGRIT_ECUDA, "synchronise: %s", cudaGetErrorString(cudaGetLastError()));
+    drop_tables(b, keep);
+    return st;
+}
+
 extern "C" double mgrit_batch_cycle_cell_updates(const mgrit_batch *b)
 {
     if (!b) return 0.0;

@@ -79,6 +79,7 @@ _SIGS = {
     "mgrit_batch_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "mgrit_batch_autotune": (_I, [_P, _P, _I, _P]),
     "mgrit_batch_cycle_cell_updates": (_D, [_P]),
+    "mgrit_batch_launch_relax": (_I, [_P, _I, _P]),
     "mgrit_batch_query": (_I, [_P, _I, _I]),
     "mgrit_batch_copy_cpoints": (_I, [_P, _I, _P, _P]),
     "mgrit_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -338,6 +339,10 @@ class Batch:
 
     def cycle_cell_updates(self):
         return load().mgrit_batch_cycle_cell_updates(self._h)
+
+    def launch_relax(self, reps=1, stream=None):
+        """Profiling hook: the batched level-0 relaxation, reps times."""
+        self._check(load().mgrit_batch_launch_relax(self._h, reps, _stream_handle(stream)))
 
     def query(self, i, what):
         """Instance i: 0 cells per thread, 1 threads per CTA, 2 levels, 3 slabs

@@ -38,3 +38,5 @@ def test_bench_uses_the_counted_figure():
     import bench
     d = C.count_step(inputs.fourier_ic(4096, seed=0), 1.0 / 16384)
     assert bench.FLOPS_PER_CELL_UPDATE == d["total"] == 555
+    da = C.count_step(inputs.fourier_ic(4096, seed=0), 1.0 / 16384, O.SCHEME_WENO5_SSPRK3, O.FLUX_ADVECTION)
+    assert bench.FLOPS_PER_CELL_UPDATE_ADVECTION == da["total"] == 531

@@ -142,6 +142,23 @@ def test_batch_solve_masks_converged_instances(M):
         assert res[k] == pytest.approx(stats.res_hist[stats.iters], rel=1e-9, abs=1e-13)
 
 
+def test_batch_relaxation_hook_leaves_cycles_unchanged(M):
+    # the profiling hook reruns the batched level-0 relaxation; cycles started
+    # afterwards from the initial iterate are the cycles of a fresh batch
+    u0s = [dev(inputs.fourier_ic(d["nx"], seed=40 + k)) for k, d in enumerate(MIXED)]
+    b = M.Batch(MIXED, precision=32)
+    b.run_cycles(u0s, 1)
+    b.launch_relax(2)
+    b.run_cycles(u0s, 2)
+    f = M.Batch(MIXED, precision=32)
+    f.run_cycles(u0s, 2)
+    torch.cuda.synchronize()
+    for k in range(len(MIXED)):
+        assert torch.equal(b.cpoints(k), f.cpoints(k))
+    with pytest.raises(M.MGRITError):
+        b.launch_relax(0)
+
+
 def test_batch_rejects_unsupported_instances(M):
     with pytest.raises(M.MGRITError):
         M.Batch([dict(nx=64, nt=64, m=2, levels=2, flux=0, T=0.1, scheme=1)])
