@@ -9,7 +9,8 @@ the NVTX range "profiled"; profile them with
 
 Cases: c2 = nx 4096, nt 16384, m 4, 6 levels, T 1 (the benchmark workload);
 small = nx 4096, nt 2048, m 4, 4 levels, T 0.125 (same kernel shape, 513
-CTAs).  The context is prepared with zero cycles (workspaces allocated,
+CTAs); c4 = nx 16384, nt 65536, m 8, 2 levels, T 0.12, u0 = 0.5 + sin 2 pi x
+(config 4, CFL-capped); c4small = the same with nt 8192, T 0.015.  The context is prepared with zero cycles (workspaces allocated,
 level-0 C-points = u0), then the chosen kernel is launched `reps` times; it
 is the first launch of that kernel in the process.
 
@@ -42,6 +43,10 @@ CASES = {
     "c2": dict(nx=4096, nt=16384, m=4, levels=6, T=1.0),
     "small": dict(nx=4096, nt=2048, m=4, levels=4, T=0.125),
     "c1": dict(nx=128, nt=256, m=4, levels=2, T=0.5),
+    # config 4 (u0 = 0.5 + sin 2 pi x), CFL-capped to 2 levels, and a short
+    # case of the same kernel shape
+    "c4": dict(nx=16384, nt=65536, m=8, levels=2, T=0.12, ic="sine"),
+    "c4small": dict(nx=16384, nt=8192, m=8, levels=2, T=0.015, ic="sine"),
 }
 KERNELS = {"relax": 0, "restrict": 1, "coarsest": 2, "interp": 3, "serial": -1}
 
@@ -86,7 +91,8 @@ def main(argv=None):
         return 0
     c = CASES[a.case]
     s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"], precision=a.precision)
-    u0 = torch.as_tensor(inputs.fourier_ic(c["nx"], seed=0), device="cuda")
+    u0_np = inputs.sine_ic(c["nx"]) if c.get("ic") == "sine" else inputs.fourier_ic(c["nx"], seed=0)
+    u0 = torch.as_tensor(u0_np, device="cuda")
     if a.kernel == "serial":
         # 64 serial steps on the sequential stepper the context chose, in the
         # NVTX range "profiled" (allocation, which times the candidates,
