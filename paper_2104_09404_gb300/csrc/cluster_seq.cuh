@@ -159,8 +159,12 @@ struct ClusterSlab {
                     const R x = w[c];
                     R p, q;
                     if (SCHEME == SCH_WENO5_SSPRK3) {
-                        p = FLUX == FLX_BURGERS ? Ar<R>::mul(Ar<R>::fma(R(0.125), x, a4), x) : R(0.5) * x;
-                        q = FLUX == FLX_BURGERS ? Ar<R>::mul(Ar<R>::fma(R(0.125), x, -a4), x) : R(0);
+                        if (FLUX == FLX_BURGERS) {
+                            burgers_q(x, a4, p, q);
+                        } else {
+                            p = R(0.5) * x;
+                            q = R(0);
+                        }
                     } else {
                         const R f2 = R(0.5) * phys_flux<FLUX>(x);
                         p = fma(h, x, f2);

@@ -191,8 +191,10 @@ __global__ void __launch_bounds__(GRID_THREADS) k_seq_grid(GridArgs<R> ga)
                 qb[slot] = fma(-h, x, p);
             } else if (FLUX == FLX_BURGERS) {
                 const R a4 = R(0.25) * alpha;
-                qa[slot] = AR::mul(AR::fma(R(0.125), x, a4), x);
-                qb[slot] = AR::mul(AR::fma(R(0.125), x, -a4), x);
+                R p, q;
+                burgers_q(x, a4, p, q);
+                qa[slot] = p;
+                qb[slot] = q;
             } else {
                 qa[slot] = R(0.5) * x;
             }

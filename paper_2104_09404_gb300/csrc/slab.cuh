@@ -432,6 +432,22 @@ __device__ __forceinline__ V split_flux_win_adv(const WenoWin<V> &P, V qp)
     return A::fma(A::k(6.0), qp, A::div(Np, Dp));
 }
 
+// The split fluxes of Burgers' flux in the scaled form the windows take,
+// q^+/- = f^+/-/2 = u (u/8 +/- alpha/4) (Eq. LFflux with f = u^2/2), a4 =
+// alpha/4.  FP64 forms q^- from q^+ as q^+ - (alpha/2) u, one multiply-add
+// instead of two operations (the FP64 sweeps are bound by their FP64
+// instruction count); FP32 keeps both products.  Every kernel forms them
+// here, so the steppers agree bit for bit.
+template <typename R>
+__device__ __forceinline__ void burgers_q(R x, R a4, R &qp, R &qm)
+{
+    qp = Ar<R>::mul(Ar<R>::fma(R(0.125), x, a4), x);
+    if constexpr (sizeof(R) == 8)
+        qm = Ar<R>::fma(R(-2) * a4, x, qp);   // -2 a4 = -alpha/2 exactly
+    else
+        qm = Ar<R>::mul(Ar<R>::fma(R(0.125), x, -a4), x);
+}
+
 // Runge-Kutta stage updates of Eq. (SSPRK3) and forward Euler (Eq. SSPRK1)
 // from the difference dG = G_{i+1/2} - G_{i-1/2} of a cell's interface
 // values G = F / s (s = 1/3 for the WENO5 split form, whose G is 3F; s = 1
@@ -813,20 +829,30 @@ struct Slab {
             alpha = key_value(m);
         }
         const R a4 = R(0.25) * alpha;
-        auto qp = [&](R x) { return FLUX == FLX_BURGERS ? Ar<R>::mul(Ar<R>::fma(R(0.125), x, a4), x) : R(0.5) * x; };
-        auto qm = [&](R x) { return Ar<R>::mul(Ar<R>::fma(R(0.125), x, -a4), x); };
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
             if (cell(c) < nx) {
-                MGRIT_SH(qa, pc(c, 0), lim()) = qp(w[c]);
-                if (FLUX == FLX_BURGERS) MGRIT_SH(qb, pc(c, 0), lim()) = qm(w[c]);
+                if (FLUX == FLX_BURGERS) {
+                    R qpv, qmv;
+                    burgers_q(w[c], a4, qpv, qmv);
+                    MGRIT_SH(qa, pc(c, 0), lim()) = qpv;
+                    MGRIT_SH(qb, pc(c, 0), lim()) = qmv;
+                } else {
+                    MGRIT_SH(qa, pc(c, 0), lim()) = R(0.5) * w[c];
+                }
             }
         if (threadIdx.x < 2 * GHOST) {
             const int t = (int)threadIdx.x;
             const int i = t < GHOST ? t - GHOST : nx + t - GHOST;
             const R x = gw[6 * p + t];
-            ce(qa, i) = qp(x);
-            if (FLUX == FLX_BURGERS) ce(qb, i) = qm(x);
+            if (FLUX == FLX_BURGERS) {
+                R qpv, qmv;
+                burgers_q(x, a4, qpv, qmv);
+                ce(qa, i) = qpv;
+                ce(qb, i) = qmv;
+            } else {
+                ce(qa, i) = R(0.5) * x;
+            }
         }
         __syncthreads();
         if constexpr (sizeof(R) == 4 && CPT <= 16)
@@ -876,8 +902,10 @@ struct Slab {
                     const int i = cell(c);
                     if (i < nx) {
                         if (FLUX == FLX_BURGERS) {
-                            put_c(qa, c, Ar<R>::mul(Ar<R>::fma(R(0.125), w[c], a4), w[c]));
-                            put_c(qb, c, Ar<R>::mul(Ar<R>::fma(R(0.125), w[c], -a4), w[c]));
+                            R qpv, qmv;
+                            burgers_q(w[c], a4, qpv, qmv);
+                            put_c(qa, c, qpv);
+                            put_c(qb, c, qmv);
                         } else {
                             put_c(qa, c, R(0.5) * w[c]);
                         }
