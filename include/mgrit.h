@@ -317,7 +317,8 @@ int mgrit_step_vjp(mgrit_ctx *ctx, const double *u_dev, const double *lam_dev, d
  * forward keeping u^{mj}, j < nt/m, then for each chunk from the last it
  * recomputes the chunk's m states from its checkpoint and applies their m
  * transposed steps backward; for nx >= 512 on a thread-block cluster of up to
- * 16 CTAs (mgrit_adjoint_query(ctx, 2)).  Asynchronous.  Baseline for
+ * 16 CTAs, its size timed when the adjoint workspaces are allocated
+ * (mgrit_adjoint_query(ctx, 2)).  Asynchronous.  Baseline for
  * mgrit_adjoint. */
 int mgrit_adjoint_serial(mgrit_ctx *ctx, const double *u0_dev, const double *lamT_dev,
                          double *lam0_dev, void *stream);

@@ -161,31 +161,81 @@ static int adj_alloc(mgrit_ctx *ctx, AdjWork *w)
     return MGRIT_OK;
 }
 
-// Cluster for the sequential adjoint chains: as the forward stepper, the
-// largest power of two K <= 16 leaving at least 256 cells per CTA, reduced
-// until one cluster of that shape can be co-scheduled; nx < 512 keeps one CTA.
-static void adj_choose_cluster(const mgrit_ctx *ctx, AdjWork *w)
+// One cluster shape for the sequential adjoint chains: K CTAs of at most 1024
+// and at least 64 cells each (1 or 2 cells per thread), if it can be
+// co-scheduled.
+static bool adj_cluster_shape(const mgrit_ctx *ctx, int K, AdjWork *w)
+{
+    const int nx = ctx->nx;
+    const int nmax = (nx + K - 1) / K;
+    if (K < 2 || K > CLUSTER_MAX || nmax > 1024 || nmax < 64) return false;
+    const int cpt = nmax <= 512 ? 1 : 2;
+    const void *fn = adj_table().kc[ctx->scheme][ctx->flux][cpt - 1];
+    const size_t fwd = cluster_smem_bytes<double>(nx, K);
+    const size_t smem = fwd + cluster_adj_extra_bytes<double>(nx, K);
+    const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
+    if (!fn || !cluster_fits(fn, K, threads, smem)) return false;
+    w->cfn = fn;
+    w->cK = K;
+    w->cthreads = threads;
+    w->csmem = smem;
+    w->cfwd = fwd;
+    return true;
+}
+
+static AdjArgs adj_base(const mgrit_ctx *ctx, int mode, int l);
+static cudaError_t adj_launch_seq(const mgrit_ctx *ctx, cudaStream_t s, AdjArgs *a);
+
+// Cluster for the sequential adjoint chains.  The forward stepper's rule
+// gives K0: the largest power of two K <= 16 leaving at least 256 cells per
+// CTA, reduced until one cluster of that shape can be co-scheduled (nx < 512:
+// none, one CTA).  A transposed step is latency-bound on its cluster (four
+// cluster barriers per stage), so K0, 2 K0 and 4 K0 (at most 16, at least 64
+// cells per CTA) are timed on 8 steps of the coarsest adjoint solve on zero
+// data, and the fastest is kept.
+static int adj_choose_cluster(mgrit_ctx *ctx, AdjWork *w)
 {
     w->cfn = nullptr;
     const int nx = ctx->nx;
     int K = 1;
     while (K < CLUSTER_MAX && nx / (2 * K) >= 256) K *= 2;
-    for (; K >= 2; K /= 2) {
-        const int nmax = (nx + K - 1) / K;
-        const int cpt = nmax <= 512 ? 1 : 2;
-        if (nmax > 1024) break;
-        const void *fn = adj_table().kc[ctx->scheme][ctx->flux][cpt - 1];
-        const size_t fwd = cluster_smem_bytes<double>(nx, K);
-        const size_t smem = fwd + cluster_adj_extra_bytes<double>(nx, K);
-        const int threads = (((nmax + cpt - 1) / cpt + 31) / 32) * 32;
-        if (!cluster_fits(fn, K, threads, smem)) continue;
-        w->cfn = fn;
-        w->cK = K;
-        w->cthreads = threads;
-        w->csmem = smem;
-        w->cfwd = fwd;
-        return;
+    for (; K >= 2; K /= 2)
+        if (adj_cluster_shape(ctx, K, w)) break;
+    if (!w->cfn) return MGRIT_OK;
+    const int K0 = w->cK;
+    const int l = ctx->L - 1;
+    AdjArgs a = adj_base(ctx, ADJ_SEQ, l);
+    a.src = w->g[l];
+    a.g = w->g[l];
+    a.rows = w->u[l];
+    a.nsteps = ctx->nt_l[l] < 8 ? ctx->nt_l[l] : 8;
+    a.nrows_g = a.nrows_rows = ctx->nt_l[l] + 1;
+    cudaStream_t s = ctx->cap;
+    CK(cudaMemsetAsync(w->traj, 0, sizeof(double) * (size_t)ctx->nt * nx, s));
+    CK(cudaMemsetAsync(w->g[l], 0, sizeof(double) * (size_t)(ctx->nt_l[l] + 1) * nx, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int bestK = K0;
+    float best = -1.f;
+    for (int k = K0; k <= 4 * K0 && k <= CLUSTER_MAX; k *= 2) {
+        if (!adj_cluster_shape(ctx, k, w)) continue;
+        float ms = 0.f;
+        CK(adj_launch_seq(ctx, s, &a));   // warm-up
+        CK(cudaEventRecord(e0, s));
+        CK(adj_launch_seq(ctx, s, &a));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best < 0.f || ms < best) {
+            best = ms;
+            bestK = k;
+        }
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    adj_cluster_shape(ctx, bestK, w);
+    return MGRIT_OK;
 }
 
 // Cluster shape for the adjoint chunks of level l, by the forward rule: with a
@@ -251,7 +301,10 @@ static int adj_ensure(mgrit_ctx *ctx)
         mgrit_adj_free(ctx);
         return st;
     }
-    adj_choose_cluster(ctx, w);
+    if ((st = adj_choose_cluster(ctx, w))) {
+        mgrit_adj_free(ctx);
+        return st;
+    }
     if (!w->fn && !w->cfn) {
         mgrit_adj_free(ctx);
         return mgrit_fail(ctx, MGRIT_EINVAL, "no adjoint cluster fits nx = %d", ctx->nx);

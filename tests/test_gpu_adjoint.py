@@ -127,15 +127,18 @@ def test_adjoint_serial_parity(M, nx, nt, m, T, scheme, flux):
     assert relerr(got, ref) <= RTOL
 
 
-@pytest.mark.parametrize("nx,K", [(256, 1), (1000, 2), (2048, 8), (4096, 16)])
-def test_sequential_adjoint_cluster_shape(M, nx, K):
+@pytest.mark.parametrize("nx,K0", [(256, 1), (1000, 2), (2048, 8), (4096, 16)])
+def test_sequential_adjoint_cluster_shape(M, nx, K0):
     # the serial adjoint and the coarsest adjoint solve spread one slab over a
-    # cluster of K CTAs (at least 256 cells each), as the forward stepper does
+    # cluster: K0 CTAs by the forward stepper's rule (at least 256 cells
+    # each), or 2 K0 or 4 K0 (at most 16, at least 64 cells each) where that
+    # was timed faster when the adjoint workspaces were allocated
     S = solver(M, nx, 16, 4, 2, 0.001)
     u0 = dev(inputs.fourier_ic(nx, seed=1))
     S.adjoint_serial(u0, u0.clone())
     torch.cuda.synchronize()
-    assert S.adjoint_query(2) == K
+    allowed = {1} if K0 == 1 else {k for k in (K0, 2 * K0, 4 * K0) if k <= 16 and -(-nx // k) >= 64}
+    assert S.adjoint_query(2) in allowed
 
 
 # ------------------------------------------------------------ MGRIT --------
