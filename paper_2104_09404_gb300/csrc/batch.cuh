@@ -73,8 +73,8 @@ struct RestrictBatchArgs {
     int nblocks;      // blocks given to this item
 };
 
-// Residual + FAS restriction of many items; item blocks walk their own
-// element range with a fixed stride, so every partial sum is reproducible.
+// Residual + FAS restriction of many items; the blocks of an item walk its
+// rows and columns as k_restrict's do, so every partial sum is reproducible.
 template <typename S, typename U>
 __global__ void __launch_bounds__(RESTRICT_THREADS)
     k_restrict_batch(const RestrictBatchArgs *__restrict__ args, const BatchItem *__restrict__ map,
@@ -85,27 +85,7 @@ __global__ void __launch_bounds__(RESTRICT_THREADS)
     if (active && !active[it.instance]) return;
     const RestrictBatchArgs &ba = args[it.args];
     const RestrictArgs &a = ba.r;
-    const S *newC = static_cast<const S *>(a.newC);
-    const S *phirow = static_cast<const S *>(a.phirow);
-    const S *cstep = static_cast<const S *>(a.cstep);
-    U *un = static_cast<U *>(a.un);
-    const long long n = (long long)a.nC * a.nx;
-    const long long stride = (long long)ba.nblocks * RESTRICT_THREADS;
-    double acc = 0.0;
-    for (long long e = (long long)it.block * RESTRICT_THREADS + threadIdx.x; e < n; e += stride) {
-        const long long i = 1 + e / a.nx;
-        const long long c = e - (i - 1) * a.nx;
-        const long long at = i * a.nx + c;
-        const double gl = a.g ? a.g[(long long)a.m * i * a.nx + c] : 0.0;
-        const double phi = (double)phirow[at];
-        const double uc = (double)newC[at];
-        const double r = phi + gl - uc;
-        acc += r * r;
-        if (cstep) {
-            a.gn[at] = gl + phi - (double)cstep[(i - 1) * a.nx + c];
-            un[at] = (U)(a.guess == 0 ? phi + gl : uc);
-        }
-    }
+    double acc = restrict_block<S, U>(a, it.block, ba.nblocks);
     if (a.partials) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -22,33 +22,7 @@ template <typename S, typename U>
 __global__ void __launch_bounds__(RESTRICT_THREADS) k_restrict(RestrictArgs a)
 {
     __shared__ double red[RESTRICT_THREADS / 32];
-    const S *newC = static_cast<const S *>(a.newC);
-    const S *phirow = static_cast<const S *>(a.phirow);
-    const S *cstep = static_cast<const S *>(a.cstep);
-    U *un = static_cast<U *>(a.un);
-    const long long n = (long long)a.nC * a.nx;
-    double acc = 0.0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long i = 1 + e / a.nx;
-        const long long c = e - (i - 1) * a.nx;
-        const long long at = i * a.nx + c;
-#ifdef MGRIT_DEBUG
-        if (a.g && (long long)a.m * i >= a.nrows_g) {
-            printf("MGRIT_DEBUG restrict g row %lld of %lld\n", (long long)a.m * i, a.nrows_g);
-            continue;
-        }
-#endif
-        const double gl = a.g ? a.g[(long long)a.m * i * a.nx + c] : 0.0;
-        const double phi = (double)phirow[at];
-        const double uc = (double)newC[at];
-        const double r = phi + gl - uc;
-        acc += r * r;
-        if (cstep) {
-            a.gn[at] = gl + phi - (double)cstep[(i - 1) * a.nx + c];
-            un[at] = (U)(a.guess == 0 ? phi + gl : uc);
-        }
-    }
+    double acc = restrict_block<S, U>(a, (int)blockIdx.x, (int)gridDim.x);
     if (a.partials) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -105,12 +79,12 @@ static int stream_blocks(long long n)
 
 int restrict_blocks(int nC, int nx)
 {
-    const long long n = (long long)nC * nx;
-    long long b = (n + RESTRICT_THREADS * 4 - 1) / (RESTRICT_THREADS * 4);
-    const long long cap = 152 * 8;   // 8 resident blocks on each of the 152 SMs
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (int)b;
+    const int gx = (nx + 2 * RESTRICT_THREADS - 1) / (2 * RESTRICT_THREADS);
+    const int cap = 152 * 8;   // 8 resident blocks on each of the 152 SMs
+    int gy = cap / gx;
+    if (gy > nC) gy = nC;
+    if (gy < 1) gy = 1;
+    return gx * gy;
 }
 
 cudaError_t launch_restrict(const RestrictArgs &a, int blocks, cudaStream_t s)
