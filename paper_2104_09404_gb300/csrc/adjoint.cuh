@@ -51,12 +51,18 @@ __device__ __forceinline__ void weno5_left_grad(R a, R b, R c, R d, R e, R (&g)[
     const R s0 = eps + R(13.0 / 12.0) * x0 * x0 + R(0.25) * y0 * y0;
     const R s1 = eps + R(13.0 / 12.0) * x1 * x1 + R(0.25) * y1 * y1;
     const R s2 = eps + R(13.0 / 12.0) * x2 * x2 + R(0.25) * y2 * y2;
-    const R s12 = s1 * s2;
-    const R iD = R(1) / (s0 * s12);
-    const R r0 = s12 * iD, r1 = s0 * s2 * iD, r2 = s0 * s1 * iD;   // 1 / s_r
-    const R a0 = R(0.1) * r0 * r0, a1 = R(0.6) * r1 * r1, a2 = R(0.3) * r2 * r2;
-    const R inv = R(1) / (a0 + a1 + a2);
-    const R w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
+    // With P_r the product of the two other s and S = s0 s1 s2, the weights
+    // are w_r = d_r P_r^2 / Q with Q = sum_r d_r P_r^2, and 1/s_r = P_r / S:
+    // both quotients come from one reciprocal X = 1 / (Q S) (1/Q = S X,
+    // 1/S = Q X).  Q S ~ s^7 stays inside the FP64 range for s <= 1e40.
+    const R P0 = s1 * s2, P1 = s0 * s2, P2 = s0 * s1;
+    const R S = s0 * P0;
+    const R t0 = R(0.1) * P0 * P0, t1 = R(0.6) * P1 * P1, t2 = R(0.3) * P2 * P2;
+    const R Q = t0 + t1 + t2;
+    const R X = R(1) / (Q * S);
+    const R iQ = S * X, iS = Q * X;
+    const R r0 = P0 * iS, r1 = P1 * iS, r2 = P2 * iS;   // 1 / s_r
+    const R w0 = t0 * iQ, w1 = t1 * iQ, w2 = t2 * iQ;
     const R W = w0 * p0 + w1 * p1 + w2 * p2;
     // (p_r - W) (dalpha_r / dbeta_r) / sum alpha = (p_r - W) (-2 w_r / s_r)
     const R k0 = (p0 - W) * (R(-2) * w0 * r0);
