@@ -2085,7 +2085,8 @@ extern "C" int mgrit_batch_autotune(mgrit_batch *b, const double *const *u0_dev,
 // launch tables of its own (dropped once the launches have finished).
 extern "C" int mgrit_batch_launch_relax(mgrit_batch *b, int reps, void *stream)
 {
-    if (!b || reps < 1) return MGRIT_EINVAL;
+    if (!b) return MGRIT_EINVAL;
+    if (reps < 1) return bfail(b, MGRIT_EINVAL, "reps must be at least 1");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<BLaunch> ls;
     const size_t keep = b->tables.size();
