@@ -53,13 +53,13 @@ static const KernelTable &table()
 }
 
 // smallest cells-per-thread giving at most MAX_THREADS threads per CTA; FP64
-// WENO5 slabs start at 2, so that every shape forms the interface pairs of
-// split_flux_pair (and gives the same bits)
+// WENO5 slabs start at 4, so that every shape forms the interface quads of
+// split_flux_quad (and gives the same bits)
 static bool choose_launch(int nx, int scheme, int flux, int f32, Launch *ln)
 {
     memset(ln, 0, sizeof *ln);
     const int ncpt = f32 ? NCPT : NCPT64;
-    for (int ci = !f32 && scheme == MGRIT_WENO5_SSPRK3 ? 1 : 0; ci < ncpt; ++ci) {
+    for (int ci = !f32 && scheme == MGRIT_WENO5_SSPRK3 ? 2 : 0; ci < ncpt; ++ci) {
         const int cpt = CPT_VALUES[ci];
         const int need = (nx + cpt - 1) / cpt;
         if (need <= MAX_THREADS) {

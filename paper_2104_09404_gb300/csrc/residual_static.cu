@@ -75,11 +75,11 @@ cudaError_t scratch_address(double **out, int *dev_out)
 }
 
 // the FP64 one-CTA slab for (scheme, flux, nx): the smallest cells per
-// thread giving at most MAX_THREADS threads (at least 2 for WENO5, as in the
-// solver contexts, so that both form the same interface pairs)
+// thread giving at most MAX_THREADS threads (at least 4 for WENO5, as in the
+// solver contexts, so that both form the same interface quads)
 const void *select_slab(int nx, int scheme, int flux, int *threads, int *cpt, int *ci_out)
 {
-    for (int ci = scheme == MGRIT_WENO5_SSPRK3 ? 1 : 0; ci < NCPT64; ++ci) {
+    for (int ci = scheme == MGRIT_WENO5_SSPRK3 ? 2 : 0; ci < NCPT64; ++ci) {
         const int need = (nx + CPT_VALUES[ci] - 1) / CPT_VALUES[ci];
         if (need <= MAX_THREADS) {
             *threads = ((need + 31) / 32) * 32;

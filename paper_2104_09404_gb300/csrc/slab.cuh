@@ -376,8 +376,8 @@ __device__ __forceinline__ V split_flux_combine(V Np, V Dp, V Nm, V Dm, V qp, V 
 }
 
 // FP64: the numerator and denominator of split_flux_combine's fraction, and
-// its base term, for an interface whose division is shared with its pair
-// partner (split_flux_pair)
+// its base term, for an interface whose division is shared with others
+// (split_flux_pair, split_flux_quad)
 struct SplitParts {
     double num, den, base;
 };
@@ -409,6 +409,30 @@ __device__ __forceinline__ void split_flux_pair(const SplitParts &a, const Split
     } else {
         Ga = A::fma(6.0, a.base, A::div(a.num, a.den));
         Gb = A::fma(6.0, b.base, A::div(b.num, b.den));
+    }
+}
+
+// G of four interfaces from one reciprocal of the product of their
+// denominators: r = 1/(d0 d1 d2 d3), 1/(d0 d1) = r d2 d3 and 1/(d2 d3) =
+// r d0 d1, then each quotient as in split_flux_pair.  The product lies in
+// [1e-184, 1e264] for |q| <= 1e3; outside [2^-996, 2^997] the two pairs are
+// formed instead (each with its own range test).
+__device__ __forceinline__ void split_flux_quad(const SplitParts (&x)[4], double (&G)[4])
+{
+    using A = Ar<double>;
+    const double p01 = A::mul(x[0].den, x[1].den), p23 = A::mul(x[2].den, x[3].den);
+    const double p = A::mul(p01, p23);
+    const unsigned e = ((unsigned)__double2hiint(p) >> 20) & 0x7ffu;
+    if (e - 27u <= 1993u) {
+        const double r = __drcp_rn(p);
+        const double i01 = A::mul(r, p23), i23 = A::mul(r, p01);   // 1/(d0 d1), 1/(d2 d3)
+        G[0] = A::fma(6.0, x[0].base, A::mul(x[0].num, A::mul(x[1].den, i01)));
+        G[1] = A::fma(6.0, x[1].base, A::mul(x[1].num, A::mul(x[0].den, i01)));
+        G[2] = A::fma(6.0, x[2].base, A::mul(x[2].num, A::mul(x[3].den, i23)));
+        G[3] = A::fma(6.0, x[3].base, A::mul(x[3].num, A::mul(x[2].den, i23)));
+    } else {
+        split_flux_pair(x[0], x[1], G[0], G[1]);
+        split_flux_pair(x[2], x[3], G[2], G[3]);
     }
 }
 
@@ -548,8 +572,8 @@ struct Slab {
     // (psiOrder 0, Eq. coarseLFord0) or first order (1, Eq. coarseLFord1)
     int psiM, psiOrder;
     R psiDt;
-    // FP64 WENO5 split form: interfaces in pairs share one reciprocal
-    // (split_flux_pair).  Set by the relaxation and interpolation sweeps; the
+    // FP64 WENO5 split form: interfaces in quads share one reciprocal
+    // (split_flux_quad).  Set by the relaxation and interpolation sweeps; the
     // sequential chains keep one division per interface, the operations of
     // the cluster and grid steppers.
     bool pair_div;
@@ -694,11 +718,33 @@ struct Slab {
         if (FLUX == FLX_BURGERS) M.init(B_(-1), B_(0), B_(1), B_(2), B_(3));
         if constexpr (sizeof(R) == 8 && FLUX == FLX_BURGERS && CPT >= 2) {
             if (pair_div) {
-                // interfaces (k, k+1), k even: i0 is even, so the pairs are
-                // the global pairs (2j, 2j+1) whatever CPT; a last interface
-                // without its partner (n odd) takes the plain division
+                // interfaces in quads (k .. k+3, k a multiple of 4), then the
+                // rest in pairs and a last one alone: i0 is a multiple of 4
+                // (FP64 WENO5 slabs have at least 4 cells per thread), so every
+                // CTA shape forms the same global quads [4j, 4j+3] and the
+                // same tail
+                int k0 = 0;
 #pragma unroll 1
-                for (int k = 0; k < n; k += 2) {
+                for (; k0 + 3 < n; k0 += 4) {
+                    SplitParts x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        R Np, Dp, Nm, Dm;
+                        P.left(Np, Dp);
+                        M.right(Nm, Dm);
+                        x[q] = split_flux_parts(Np, Dp, Nm, Dm, A_(k0 + q), B_(k0 + q + 1));
+                        if (k0 + q + 1 < n) {
+                            P.advance(A_(k0 + q + 3));
+                            M.advance(B_(k0 + q + 4));
+                        }
+                    }
+                    R G[4];
+                    split_flux_quad(x, G);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) MGRIT_SH(qf, rs(k0 + q), lim()) = G[q];
+                }
+#pragma unroll 1
+                for (int k = k0; k < n; k += 2) {
                     R Np, Dp, Nm, Dm;
                     P.left(Np, Dp);
                     M.right(Nm, Dm);

@@ -88,8 +88,8 @@ def test_create_set_params_destroy_without_gpu(lib):
         q = M.mgrit_params.from_buffer_copy(p)
         setattr(q, field, bad)
         assert lib.mgrit_set_params(h, ctypes.byref(q)) == M.EINVAL, field
-    # 100 cells: FP64 WENO5 slabs take at least 2 cells per thread (interface pairs)
-    assert lib.mgrit_query(h, 0) == 2 and lib.mgrit_query(h, 1) == 64
+    # 100 cells: FP64 WENO5 slabs take at least 4 cells per thread (interface quads)
+    assert lib.mgrit_query(h, 0) == 4 and lib.mgrit_query(h, 1) == 32
     assert lib.mgrit_query(h, 2) == 0 and lib.mgrit_query(h, 9) == -1    # nothing allocated yet
     assert lib.mgrit_query(h, 3) == 0                                     # grid stepper unknown yet
     # chunk cluster sizes of levels 0 and 1 (3 levels): unknown before allocation

@@ -334,10 +334,10 @@ def test_full_width_multicycle_solve_matches_oracle(M):
     assert relerr(uT, ref["uT"]) <= RTOL
 
 
-def _pair_denominator_products(u):
-    # coverage check only: the products den_2j * den_2j+1 of the interface
-    # denominators D+ D- (Sec. 2.1.1 indicators in closed form) that the FP64
-    # sweeps pair up, from the stage input u
+def _interface_denominators(u):
+    # coverage check only: the interface denominators D+ D- (Sec. 2.1.1
+    # indicators in closed form) that the FP64 sweeps combine in quads and
+    # pairs, from the stage input u
     a = np.abs(u).max()
     qp, qm = u * (u / 8 + a / 4), u * (u / 8 - a / 4)
 
@@ -349,26 +349,30 @@ def _pair_denominator_products(u):
         return s1 * s2 + 6 * s0 * s2 + 3 * s0 * s1
 
     r = np.roll
-    with np.errstate(over="ignore"):
-        den = (dn(r(qp, 2), r(qp, 1), qp, r(qp, -1), r(qp, -2)) *
-               dn(r(qm, -3), r(qm, -2), r(qm, -1), qm, r(qm, 1)))
-        n = len(u) // 2
-        return den[0:2 * n:2] * den[1:2 * n:2]
+    return (dn(r(qp, 2), r(qp, 1), qp, r(qp, -1), r(qp, -2)) *
+            dn(r(qm, -3), r(qm, -2), r(qm, -1), qm, r(qm, 1)))
 
 
 @pytest.mark.parametrize("nx", [1000, 4096])
-def test_sweeps_where_paired_reciprocals_leave_their_range(M, nx):
-    # amplitudes from 1 to 1e7 across the slice: where |u| reaches ~1e6 the
-    # product of two interface denominators leaves [2^-996, 2^997] and the
-    # FP64 sweeps divide per interface; elsewhere the pair shares one
-    # reciprocal.  The first FCF relaxation from C-points all equal to u0
-    # gives Phi^m(u0) at every C-point (cycle 0 of Algorithm 1), which the
-    # oracle computes by m serial steps.
+def test_sweeps_where_shared_reciprocals_leave_their_range(M, nx):
+    # amplitudes from 1 to 1e7 across the slice: the FP64 sweeps share one
+    # reciprocal among four interfaces where the product of their
+    # denominators lies in [2^-996, 2^997], else among two where theirs does,
+    # else divide per interface; all three occur here.  The first FCF
+    # relaxation from C-points all equal to u0 gives Phi^m(u0) at every
+    # C-point (cycle 0 of Algorithm 1), which the oracle computes by m serial
+    # steps.
     x = (np.arange(nx) + 0.5) / nx
     u0 = inputs.fourier_ic(nx, seed=3) * 10.0 ** (3.5 + 3.5 * np.sin(2 * np.pi * x))
-    d = _pair_denominator_products(u0)
-    inside = (d > 2.0 ** -996) & (d < 2.0 ** 997)
-    assert inside.sum() > nx // 8 and (~inside).sum() > nx // 8   # both branches are taken
+    den = _interface_denominators(u0)
+    ok = lambda v: (v > 2.0 ** -996) & (v < 2.0 ** 997)
+    with np.errstate(over="ignore"):
+        n4 = len(u0) // 4
+        quad = den[0:4 * n4:4] * den[1:4 * n4:4] * den[2:4 * n4:4] * den[3:4 * n4:4]
+        pair = den[0:4 * n4:2] * den[1:4 * n4:2]
+    pair_ok = ok(pair).reshape(-1, 2)
+    assert ok(quad).sum() > 0 and (~ok(quad)).sum() > 0
+    assert pair_ok[~ok(quad)].any() and (~pair_ok[~ok(quad)]).any()
     nt, m = 64, 4
     T = 0.25 * nt / (nx * np.abs(u0).max())
     s = M.Solver(nx, nt, m, 2, T=T, max_iter=0)
