@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(nx=4096, nt=16384, m=4, levels=6, T=1.0, seed=0)
 SAMPLE = dict(nx=4096, nt=4096, m=4, levels=6, T=0.25, seed=0)   # CPU baseline sample
 SAMPLE1 = dict(nx=4096, nt=1024, m=4, levels=5, T=0.0625, seed=0)  # single-thread sample
+CPU_BASELINE_SECONDS = 10.0   # the host-core timing repeats its sample for at least this long
 
 # Algorithmic FLOPs per cell update of one SSPRK3 step of WENO5-JS with the
 # global LF splitting (Burgers): the operations the paper's formulas take, as
@@ -199,19 +200,26 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- oracle ---
 
-def oracle_cycle_rate(sample, cycles=1):
-    """The oracle, as it stands, on `cycles` V-cycles of the sample; returns
-    (cell updates/s, seconds, threads).  Cell updates counted like the GPU's."""
+def oracle_cycle_rate(sample, min_seconds=0.0):
+    """The oracle, as it stands, on one V-cycle of the sample from its initial
+    iterate, repeated until `min_seconds` have passed; returns (cell
+    updates/s, seconds, threads, repetitions).  Cell updates counted like the
+    GPU's."""
     import numpy as np  # noqa: F401
     import oracle as O
     from paper_2104_09404_gb300 import inputs
     O.build()
     u0 = inputs.fourier_ic(sample["nx"], seed=sample["seed"])
+    reps = 0
     t0 = time.perf_counter()
-    O.vcycles(u0, sample["nt"], sample["m"], sample["levels"], sample["T"], cycles)
-    dt = time.perf_counter() - t0
-    upd = cycle_updates(sample) * cycles
-    return upd / dt, dt, O.num_threads()
+    while True:
+        O.vcycles(u0, sample["nt"], sample["m"], sample["levels"], sample["T"], 1)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds:
+            break
+    upd = cycle_updates(sample) * reps
+    return upd / dt, dt, O.num_threads(), reps
 
 
 def oracle_single_thread(sample):
@@ -292,7 +300,7 @@ def run_reference(args):
         oracle_cycle_rate(SAMPLE)
     times = []
     for _ in range(args.steps):
-        _, dt, cores = oracle_cycle_rate(SAMPLE)
+        _, dt, cores, _ = oracle_cycle_rate(SAMPLE)
         times.append(dt)
     tot = sum(times)
     upd = cycle_updates(SAMPLE) * args.steps
@@ -783,9 +791,10 @@ def run_mgrit(args):
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        rate, secs, cores = oracle_cycle_rate(SAMPLE)
+        rate, secs, cores, reps = oracle_cycle_rate(SAMPLE, min_seconds=CPU_BASELINE_SECONDS)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-               "sample": sample_desc(SAMPLE), "seconds": secs, "cpu_model": host_cpu_model()}
+               "sample": "%s, repeated %d times" % (sample_desc(SAMPLE), reps), "seconds": secs,
+               "repetitions": reps, "cpu_model": host_cpu_model()}
         one = oracle_single_thread(SAMPLE1)
         if one is not None:
             cpu["single_thread"] = {"value": one[0], "unit": "cell-updates/s", "threads": one[2],
