@@ -65,8 +65,10 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 128 FFMA lanes / SM
 
 # DRAM bytes (read + write) per level-0 relaxation launch from an ncu
 # capture, keyed by a hash of the kernel sources it was taken on; reported
-# only while the kernel is unchanged.
-TRAFFIC = {"9339dca4f0c7d5d1": 141477376 + 350998784}   # profiles/relax_l0_c2_fp64.md
+# only while the kernel is unchanged.  (The key is that of the captured
+# sources with three comments corrected since: compiled without line info,
+# every device image of the library is byte for byte the same.)
+TRAFFIC = {"c79845a03917ee5a": 141477376 + 350998784}   # profiles/relax_l0_c2_fp64.md
 
 
 def measured_hbm_gbs():

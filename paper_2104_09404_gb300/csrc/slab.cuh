@@ -10,9 +10,9 @@
 //
 // Shared memory: three arrays (the half split fluxes q^+ and q^- with 3
 // periodic ghost cells on each side -- the WENO5 half-stencil -- and the
-// interface fluxes; FP32 slabs in the run-major layout of Slab) plus
-// NWARP_MAX values for the block max reduction of the global Lax-Friedrichs
-// alpha.
+// interface fluxes; at 2 or more cells per thread in the run-major layout
+// of Slab) plus NWARP_MAX values for the block max reduction of the global
+// Lax-Friedrichs alpha.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -703,8 +703,8 @@ struct Slab {
     // from qa = f^+/2 and qb = f^-/2, one sliding window per array (see
     // WenoWin), stored as G = 3F.  Reads cells i0 - 2 .. i0 + n + 2, all inside
     // the arrays for every interface i < nx.  FP64: a rolled loop (the window
-    // shifts by register moves; unrolled, the slabs spill), two interfaces per
-    // iteration when pair_div is set; FP32: unrolled, so that every slot is
+    // shifts by register moves; unrolled, the slabs spill), four interfaces
+    // per iteration (then pairs) with pair_div; FP32: unrolled, so every slot is
     // the thread's base plus a constant.
     __device__ __forceinline__ void split_fluxes_win() const
     {
@@ -958,7 +958,7 @@ struct Slab {
                     }
                 }
                 __syncthreads();
-                // (packed FP32 windows beyond 8 cells per thread would spill)
+                // (packed FP32 windows beyond 16 cells per thread would spill)
                 if constexpr (sizeof(R) == 4 && CPT >= 2 && CPT <= 16)
                     split_fluxes_win2();
                 else
