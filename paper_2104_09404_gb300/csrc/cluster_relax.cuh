@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(512) k_slab_cluster(SlabArgs<R> a)
 // slab's layout and arithmetic, with alpha and the ghost cells exchanged
 // through distributed shared memory, one cluster barrier per stage.  Slices
 // too wide for one CTA's registers (FP32 beyond 8192 cells, FP64 beyond 8192)
-// then run at 16 cells per thread with the sliding windows.
+// then run at 8 or 16 cells per thread (timed at allocation) with the
+// sliding windows.
 template <typename R, int SCHEME, int FLUX, int CPT>
 __global__ void __launch_bounds__(512) k_slab_tlc(SlabArgs<R> a)
 {
