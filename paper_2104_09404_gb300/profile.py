@@ -21,6 +21,13 @@ T 0.12, u0 Fourier seed 1, target seed 1001): a forward solve, then one
 adjoint cycle (k_adjoint launches: the forward-trajectory regeneration, then
 the level-0 adjoint relaxation).
 
+    python -m paper_2104_09404_gb300.profile --batch
+
+builds the 64-instance uneven batch (inputs.batch_workload, seed 0; FP32
+sweeps), autotunes it as the benchmark does, runs one cycle, and then
+launches its level-0 relaxation (one k_slab_batch launch per (flux, cells
+per thread, threads) class) `reps` times inside the range "profiled".
+
     python -m paper_2104_09404_gb300.profile --peaks
 
 measures the multiply-add throughput of the FP64 and FP32 pipes
@@ -58,6 +65,8 @@ def main(argv=None):
     p.add_argument("--level", type=int, default=0)
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--adjoint", action="store_true")
+    p.add_argument("--batch", action="store_true",
+                   help="the batched level-0 relaxation of the 64-instance workload")
     p.add_argument("--peaks", action="store_true", help="FP64 / FP32 multiply-add throughput")
     p.add_argument("--steppers", action="store_true",
                    help="microseconds per serial step on each sequential stepper")
@@ -88,6 +97,23 @@ def main(argv=None):
         s.adjoint(uC, (uT - target).contiguous())
         torch.cuda.synchronize()
         print("adjoint workload: trajectory + one adjoint cycle")
+        return 0
+    if a.batch:
+        insts, bu0 = inputs.batch_workload(seed=0, n=64)
+        bu0 = [torch.as_tensor(u, device="cuda") for u in bu0]
+        bt = mgrit.Batch(insts, precision=32)
+        bt.autotune(bu0, reps=2)
+        bt.run_cycles(bu0, 1)
+        bt.launch_relax(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        bt.launch_relax(a.reps)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        cells = sum(d["nx"] * (d["nt"] // d["m"]) * (2 * d["m"] + 1) for d in insts)
+        print("batched level-0 relaxation x%d: %d instances, %d cell updates per launch"
+              % (a.reps, len(insts), cells))
+        bt.close()
         return 0
     c = CASES[a.case]
     s = mgrit.Solver(c["nx"], c["nt"], c["m"], c["levels"], T=c["T"], precision=a.precision)
