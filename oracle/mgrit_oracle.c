@@ -47,9 +47,11 @@
  * Pinned by tests/test_oracle_*.py against closed forms (polynomial cell
  * averages, the smoothness-indicator integral of Eq. (B), the SSPRK3 Taylor
  * polynomial for a linear operator, exact shift of first-order upwind at
- * CFL 1, conservation, 5th-order accuracy) and against the MGRIT structure
- * (fixed point = serial stepping, two-level exactness, brute-force
- * monolithic residual).
+ * CFL 1, conservation, 5th-order accuracy, the exact entropy solution of
+ * Burgers Riemann problems), against the k = 2 tables as printed
+ * (tests/golden/, tests/test_golden_tables.py) and against the MGRIT
+ * structure (fixed point = serial stepping, two-level exactness,
+ * brute-force monolithic residual).
  */
 #include <math.h>
 #include <stdlib.h>
