@@ -1,7 +1,7 @@
 """The bench's multi-rank logic on CPU with the gloo backend (world size 2):
 replicas only, so the one exchange is the max of the per-rank times; the
 whole-job rate counts the units of all ranks; non-zero ranks of the oracle
-arm exit without work or output."""
+arm exit without work or output, and rank 0 prints the contract's line."""
 import importlib.util
 import os
 import socket
@@ -74,3 +74,27 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     monkeypatch.setattr(b, "oracle_cycle_rate", no_work)
     assert b.main() == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    # the oracle arm's JSON line on a tiny sample: the contract's keys, its
+    # own rate as cpu_baseline and e2e, and no host<->device bytes
+    import json
+    b = _bench()
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(b, "SAMPLE", dict(nx=64, nt=64, m=4, levels=2, T=0.05, seed=0))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1"])
+    assert b.main() == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["unit"] == "cell-updates/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert "nx=64" in d["config"]["workload"] and "nt=16384" in d["config"]["sample_of"]
+    steps_updates = b.cycle_updates(b.SAMPLE) * 2
+    assert d["value"] == pytest.approx(steps_updates / (d["ms_per_step"] * 2 / 1e3), rel=1e-9)
