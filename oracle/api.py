@@ -8,6 +8,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mgrit_oracle.c")
 _LIB = os.path.join(_HERE, "liborc_mgrit.so")
+# a prebuilt library to load instead (the mutation tests point this at copies
+# of the oracle with a planted mistake); build() leaves it untouched
+_LIB_OVERRIDE = os.environ.get("MGRIT_ORACLE_LIB")
 
 SCHEME_WENO5_SSPRK3, SCHEME_FO_FE, SCHEME_LF_FE = 0, 1, 2
 FLUX_BURGERS, FLUX_ADVECTION = 0, 1
@@ -21,13 +24,19 @@ OK, EINVAL, EDIVERGED, ENOTCONV = 0, -1, -4, -5
 _lib = None
 
 
+def compile_oracle(src, out):
+    """gcc, plain -O2, no FMA contraction (the same bits on x86 and Arm), OpenMP."""
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                           "-shared", src, "-o", out, "-lm"])
+
+
 def build(force=False):
-    """Compile the oracle with gcc (plain -O2, no FMA contraction, OpenMP)."""
+    """Compile the oracle (compile_oracle) unless it is up to date."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-               _SRC, "-o", tmp, "-lm"]
-        subprocess.check_call(cmd)
+        compile_oracle(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -35,8 +44,7 @@ def build(force=False):
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        lib = ctypes.CDLL(build())
         D = ctypes.c_double
         I = ctypes.c_int
         P = ctypes.c_void_p
