@@ -35,6 +35,8 @@ MUTANTS = {
                         "alpha[r] = (TAB_D[r] / 10.0) / den;", 0),
     "stencil-order": ("reading A5 (row r on cells i-r..i-r+2)", "const double *s = &q[2 - r];",
                       "const double *s = &q[r];", 0),
+    "weno-eps": ("reading A6 (eps = 1e-6)", "#define WENO_EPS 1e-6", "#define WENO_EPS 1e-5", 0),
+    "periodic-wrap": ("periodic indices", "return i < 0 ? i + nx : i;", "return i < 0 ? i + nx - 1 : i;", 0),
     # Secs. 2, 2.1, 2.1.2: flux, splitting, divergence form
     "burgers-flux": ("Eq. (burgers) f = u^2/2", "return flux == ORC_FLUX_BURGERS ? 0.5 * u * u : u;",
                      "return flux == ORC_FLUX_BURGERS ? u * u : u;", 0),
@@ -60,12 +62,16 @@ MUTANTS = {
                       "out[i] = 1.0 / 3.0 * u[i] + 2.0 / 3.0 * u2[i] + 1.0 / 3.0 * dt * A[i];", 0),
     "lf-fine-sign": ("Eq. (fineLF) sign", "for (int i = 0; i < nx; ++i) out[i] = u1[i] - dt * A[i];",
                      "for (int i = 0; i < nx; ++i) out[i] = u1[i] + dt * A[i];", 0),
+    "psi0-factor": ("Eq. (coarseLFord0) M dt", "for (int i = 0; i < nx; ++i) out[i] -= M * dt * b[i];",
+                    "for (int i = 0; i < nx; ++i) out[i] -= dt * b[i];", 0),
     "psi1-powers": ("Eq. (coarseLFord1) powers of E", "op_E_pow(nx, M - i, a, t);          /* E^{M-i} u */",
                     "op_E_pow(nx, i - 1, a, t);          /* E^{M-i} u */", 0),
     # Sec. 3.2 and Algorithm 1
     "frelax-g-index": ("Eq. (relaxation) right-hand side",
                        "step_plus_g(M, l, row(M->u[l], nx, m * j + r - 1), m * j + r,",
                        "step_plus_g(M, l, row(M->u[l], nx, m * j + r - 1), m * j + r - 1,", 0),
+    "frelax-range": ("reading A14 (m - 1 F-points per chunk)", "for (int r = 1; r < m; ++r)",
+                     "for (int r = 1; r < m - 1; ++r)", 0),
     "fcf-without-c": ("FCF-relaxation", "        c_relax(M, l);\n        f_relax(M, l);\n",
                       "        f_relax(M, l);\n", 0),
     "residual-index": ("Eq. (restriction::rhs) residual",
@@ -78,6 +84,13 @@ MUTANTS = {
     "coarse-g-index": ("Eq. (coarseCorr)",
                        "step_plus_g(M, l, row(M->u[l], nx, i - 1), i, row(M->u[l], nx, i), work);",
                        "step_plus_g(M, l, row(M->u[l], nx, i - 1), i - 1, row(M->u[l], nx, i), work);", 0),
+    "restrict-without-g0": ("reading A8 (g^0 = u0 on every level)",
+                            "memcpy(row(M->g[l + 1], nx, 0), row(M->g[l], nx, 0), sizeof(double) * (size_t)nx);",
+                            "", 0),
+    "inject-without-last": ("Eq. (interpolation) injection", "for (int i = 0; i <= nc; ++i)",
+                            "for (int i = 0; i < nc; ++i)", 0),
+    "stop-rule": ("reading A11 (stop when ||r|| < tol)", "if (rk < tol) { st = ORC_OK; break; }",
+                  "if (rk < 10 * tol) { st = ORC_OK; break; }", 0),
     "interp-without-frelax": ("Eq. (interpolation) F-relaxation", "    if (do_frelax) f_relax(M, l);\n",
                               "    (void)do_frelax;\n", 0),
     "vcycle-without-recursion": ("Algorithm 1 below level 0",

@@ -133,3 +133,26 @@ def test_eno_property_discontinuity():
     assert om[rough[0]] < 1e-10
     w, _, _, _ = O.weno5_left(q)
     assert abs(w - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("ratio", [1.0, 0.25, 7.0])
+def test_eps_is_one_millionth(ratio):
+    # reading A6: eps = 1e-6.  Only the stencil {i, i+1, i+2} sees the
+    # bump, so beta_1 = beta_2 = 0 and alpha_1 / alpha_0 = (d_1/d_0)
+    # ((eps + beta_0) / eps)^2.  Scale the bump so that beta_0 = ratio * eps
+    # (the indicator is quadratic in the data), then the weight ratio is
+    # (d_1/d_0) (1 + ratio)^2 for eps = 1e-6, and far from it for 1e-5.
+    unit = np.array([0.0, 0.0, 0.0, 0.0, 1.0])
+    _, _, b1, _ = O.weno5_left(unit)
+    r0 = int(np.argmax(b1))
+    assert b1[r0] > 0 and np.count_nonzero(b1) == 1
+    q = unit * np.sqrt(ratio * 1e-6 / b1[r0])
+    _, _, beta, om = O.weno5_left(q)
+    assert beta[r0] == pytest.approx(ratio * 1e-6, rel=1e-12)
+    others = [r for r in range(3) if r != r0]
+    for r in others:
+        d_ratio = om[r] / om[r0]
+        # the linear weights from a constant state (beta = 0)
+        _, _, _, lin = O.weno5_left(np.zeros(5))
+        assert d_ratio == pytest.approx(lin[r] / lin[r0] * (1.0 + ratio) ** 2, rel=1e-10)
+        assert abs(d_ratio - lin[r] / lin[r0] * (1.0 + ratio / 10.0) ** 2) > 1e-3 * d_ratio
