@@ -23,7 +23,6 @@ Multi-GPU (torchrun): independent replicas, one per GPU (the path has no
 exchange step on one problem); value = all ranks' cell updates / max time.
 """
 import argparse
-import ctypes
 import hashlib
 import json
 import os
