@@ -106,13 +106,17 @@ def main(argv=None):
         bt.run_cycles(bu0, 1)
         bt.launch_relax(1)
         torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("profiled")
+        t0.record()
         bt.launch_relax(a.reps)
+        t1.record()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         cells = sum(d["nx"] * (d["nt"] // d["m"]) * (2 * d["m"] + 1) for d in insts)
-        print("batched level-0 relaxation x%d: %d instances, %d cell updates per launch"
-              % (a.reps, len(insts), cells))
+        print("batched level-0 relaxation x%d: %d instances, %d cell updates per launch, "
+              "%.3f ms per launch (CUDA events)" % (a.reps, len(insts), cells, t0.elapsed_time(t1) / a.reps))
         bt.close()
         return 0
     c = CASES[a.case]
