@@ -12,14 +12,19 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_run_major_layout(tmp_path):
+def test_run_major_layout():
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
-    exe = str(tmp_path / "layout_check")
+    out = os.path.join(ROOT, "tests", "_build")   # git-ignored
+    os.makedirs(out, exist_ok=True)
+    exe = os.path.join(out, "layout_check.%d" % os.getpid())
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "layout_check.cu"), "-o", exe],
                    check=True, capture_output=True, text=True, timeout=600)
-    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    try:
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    finally:
+        os.remove(exe)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "0 failures" in r.stdout

@@ -11,6 +11,7 @@ stencil minus its middle value), and the coarsest solve's first row is the
 restricted u^0, which already equals g^0 (A8).
 """
 import os
+import shutil
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -135,8 +136,9 @@ def run_pins(lib):
 
 
 @pytest.fixture(scope="module")
-def outcomes(tmp_path_factory):
-    d = tmp_path_factory.mktemp("mutants")
+def outcomes():
+    d = os.path.join(ROOT, "tests", "_build", "mutants.%d" % os.getpid())   # git-ignored
+    os.makedirs(d, exist_ok=True)
     src = open(SRC).read()
     jobs = {"unchanged": src}
     for name, (_, text, new, occ) in MUTANTS.items():
@@ -144,14 +146,17 @@ def outcomes(tmp_path_factory):
 
     def one(item):
         name, code = item
-        c, so = str(d / (name + ".c")), str(d / (name + ".so"))
+        c, so = os.path.join(d, name + ".c"), os.path.join(d, name + ".so")
         with open(c, "w") as fh:
             fh.write(code)
         compile_oracle(c, so)
         return name, run_pins(so)
 
-    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
-        return dict(ex.map(one, jobs.items()))
+    try:
+        with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+            return dict(ex.map(one, jobs.items()))
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
 
 
 def test_unchanged_oracle_passes_the_pins(outcomes):
